@@ -1,0 +1,199 @@
+/*
+ * jetsci.h -- C ABI of the B300 (sm_103a) hex8 finite-element assembly library.
+ *
+ * The library evaluates, for a hex8 mesh with per-element material phases, the
+ * discrete residual R(u) of a nonlinear finite-element problem and its Jacobian
+ * K(u) = dR/du (JetSCI, Section II-A), assembles K into a CSR matrix whose pattern
+ * is fixed once before any values are produced (Section III-B: the non-zero count is
+ * precomputed, local dense element blocks are summed into a global sparse matrix),
+ * applies K to vectors without assembling it (the matrix-free operator of
+ * Section III-A), gives the gradient of 1/2 ||R||^2 with respect to a per-element
+ * Young's modulus (the differentiable-calibration use of the Introduction), and can
+ * replace the constitutive law by a learned MLP surrogate whose Jacobian provides the
+ * tangent (Section III-B, last paragraph).
+ *
+ * Discretisation (the paper fixes none of it; these are the library's readings):
+ * trilinear hex8 elements, 2x2x2 Gauss rule (points +-1/sqrt(3), unit weights,
+ * lexicographic order with xi fastest), total Lagrangian kinematics, no external
+ * load (R = f_int), and per phase either small-strain Hooke or the compressible
+ * neo-Hookean law W = mu/2 (I1-3) - mu lnJ + lambda/2 (lnJ)^2, with Lame constants
+ * from (E, nu).  Hex8 local node order: (-,-,-), (+,-,-), (+,+,-), (-,+,-),
+ * (-,-,+), (+,-,+), (+,+,+), (-,+,+).  DOF of node n, component c = 3n + c.
+ *
+ * Conventions for every call:
+ *  - Pointers named *_host are host memory; *_dev are device memory of the device
+ *    that was current when the mesh was created.  All device buffers are owned and
+ *    allocated by the caller unless stated; the library never frees caller memory.
+ *  - Outputs are overwritten (INSERT semantics, as in the paper's MatSetValuesCOO
+ *    with INSERT_ALL), never accumulated into.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) unless stated.  Only jetsci_mesh_create, jetsci_mesh_destroy,
+ *    jetsci_mesh_check and the surrogate create/destroy/get calls synchronise.
+ *  - Results are deterministic: element contributions are summed in a fixed
+ *    (colour-major) order without atomics, so repeated calls are bitwise identical.
+ *  - Every call returns a jetsci_status; on failure jetsci_last_error() gives a
+ *    thread-local message.  No C++ exception crosses the ABI.  Arguments are checked
+ *    on the host before any launch; kernels record inadmissible states (detJ <= 0,
+ *    det F <= 0, non-finite values) in a per-mesh device flag word read by
+ *    jetsci_mesh_check, and never trap.
+ */
+#ifndef JETSCI_H
+#define JETSCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jetsci_mesh_s *jetsci_mesh;           /* opaque, library-owned */
+typedef struct jetsci_surrogate_s *jetsci_surrogate; /* opaque, library-owned */
+
+typedef enum {
+    JETSCI_OK = 0,
+    JETSCI_ERR_ARG = 1,           /* NULL/invalid pointer, size or enum value          */
+    JETSCI_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has details)  */
+    JETSCI_ERR_OOM = 3,           /* device or host allocation failed                  */
+    JETSCI_ERR_MESH = 4,          /* connectivity/phase out of range, degenerate element */
+    JETSCI_ERR_NONFINITE = 5,     /* a kernel met a non-finite or inadmissible value   */
+    JETSCI_ERR_NOT_CONVERGED = 6, /* an iteration hit its cap                          */
+    JETSCI_ERR_UNSUPPORTED = 7    /* valid request the library does not implement      */
+} jetsci_status;
+
+/* Arithmetic of the element computations.  The global residual scatter and the
+ * residual norm are FP64 in every mode. */
+typedef enum {
+    JETSCI_FP64 = 0,      /* all element arithmetic in FP64; CSR values double        */
+    JETSCI_FP32 = 1,      /* element arithmetic in FP32 (FP64 geometry differences);
+                             CSR values float; R, K.v accumulated in FP64              */
+    JETSCI_TF32 = 2,      /* as FP32, with the element stiffness contraction on
+                             tensor cores in TF32 with FP32 accumulation               */
+    JETSCI_SURROGATE = 3, /* FP32 element arithmetic, stress and tangent from the
+                             mesh's MLP surrogate (BF16 tensor cores, FP32 accumulate)
+                             with the plain law as fallback out of range; CSR float    */
+    JETSCI_DF64 = 4       /* FP64-accurate two-float arithmetic on the FP32 pipes;
+                             CSR values double                                        */
+} jetsci_precision;
+
+typedef enum { JETSCI_LINEAR_ELASTIC = 0, JETSCI_NEO_HOOKEAN = 1 } jetsci_law;
+
+typedef enum { JETSCI_MATRIX_FREE = 0, JETSCI_CSR = 1 } jetsci_apply_mode;
+
+/* Material of one phase: Young's modulus [Pa], Poisson ratio (-1 < nu < 0.5), law. */
+typedef struct {
+    double E;
+    double nu;
+    int32_t law;
+    int32_t reserved; /* must be 0 */
+} jetsci_material;
+
+/* Device flag bits reported by jetsci_mesh_check. */
+#define JETSCI_FLAG_BAD_ELEMENT 0x1u /* detJ <= 0 at a Gauss point                 */
+#define JETSCI_FLAG_BAD_STATE 0x2u   /* det F <= 0 under the neo-Hookean law        */
+#define JETSCI_FLAG_NONFINITE 0x4u   /* NaN/Inf met in an input or an intermediate  */
+
+/* ---------------------------------------------------------------------------
+ * Mesh: geometry, connectivity, phases and materials ("element information" and
+ * "problem structure" of the paper's Fig. 1) plus everything derived once from
+ * them: the CSR pattern of K (rows = DOFs; per row the columns sorted ascending;
+ * DOFs of one node are interleaved so each row's columns come in node-sorted
+ * 3-wide blocks), an element colouring (no two elements of one colour share a
+ * node) and the element-to-CSR slot map.
+ *
+ * coords_host [n_nodes*3] (x,y,z per node), conn_host [n_elem*8] (node ids in the
+ * hex8 order above), phase_host [n_elem] (index into mats; may be NULL = all 0),
+ * mats [n_mats].  n_elem may be 0 (an empty mesh; every call is then a no-op that
+ * still overwrites its outputs).  Synchronises `stream`.  Errors: JETSCI_ERR_ARG
+ * (NULL where required, negative sizes, bad law/nu), JETSCI_ERR_MESH (node id or
+ * phase out of range, repeated node in an element, more than 255 neighbours of a
+ * node or more than 64 colours), JETSCI_ERR_OOM, JETSCI_ERR_CUDA.  On error *out
+ * is set to NULL and nothing is leaked.
+ */
+jetsci_status jetsci_mesh_create(const double *coords_host, int64_t n_nodes,
+                                 const int32_t *conn_host, int64_t n_elem,
+                                 const int32_t *phase_host, const jetsci_material *mats,
+                                 int32_t n_mats, void *stream, jetsci_mesh *out);
+
+/* Frees everything the mesh owns (waits for its work to finish).  NULL is a no-op. */
+jetsci_status jetsci_mesh_destroy(jetsci_mesh mesh);
+
+/* Sizes and the device CSR pattern (mesh-owned, read-only, valid until destroy).
+ * Any output pointer may be NULL.  rowptr has n_dof+1 int64 entries, col nnz int32. */
+jetsci_status jetsci_mesh_info(jetsci_mesh mesh, int64_t *n_dof, int64_t *nnz,
+                               const int64_t **rowptr_dev, const int32_t **col_dev,
+                               int32_t *n_colours);
+
+/* Copies the CSR pattern into caller buffers rowptr [n_dof+1] int64 and col [nnz] int32,
+ * which may be host or device memory (cudaMemcpyDefault).  Synchronises `stream`. */
+jetsci_status jetsci_mesh_copy_pattern(jetsci_mesh mesh, int64_t *rowptr, int32_t *col, void *stream);
+
+/* Synchronises the mesh's last stream, returns the device flag word (bits above) in
+ * *flags_host and clears it.  Returns JETSCI_ERR_NONFINITE if any bit was set. */
+jetsci_status jetsci_mesh_check(jetsci_mesh mesh, uint32_t *flags_host);
+
+/* ---------------------------------------------------------------------------
+ * Global residual R(u) = sum_e P_e^T R_e (Section II-A, R(u) = 0), with
+ * R_e(a,i) = sum_q w_q detJ_q (F S)_iJ G_aJ.
+ * u_dev [n_dof] FP64, R_dev [n_dof] FP64 (overwritten).  E_elem_dev [n_elem] FP64 or
+ * NULL: per-element Young's modulus replacing the phase's (the phase's nu and law are
+ * kept).  precision: JETSCI_FP64, FP32, DF64 or SURROGATE (TF32 acts as FP32 here).
+ */
+jetsci_status jetsci_residual(jetsci_mesh mesh, const double *u_dev, double *R_dev,
+                              int32_t precision, const double *E_elem_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Consistent tangent K(u) = dR/du in CSR values against the mesh's pattern
+ * (Section II-A; the values the paper hands to MatSetValuesCOO, Section III-C),
+ * K_e(a,i)(b,k) = sum_q w_q detJ_q sum_{J,L} G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL.
+ * vals_dev [nnz]: double for FP64/DF64, float for FP32/TF32/SURROGATE (overwritten).
+ * R_dev [n_dof] FP64 or NULL: if given, the residual is produced by the same pass.
+ */
+jetsci_status jetsci_tangent_csr(jetsci_mesh mesh, const double *u_dev, void *vals_dev,
+                                 double *R_dev, int32_t precision, const double *E_elem_dev,
+                                 void *stream);
+
+/* ---------------------------------------------------------------------------
+ * y = K(u) v.  mode JETSCI_MATRIX_FREE: element by element without forming K
+ * (Section III-A's matrix-free operator); vals_dev is ignored (may be NULL).
+ * mode JETSCI_CSR: sparse product with the CSR values vals_dev of the same mesh
+ * (double for FP64/DF64, float for FP32/TF32/SURROGATE); u_dev is ignored.
+ * u_dev, v_dev, y_dev [n_dof] FP64; y overwritten.  y must not alias u or v.
+ */
+jetsci_status jetsci_apply_tangent(jetsci_mesh mesh, const double *u_dev, const double *v_dev,
+                                   double *y_dev, int32_t mode, const void *vals_dev,
+                                   int32_t precision, const double *E_elem_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Gradient of L(E) = 1/2 ||R(u; E)||^2 with respect to each element's Young's modulus
+ * (differentiable calibration, Introduction).  Because the stress of both laws is
+ * linear in (lambda, mu), which are proportional to E at fixed nu,
+ * dL/dE_e = R[dofs_e] . R_e(u; E = 1).  R_dev must be jetsci_residual(u, E) of the
+ * same mesh/precision.  E_elem_dev [n_elem] or NULL (phase moduli); dLdE_dev [n_elem]
+ * FP64 (overwritten).  precision: JETSCI_FP64, FP32 or DF64.
+ */
+jetsci_status jetsci_material_grad(jetsci_mesh mesh, const double *u_dev,
+                                   const double *E_elem_dev, const double *R_dev,
+                                   double *dLdE_dev, int32_t precision, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * ||x||_2 of x_dev [n] FP64 into out_dev[0] (device FP64), by a fixed-shape two-pass
+ * reduction (chunks of 8192 entries, fixed trees), so the result is bitwise
+ * reproducible.  This decides Newton convergence (the paper solves to a relative
+ * residual of 1e-13, Section V-B).  Uses mesh-owned scratch, so calls on one mesh must
+ * not overlap on different streams.  n may exceed n_dof up to 2^31 * 8192 - 1.
+ */
+jetsci_status jetsci_norm2(jetsci_mesh mesh, const double *x_dev, int64_t n, double *out_dev,
+                           void *stream);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *jetsci_last_error(void);
+
+/* Library version string. */
+const char *jetsci_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JETSCI_H */

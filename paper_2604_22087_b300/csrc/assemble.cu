@@ -1,0 +1,401 @@
+// Element kernels: residual, consistent tangent into CSR, matrix-free tangent product and
+// the material-gradient (adjoint) pass.  All scatters are coloured read-modify-writes:
+// within one colour no two elements share a node, colours run in a fixed order, so the
+// sums are race-free without atomics and bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include "element.cuh"
+#include "jetsci_internal.h"
+
+namespace jetsci {
+
+struct ElemArgs {
+    const int32_t *__restrict__ conn;
+    const double *__restrict__ coords;
+    const int32_t *__restrict__ phase;
+    const Material *__restrict__ mats;
+    const double *__restrict__ E_elem;
+    const int32_t *__restrict__ elems;  // element ids of one colour (NULL = identity)
+    int64_t n;                          // number of elements in the list
+    uint32_t *flags;
+};
+
+template <typename T>
+__device__ __forceinline__ bool finite3(const T f[3]) {
+    return isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]);
+}
+
+__device__ __forceinline__ void raise_flag(uint32_t *flags, uint32_t bits) {
+    if (bits) atomicOr(flags, bits);
+}
+
+// Upper-triangle node pairs (a <= b) of the 8x8 block structure of K_e.
+__constant__ int8_t kPairA[36] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2,
+                                  2, 2, 2, 3, 3, 3, 3, 3, 4, 4, 4, 4, 5, 5, 5, 6, 6, 7};
+__constant__ int8_t kPairB[36] = {0, 1, 2, 3, 4, 5, 6, 7, 1, 2, 3, 4, 5, 6, 7, 2, 3, 4,
+                                  5, 6, 7, 3, 4, 5, 6, 7, 4, 5, 6, 7, 5, 6, 7, 6, 7, 7};
+// Reference coordinates (+-1) of the hex8 local nodes, packed as bits (xi, eta, zeta).
+__constant__ int8_t kNodeBits[8] = {0, 1, 3, 2, 4, 5, 7, 6};
+
+// ---------------------------------------------------------------------------- residual
+// R_e(a,i) = sum_q w detJ P_iJ G_aJ, scattered into R (FP64 in every precision).
+template <typename T>
+__global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__restrict__ u,
+                                                  double *__restrict__ R) {
+    const int l = threadIdx.x & 7;
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool active = slot < A.n;
+    const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
+    int32_t node;
+    GaussKinematics<T> K;
+    T cu[3];
+    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+    ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
+    Constitutive<T> c;
+    constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, false);
+    T f[3];
+    nodal_force(c.P, K, l, f);
+    if (active) {
+        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+                        (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
+        raise_flag(A.flags, bits);
+#pragma unroll
+        for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
+    }
+}
+
+// ---------------------------------------------------------------------------- tangent
+// Phase 1 (8 lanes per element, lane = Gauss point): kinematics, constitutive update,
+// optional residual, and per Gauss point the spatial gradients g_a = F^-T G_a of all
+// eight shape functions plus c*lam, c*m, c*tau (c = w detJ) into shared memory.
+// Phase 2 (one thread per element and node pair a <= b):
+//   K_ab,ik = sum_q c [ lam g_ai g_bk + m g_ak g_bi + delta_ik (g_a.tau g_b + m g_a.g_b) ]
+// which is the push-forward of sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL
+// for the neo-Hookean CC (and lam, m = mu, tau = 0, g = G for the linear law).
+constexpr int kTanElems = 32;  // elements per 256-thread block
+
+template <typename T>
+struct TangentSmem {
+    T g[kTanElems][8][8][3];  // [elem][q][node a][component]
+    T coef[kTanElems][8][8];  // [elem][q]: c lam, c m, c tau (00,11,22,12,02,01)
+    int32_t node[kTanElems][8];
+    int32_t elem[kTanElems];
+};
+
+template <typename T, typename VT>
+__global__ void __launch_bounds__(256) k_tangent(ElemArgs A, const double *__restrict__ u,
+                                                 const int64_t *__restrict__ rowptr,
+                                                 const uint8_t *__restrict__ slotmap,
+                                                 VT *__restrict__ vals, double *__restrict__ R) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TangentSmem<T> &sm = *reinterpret_cast<TangentSmem<T> *>(smem_raw);
+    const int l = threadIdx.x & 7;
+    const int es = threadIdx.x >> 3;
+    const int64_t slot = (int64_t)blockIdx.x * kTanElems + es;
+    const bool active = slot < A.n;
+    const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
+    {
+        int32_t node;
+        GaussKinematics<T> K;
+        T cu[3];
+        gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+        ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
+        Constitutive<T> c;
+        constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, true);
+        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
+        if (R) {
+            T f[3];
+            nodal_force(c.P, K, l, f);
+            if (active) {
+                bits |= finite3(f) ? 0u : JETSCI_FLAG_NONFINITE;
+#pragma unroll
+                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
+            }
+        }
+        if (active) raise_flag(A.flags, bits);
+        // W = (F Jp)^-1 = Jp^-1 F^-1 = adj(Jp) F^-1 / det(Jp)
+        T rdJ = my_rcp(K.dJ);
+        T W[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                W[d][j] = (K.aJ[d][0] * c.Fi[0][j] + K.aJ[d][1] * c.Fi[1][j] + K.aJ[d][2] * c.Fi[2][j]) * rdJ;
+        // g_a,j = sum_d W_dj n_a,d with n_a = 8 dN_a/dxi at this Gauss point
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            const int bits_a = kNodeBits[a];
+            T s0 = (bits_a & 1) ? T(1) : T(-1), s1 = (bits_a & 2) ? T(1) : T(-1), s2 = (bits_a & 4) ? T(1) : T(-1);
+            T fx = T(1) + s0 * K.xi, fy = T(1) + s1 * K.eta, fz = T(1) + s2 * K.zeta;
+            T n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
+#pragma unroll
+            for (int j = 0; j < 3; j++) sm.g[es][l][a][j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
+        }
+        T cw = K.dJ * T(1.0 / 512.0);
+        sm.coef[es][l][0] = cw * c.lam;
+        sm.coef[es][l][1] = cw * c.m;
+        sm.coef[es][l][2] = cw * c.tau[0][0];
+        sm.coef[es][l][3] = cw * c.tau[1][1];
+        sm.coef[es][l][4] = cw * c.tau[2][2];
+        sm.coef[es][l][5] = cw * c.tau[1][2];
+        sm.coef[es][l][6] = cw * c.tau[0][2];
+        sm.coef[es][l][7] = cw * c.tau[0][1];
+        sm.node[es][hex_node_of_lane(l)] = node;
+        if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < kTanElems * 36; it += blockDim.x) {
+        const int ee = it / 36, p = it - 36 * (it / 36);
+        const int32_t eid = sm.elem[ee];
+        if (eid < 0) continue;
+        const int a = kPairA[p], b = kPairB[p];
+        T Kab[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
+#pragma unroll 2
+        for (int q = 0; q < 8; q++) {
+            const T *ga = sm.g[ee][q][a];
+            const T *gb = sm.g[ee][q][b];
+            const T *cf = sm.coef[ee][q];
+            T a0 = ga[0], a1 = ga[1], a2 = ga[2], b0 = gb[0], b1 = gb[1], b2 = gb[2];
+            T lam = cf[0], m = cf[1];
+            T t0 = cf[2] * b0 + cf[7] * b1 + cf[6] * b2;
+            T t1 = cf[7] * b0 + cf[3] * b1 + cf[5] * b2;
+            T t2 = cf[6] * b0 + cf[5] * b1 + cf[4] * b2;
+            T s = a0 * (t0 + m * b0) + a1 * (t1 + m * b1) + a2 * (t2 + m * b2);
+            T la0 = lam * a0, la1 = lam * a1, la2 = lam * a2;
+            T ma0 = m * a0, ma1 = m * a1, ma2 = m * a2;
+            Kab[0][0] += la0 * b0 + ma0 * b0 + s;
+            Kab[0][1] += la0 * b1 + ma1 * b0;
+            Kab[0][2] += la0 * b2 + ma2 * b0;
+            Kab[1][0] += la1 * b0 + ma0 * b1;
+            Kab[1][1] += la1 * b1 + ma1 * b1 + s;
+            Kab[1][2] += la1 * b2 + ma2 * b1;
+            Kab[2][0] += la2 * b0 + ma0 * b2;
+            Kab[2][1] += la2 * b1 + ma1 * b2;
+            Kab[2][2] += la2 * b2 + ma2 * b2 + s;
+        }
+        const int32_t na = sm.node[ee][a], nb = sm.node[ee][b];
+        const int64_t sbase = 64 * (int64_t)eid;
+        const int sab = slotmap[sbase + 8 * a + b];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
+#pragma unroll
+            for (int k = 0; k < 3; k++) dst[k] += (VT)Kab[i][k];
+        }
+        if (a != b) {
+            const int sba = slotmap[sbase + 8 * b + a];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
+#pragma unroll
+                for (int i = 0; i < 3; i++) dst[i] += (VT)Kab[i][k];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- K v, matrix-free
+// y_a += sum_q w detJ [ (Hv S) + tau' F^-T ] G_a with Hv = grad_X v, h = Hv F^-1,
+// tau' = lam tr(h) I + m (h + h^T)  (neo-Hookean);  y_a += sum_q w detJ sigma(Hv) G_a (linear).
+template <typename T>
+__global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__restrict__ u,
+                                                  const double *__restrict__ v, double *__restrict__ y) {
+    const int l = threadIdx.x & 7;
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool active = slot < A.n;
+    const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
+    int32_t node;
+    GaussKinematics<T> K;
+    T cu[3];
+    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+    ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
+    T Hv[3][3];
+    field_gradient<T>(v, node, l, K, Hv);
+    T Y[3][3];
+    bool ok = true;
+    if (mt.law == JETSCI_LINEAR_ELASTIC) {
+        T lam = (T)mt.lam, mu = (T)mt.mu;
+        T tr = Hv[0][0] + Hv[1][1] + Hv[2][2];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) Y[i][j] = mu * (Hv[i][j] + Hv[j][i]) + ((i == j) ? lam * tr : T(0));
+    } else {
+        Constitutive<T> c;
+        constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, false);
+        ok = c.ok;
+        T h[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) h[i][j] = Hv[i][0] * c.Fi[0][j] + Hv[i][1] * c.Fi[1][j] + Hv[i][2] * c.Fi[2][j];
+        T trh = h[0][0] + h[1][1] + h[2][2];
+        T tp[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) tp[i][j] = c.m * (h[i][j] + h[j][i]) + ((i == j) ? c.lam * trh : T(0));
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int J2 = 0; J2 < 3; J2++)
+                Y[i][J2] = Hv[i][0] * c.S[0][J2] + Hv[i][1] * c.S[1][J2] + Hv[i][2] * c.S[2][J2] +
+                           tp[i][0] * c.Fi[J2][0] + tp[i][1] * c.Fi[J2][1] + tp[i][2] * c.Fi[J2][2];
+    }
+    T f[3];
+    nodal_force(Y, K, l, f);
+    if (active) {
+        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+                        (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
+        raise_flag(A.flags, bits);
+#pragma unroll
+        for (int i = 0; i < 3; i++) y[3 * (int64_t)node + i] += (double)f[i];
+    }
+}
+
+// ---------------------------------------------------------------------------- adjoint
+// dL/dE_e = R[dofs_e] . R_e(u; E = 1) for L = 1/2 ||R||^2 (stress linear in E at fixed nu).
+template <typename T>
+__global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double *__restrict__ u,
+                                                       const double *__restrict__ R, double *__restrict__ g) {
+    const int l = threadIdx.x & 7;
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool active = slot < A.n;
+    const int64_t e = active ? slot : A.n - 1;
+    int32_t node;
+    GaussKinematics<T> K;
+    T cu[3];
+    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+    ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, true);
+    Constitutive<T> c;
+    constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, false);
+    T f[3];
+    nodal_force(c.P, K, l, f);
+    double d = R[3 * (int64_t)node] * (double)f[0] + R[3 * (int64_t)node + 1] * (double)f[1] +
+               R[3 * (int64_t)node + 2] * (double)f[2];
+    d = allreduce8(d);
+    if (active && l == 0) {
+        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+                        (isfinite(d) ? 0u : JETSCI_FLAG_NONFINITE);
+        raise_flag(A.flags, bits);
+        g[e] = d;
+    }
+}
+
+// ---------------------------------------------------------------------------- launchers
+static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
+    ElemArgs A;
+    A.conn = m->d_conn;
+    A.coords = m->d_coords;
+    A.phase = m->d_phase;
+    A.mats = m->d_mats;
+    A.E_elem = E_elem;
+    A.elems = nullptr;
+    A.n = 0;
+    A.flags = m->d_flags;
+    return A;
+}
+
+template <typename T>
+static void residual_colours(jetsci_mesh m, ElemArgs A, const double *u, double *R, cudaStream_t s) {
+    for (int c = 0; c < m->n_colours; c++) {
+        A.elems = m->d_colour_elems + m->colour_ptr[c];
+        A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
+        if (A.n == 0) continue;
+        unsigned grid = (unsigned)((8 * A.n + 127) / 128);
+        k_residual<T><<<grid, 128, 0, s>>>(A, u, R);
+    }
+}
+
+jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int precision,
+                              const double *E_elem, cudaStream_t s) {
+    JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
+    ElemArgs A = make_args(m, E_elem);
+    if (precision == JETSCI_FP64)
+        residual_colours<double>(m, A, u, R, s);
+    else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
+        residual_colours<float>(m, A, u, R, s);
+    else
+        return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the residual");
+    JETSCI_CUDA_TRY(cudaGetLastError());
+    return JETSCI_OK;
+}
+
+template <typename T, typename VT>
+static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u, VT *vals, double *R,
+                                     cudaStream_t s) {
+    const size_t smem = sizeof(TangentSmem<T>);
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int c = 0; c < m->n_colours; c++) {
+        A.elems = m->d_colour_elems + m->colour_ptr[c];
+        A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
+        if (A.n == 0) continue;
+        unsigned grid = (unsigned)((A.n + kTanElems - 1) / kTanElems);
+        k_tangent<T, VT><<<grid, 256, smem, s>>>(A, u, m->d_rowptr, m->d_slot, vals, R);
+    }
+    JETSCI_CUDA_TRY(cudaGetLastError());
+    return JETSCI_OK;
+}
+
+jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double *R, int precision,
+                             const double *E_elem, cudaStream_t s) {
+    ElemArgs A = make_args(m, E_elem);
+    if (precision == JETSCI_FP64) {
+        JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(double), s));
+        if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
+        return tangent_colours<double, double>(m, A, u, (double *)vals, R, s);
+    }
+    if (precision == JETSCI_FP32) {
+        JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(float), s));
+        if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
+        return tangent_colours<float, float>(m, A, u, (float *)vals, R, s);
+    }
+    return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the tangent");
+}
+
+template <typename T>
+static void apply_colours(jetsci_mesh m, ElemArgs A, const double *u, const double *v, double *y,
+                          cudaStream_t s) {
+    for (int c = 0; c < m->n_colours; c++) {
+        A.elems = m->d_colour_elems + m->colour_ptr[c];
+        A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
+        if (A.n == 0) continue;
+        unsigned grid = (unsigned)((8 * A.n + 127) / 128);
+        k_apply_mf<T><<<grid, 128, 0, s>>>(A, u, v, y);
+    }
+}
+
+jetsci_status launch_apply_mf(jetsci_mesh m, const double *u, const double *v, double *y, int precision,
+                              const double *E_elem, cudaStream_t s) {
+    JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
+    ElemArgs A = make_args(m, E_elem);
+    if (precision == JETSCI_FP64)
+        apply_colours<double>(m, A, u, v, y, s);
+    else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
+        apply_colours<float>(m, A, u, v, y, s);
+    else
+        return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the matrix-free product");
+    JETSCI_CUDA_TRY(cudaGetLastError());
+    return JETSCI_OK;
+}
+
+jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem, const double *R,
+                                   double *g, int precision, cudaStream_t s) {
+    ElemArgs A = make_args(m, E_elem);
+    A.n = m->n_elem;
+    unsigned grid = (unsigned)((8 * A.n + 127) / 128);
+    if (precision == JETSCI_FP64)
+        k_material_grad<double><<<grid, 128, 0, s>>>(A, u, R, g);
+    else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
+        k_material_grad<float><<<grid, 128, 0, s>>>(A, u, R, g);
+    else
+        return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the material gradient");
+    JETSCI_CUDA_TRY(cudaGetLastError());
+    return JETSCI_OK;
+}
+
+}  // namespace jetsci

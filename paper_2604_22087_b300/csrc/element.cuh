@@ -1,0 +1,329 @@
+// Device-side element arithmetic for hex8 / 2x2x2 Gauss, shared by the assembly,
+// matrix-free and adjoint kernels.
+//
+// Layout: eight consecutive lanes of a warp own one element.  Lane l (0..7) stands for
+// Gauss point q = l (xi = +-g by bit 0, eta by bit 1, zeta by bit 2, g = 1/sqrt 3; the
+// paper's per-element quadrature, Section III-B) and, for gathers and scatters, for the
+// element node whose reference coordinates carry the same bit pattern, i.e. hex8 local
+// node kPerm[l].
+//
+// Geometry and displacement fields are trilinear, f(xi) = sum_m c_m mono_m(xi) over the
+// monomials m in {1, xi, eta, xi eta, zeta, xi zeta, eta zeta, xi eta zeta} (bit pattern
+// of m = which coordinates appear).  A 3-stage shuffle butterfly over the eight lanes
+// turns nodal values into 8*c_m held by lane m; it runs in FP64 on the gathered data, so
+// the differences that carry the element's small size and strain are exact before any
+// conversion to a lower-precision element type.  Reference derivatives at the lane's
+// Gauss point then need four coefficients per direction.  The transposed butterfly
+// turns per-Gauss-point stress moments back into nodal forces.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jetsci_internal.h"
+
+namespace jetsci {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int hex_node_of_lane(int l) {
+    // binary (xi, eta, zeta) bit pattern -> hex8 local node number
+    return (0x67542310 >> (4 * l)) & 0xF;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl8(T v, int src) {
+    return __shfl_sync(kFull, v, src, 8);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_xor8(T v, int mask) {
+    return __shfl_xor_sync(kFull, v, mask, 8);
+}
+
+// Nodal values (lane = node in binary order) -> 8 * monomial coefficient (lane = monomial).
+__device__ __forceinline__ double butterfly_forward(double v, int l) {
+#pragma unroll
+    for (int s = 1; s < 8; s <<= 1) {
+        double p = shfl_xor8(v, s);
+        v = (l & s) ? v - p : v + p;
+    }
+    return v;
+}
+
+// Transpose of the forward butterfly: lane m holds a monomial moment, result at lane l
+// (node in binary order) is sum_m mono_m(node l) * moment_m.
+template <typename T>
+__device__ __forceinline__ T butterfly_transpose(T v, int l) {
+#pragma unroll
+    for (int s = 1; s < 8; s <<= 1) {
+        T p = shfl_xor8(v, s);
+        v = (l & s) ? v + p : v - p;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T allreduce8(T v) {
+    v += shfl_xor8(v, 1);
+    v += shfl_xor8(v, 2);
+    v += shfl_xor8(v, 4);
+    return v;
+}
+
+// 8 * reference derivatives at the lane's Gauss point from 8 * monomial coefficients held
+// by lanes 1..7 (component held by the calling lane in `c`):
+//   d/dxi   = c_xi   + c_xieta eta + c_xizeta zeta + c_xietazeta eta zeta
+//   d/deta  = c_eta  + c_xieta xi  + c_etazeta zeta + c_xietazeta xi zeta
+//   d/dzeta = c_zeta + c_xizeta xi + c_etazeta eta  + c_xietazeta xi eta
+template <typename T>
+__device__ __forceinline__ void ref_gradient(T c, T xi, T eta, T zeta, T out[3]) {
+    T c1 = shfl8(c, 1), c2 = shfl8(c, 2), c3 = shfl8(c, 3), c4 = shfl8(c, 4);
+    T c5 = shfl8(c, 5), c6 = shfl8(c, 6), c7 = shfl8(c, 7);
+    out[0] = c1 + c3 * eta + c5 * zeta + c7 * (eta * zeta);
+    out[1] = c2 + c3 * xi + c6 * zeta + c7 * (xi * zeta);
+    out[2] = c4 + c5 * xi + c6 * eta + c7 * (xi * eta);
+}
+
+template <typename T>
+__device__ __forceinline__ T det3(const T A[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+           A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+// Adjugate (transpose of the cofactor matrix): A^-1 = adj / det.
+template <typename T>
+__device__ __forceinline__ void adj3(const T A[3][3], T B[3][3]) {
+    B[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    B[0][1] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+    B[0][2] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    B[1][0] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    B[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    B[1][2] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+    B[2][0] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    B[2][1] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+    B[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+}
+
+template <typename T>
+__device__ __forceinline__ T my_log(T x);
+template <>
+__device__ __forceinline__ double my_log<double>(double x) { return log(x); }
+template <>
+__device__ __forceinline__ float my_log<float>(float x) { return logf(x); }
+
+template <typename T>
+__device__ __forceinline__ T my_rcp(T x) { return T(1) / x; }
+
+// Material of element e as (law, lambda, mu) in T.
+struct ElemMaterial {
+    int law;
+    double lam, mu;
+};
+
+__device__ __forceinline__ ElemMaterial element_material(const Material *__restrict__ mats,
+                                                         const int32_t *__restrict__ phase,
+                                                         const double *__restrict__ E_elem,
+                                                         int64_t e, bool unit_modulus) {
+    const Material &mt = mats[phase[e]];
+    ElemMaterial r;
+    r.law = mt.law;
+    if (unit_modulus) {
+        r.lam = mt.lam1;
+        r.mu = mt.mu1;
+    } else if (E_elem) {
+        double E = E_elem[e];
+        r.lam = E * mt.lam1;
+        r.mu = E * mt.mu1;
+    } else {
+        r.lam = mt.lam;
+        r.mu = mt.mu;
+    }
+    return r;
+}
+
+// Per-lane kinematics at the lane's Gauss point.
+//   Jp = 8 dX/dxi, aJ = adj(Jp), dJ = det(Jp)   (detJ = dJ / 512)
+//   H  = grad_X u = (8 du/dxi) Jp^-1
+template <typename T>
+struct GaussKinematics {
+    T xi, eta, zeta;
+    T Jp[3][3], aJ[3][3], dJ;
+    T H[3][3];
+};
+
+// Gathers coordinates and one nodal field for element e, forms coefficients (FP64) and the
+// kinematics at the lane's Gauss point.  `node` receives the global node of the lane.
+template <typename T>
+__device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ conn,
+                                                 const double *__restrict__ coords,
+                                                 const double *__restrict__ u, int64_t e, int l,
+                                                 int32_t &node, GaussKinematics<T> &K, T cu[3]) {
+    node = conn[8 * e + hex_node_of_lane(l)];
+    double X[3], U[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        X[i] = coords[3 * (int64_t)node + i];
+        U[i] = u ? u[3 * (int64_t)node + i] : 0.0;
+    }
+    T cx[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        cx[i] = (T)butterfly_forward(X[i], l);
+        cu[i] = (T)butterfly_forward(U[i], l);
+    }
+    const T g = (T)0.57735026918962576451;
+    K.xi = (l & 1) ? g : -g;
+    K.eta = (l & 2) ? g : -g;
+    K.zeta = (l & 4) ? g : -g;
+    T Du[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        ref_gradient(cx[i], K.xi, K.eta, K.zeta, K.Jp[i]);
+        ref_gradient(cu[i], K.xi, K.eta, K.zeta, Du[i]);
+    }
+    adj3(K.Jp, K.aJ);
+    K.dJ = K.Jp[0][0] * K.aJ[0][0] + K.Jp[0][1] * K.aJ[1][0] + K.Jp[0][2] * K.aJ[2][0];
+    T rdJ = my_rcp(K.dJ);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            K.H[i][j] = (Du[i][0] * K.aJ[0][j] + Du[i][1] * K.aJ[1][j] + Du[i][2] * K.aJ[2][j]) * rdJ;
+}
+
+// Gradient of a second nodal field v with the same geometry: Hv = (8 dv/dxi) Jp^-1.
+template <typename T>
+__device__ __forceinline__ void field_gradient(const double *__restrict__ v, int32_t node, int l,
+                                               const GaussKinematics<T> &K, T Hv[3][3]) {
+    T cv[3], Dv[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) cv[i] = (T)butterfly_forward(v[3 * (int64_t)node + i], l);
+#pragma unroll
+    for (int i = 0; i < 3; i++) ref_gradient(cv[i], K.xi, K.eta, K.zeta, Dv[i]);
+    T rdJ = my_rcp(K.dJ);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            Hv[i][j] = (Dv[i][0] * K.aJ[0][j] + Dv[i][1] * K.aJ[1][j] + Dv[i][2] * K.aJ[2][j]) * rdJ;
+}
+
+// Constitutive state at one Gauss point.  P = first Piola-Kirchhoff stress.  For the
+// tangent: Fi = F^-1 (identity for the linear law), tau = Kirchhoff stress F S F^T,
+// lam and m = mu - lam lnJ so that the push-forward of CC is lam I(x)I + 2m Isym.
+template <typename T>
+struct Constitutive {
+    T P[3][3];
+    T S[3][3];
+    T Fi[3][3];
+    T F[3][3];
+    T tau[3][3];
+    T lam, m;
+    bool ok;
+};
+
+template <typename T>
+__device__ __forceinline__ void constitutive(int law, T lam, T mu, const T H[3][3],
+                                             Constitutive<T> &c, bool want_tangent) {
+    c.ok = true;
+    if (law == JETSCI_LINEAR_ELASTIC) {
+        T tr = H[0][0] + H[1][1] + H[2][2];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                T s = mu * (H[i][j] + H[j][i]);
+                if (i == j) s += lam * tr;
+                c.P[i][j] = s;
+                c.S[i][j] = s;
+                c.F[i][j] = (i == j) ? T(1) : T(0);
+                c.Fi[i][j] = c.F[i][j];
+                c.tau[i][j] = T(0);
+            }
+        c.lam = lam;
+        c.m = mu;
+        return;
+    }
+    // compressible neo-Hookean: S = mu I + (lam lnJ - mu) C^-1
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) c.F[i][j] = ((i == j) ? T(1) : T(0)) + H[i][j];
+    T aF[3][3];
+    adj3(c.F, aF);
+    T J = c.F[0][0] * aF[0][0] + c.F[0][1] * aF[1][0] + c.F[0][2] * aF[2][0];
+    c.ok = J > T(0);
+    T Js = c.ok ? J : T(1);
+    T rJ = my_rcp(Js);
+    T lnJ = my_log(Js);
+    // C^-1 = F^-1 F^-T with F^-1 = adj(F) / J
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) c.Fi[i][j] = aF[i][j] * rJ;
+    T Ci[3][3];
+#pragma unroll
+    for (int I = 0; I < 3; I++)
+#pragma unroll
+        for (int K = I; K < 3; K++) {
+            T s = c.Fi[I][0] * c.Fi[K][0] + c.Fi[I][1] * c.Fi[K][1] + c.Fi[I][2] * c.Fi[K][2];
+            Ci[I][K] = s;
+            Ci[K][I] = s;
+        }
+    T a = lam * lnJ - mu;
+#pragma unroll
+    for (int I = 0; I < 3; I++)
+#pragma unroll
+        for (int K = 0; K < 3; K++) c.S[I][K] = a * Ci[I][K] + ((I == K) ? mu : T(0));
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int J2 = 0; J2 < 3; J2++)
+            c.P[i][J2] = c.F[i][0] * c.S[0][J2] + c.F[i][1] * c.S[1][J2] + c.F[i][2] * c.S[2][J2];
+    c.lam = lam;
+    c.m = mu - lam * lnJ;
+    if (want_tangent) {
+        // tau = F S F^T = mu (F F^T - I) + lam lnJ I
+        T ll = lam * lnJ;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = i; k < 3; k++) {
+                T b = c.F[i][0] * c.F[k][0] + c.F[i][1] * c.F[k][1] + c.F[i][2] * c.F[k][2];
+                T t = mu * b + ((i == k) ? (ll - mu) : T(0));
+                c.tau[i][k] = t;
+                c.tau[k][i] = t;
+            }
+    }
+}
+
+// Nodal force of the lane's node from the lane's (Gauss point's) stress moment matrix
+// Q_id = (w/64) sum_j Y_ij adj(Jp)_dj, i.e. w detJ Y J^-T: returns
+// f_a,i = sum_q sum_d Q_q,id dN_a/dxi_d(q) for node a = lane (binary order).
+template <typename T>
+__device__ __forceinline__ void nodal_force(const T Y[3][3], const GaussKinematics<T> &K, int l,
+                                            T f[3]) {
+    const T w64 = T(1.0 / 64.0);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        T Q0 = (Y[i][0] * K.aJ[0][0] + Y[i][1] * K.aJ[0][1] + Y[i][2] * K.aJ[0][2]) * w64;
+        T Q1 = (Y[i][0] * K.aJ[1][0] + Y[i][1] * K.aJ[1][1] + Y[i][2] * K.aJ[1][2]) * w64;
+        T Q2 = (Y[i][0] * K.aJ[2][0] + Y[i][1] * K.aJ[2][1] + Y[i][2] * K.aJ[2][2]) * w64;
+        // moment contributions of this Gauss point for monomials 1..7
+        T m1 = Q0, m2 = Q1, m4 = Q2;
+        T m3 = Q0 * K.eta + Q1 * K.xi;
+        T m5 = Q0 * K.zeta + Q2 * K.xi;
+        T m6 = Q1 * K.zeta + Q2 * K.eta;
+        T m7 = Q0 * (K.eta * K.zeta) + Q1 * (K.xi * K.zeta) + Q2 * (K.xi * K.eta);
+        // sum over the 8 Gauss points, then place moment m at lane m
+        m1 = allreduce8(m1); m2 = allreduce8(m2); m3 = allreduce8(m3); m4 = allreduce8(m4);
+        m5 = allreduce8(m5); m6 = allreduce8(m6); m7 = allreduce8(m7);
+        T mine = (l == 1) ? m1 : (l == 2) ? m2 : (l == 3) ? m3 : (l == 4) ? m4
+               : (l == 5) ? m5 : (l == 6) ? m6 : (l == 7) ? m7 : T(0);
+        f[i] = butterfly_transpose(mine, l) * T(0.125);
+    }
+}
+
+}  // namespace jetsci

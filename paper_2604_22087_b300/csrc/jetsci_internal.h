@@ -1,0 +1,84 @@
+// Internal declarations of libjetsci (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "jetsci.h"
+
+namespace jetsci {
+
+// Per-phase material table as the kernels read it.  lam1/mu1 are the Lame constants
+// for E = 1 (used when a per-element modulus scales them, and by the adjoint).
+struct Material {
+    double lam, mu;    // Lame constants of the phase's own E
+    double lam1, mu1;  // Lame constants per unit E (same nu)
+    int32_t law;
+    int32_t pad;
+};
+
+constexpr int kMaxPhases = 16;
+constexpr int kNormChunk = 8192;             // entries per first-pass partial
+constexpr int64_t kNormMaxPartials = 65536;  // mesh-owned scratch capacity
+
+struct Surrogate;
+
+}  // namespace jetsci
+
+struct jetsci_mesh_s {
+    int device = 0;
+    int64_t n_nodes = 0, n_elem = 0, n_dof = 0, nnz = 0;
+    int32_t n_mats = 0;
+    int32_t n_colours = 0;
+    std::vector<int64_t> colour_ptr;  // host: offsets of each colour in d_colour_elems
+    jetsci::Material mats[jetsci::kMaxPhases];
+
+    int32_t *d_conn = nullptr;          // [n_elem*8]
+    double *d_coords = nullptr;         // [n_nodes*3]
+    int32_t *d_phase = nullptr;         // [n_elem]
+    int64_t *d_rowptr = nullptr;        // [n_dof+1]
+    int32_t *d_col = nullptr;           // [nnz]
+    uint8_t *d_slot = nullptr;          // [n_elem*64]: slot[a*8+b] = rank of node b among node a's neighbours
+    int32_t *d_colour_elems = nullptr;  // [n_elem], grouped by colour, ascending within a colour
+    jetsci::Material *d_mats = nullptr; // [kMaxPhases]
+    double *d_norm_partials = nullptr;  // [kNormMaxPartials]
+    uint32_t *d_flags = nullptr;        // [1]
+    cudaStream_t last_stream = nullptr;
+    jetsci_surrogate surrogate = nullptr;
+};
+
+namespace jetsci {
+
+// Thread-local error message and helpers.
+void set_error(const std::string &msg);
+jetsci_status fail(jetsci_status st, const std::string &msg);
+jetsci_status cuda_fail(cudaError_t err, const char *what);
+
+#define JETSCI_CUDA_TRY(call)                                      \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::jetsci::cuda_fail(_e, #call); \
+    } while (0)
+
+// Checks that the current device is the mesh's device (switches to it) and records
+// the stream; returns JETSCI_OK or an error.
+jetsci_status enter(jetsci_mesh m, void *stream, cudaStream_t *s);
+
+// Launch wrappers implemented in the .cu files.
+jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int precision,
+                              const double *E_elem, cudaStream_t s);
+jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double *R,
+                             int precision, const double *E_elem, cudaStream_t s);
+jetsci_status launch_apply_mf(jetsci_mesh m, const double *u, const double *v, double *y,
+                              int precision, const double *E_elem, cudaStream_t s);
+jetsci_status launch_spmv(jetsci_mesh m, const void *vals, bool fp32, const double *v,
+                          double *y, cudaStream_t s);
+jetsci_status launch_norm2(const double *x, int64_t n, double *partials, int64_t cap,
+                           double *out, cudaStream_t s);
+jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
+                                   const double *R, double *g, int precision, cudaStream_t s);
+
+}  // namespace jetsci

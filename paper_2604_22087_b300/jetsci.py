@@ -1,0 +1,238 @@
+"""Thin Python binding of libjetsci (ctypes): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts torch tensors
+to raw pointers and the current CUDA stream, checks shapes/dtypes/devices, and turns
+status codes into exceptions.  There is no CPU path: if the compiled library is missing
+or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libjetsci.so")
+
+FP64, FP32, TF32, SURROGATE, DF64 = 0, 1, 2, 3, 4
+LINEAR_ELASTIC, NEO_HOOKEAN = 0, 1
+MATRIX_FREE, CSR = 0, 1
+FLAG_BAD_ELEMENT, FLAG_BAD_STATE, FLAG_NONFINITE = 0x1, 0x2, 0x4
+
+_STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_MESH", 5: "ERR_NONFINITE",
+           6: "ERR_NOT_CONVERGED", 7: "ERR_UNSUPPORTED"}
+
+# Names the C ABI exports (include/jetsci.h); checked by the CPU tests.
+EXPORTS = [
+    "jetsci_mesh_create", "jetsci_mesh_destroy", "jetsci_mesh_info", "jetsci_mesh_check",
+    "jetsci_mesh_copy_pattern",
+    "jetsci_residual", "jetsci_tangent_csr", "jetsci_apply_tangent", "jetsci_material_grad",
+    "jetsci_norm2", "jetsci_last_error", "jetsci_version",
+]
+
+
+class JetsciError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Material(C.Structure):
+    _fields_ = [("E", C.c_double), ("nu", C.c_double), ("law", C.c_int32), ("reserved", C.c_int32)]
+
+
+_vp = C.c_void_p
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libjetsci.so not built ({LIB_PATH}); run paper_2604_22087_b300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    i64, i32 = C.c_int64, C.c_int32
+    sig = {
+        "jetsci_mesh_create": [_vp, i64, _vp, i64, _vp, C.POINTER(Material), i32, _vp, C.POINTER(_vp)],
+        "jetsci_mesh_destroy": [_vp],
+        "jetsci_mesh_info": [_vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(_vp), C.POINTER(_vp),
+                             C.POINTER(i32)],
+        "jetsci_mesh_check": [_vp, C.POINTER(C.c_uint32)],
+        "jetsci_mesh_copy_pattern": [_vp, _vp, _vp, _vp],
+        "jetsci_residual": [_vp, _vp, _vp, i32, _vp, _vp],
+        "jetsci_tangent_csr": [_vp, _vp, _vp, _vp, i32, _vp, _vp],
+        "jetsci_apply_tangent": [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp],
+        "jetsci_material_grad": [_vp, _vp, _vp, _vp, _vp, i32, _vp],
+        "jetsci_norm2": [_vp, _vp, i64, _vp, _vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.jetsci_last_error.restype = C.c_char_p
+    lib.jetsci_version.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(st):
+    if st != 0:
+        raise JetsciError(st, lib.jetsci_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(t, n, name):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and t.numel() == n):
+        raise ValueError(f"{name}: need a contiguous CUDA float64 tensor of {n} entries")
+    return t
+
+
+def vals_dtype(precision):
+    return torch.float64 if precision in (FP64, DF64) else torch.float32
+
+
+class Mesh:
+    """A hex8 mesh on the current CUDA device (wraps jetsci_mesh)."""
+
+    def __init__(self, coords, conn, phase, materials, stream=None):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        phase = None if phase is None else np.ascontiguousarray(phase, dtype=np.int32)
+        mats = (Material * len(materials))(*[Material(float(E), float(nu), int(law), 0)
+                                             for E, nu, law in materials])
+        h = C.c_void_p()
+        _check(lib.jetsci_mesh_create(coords.ctypes.data, coords.shape[0], conn.ctypes.data, conn.shape[0],
+                                      None if phase is None else phase.ctypes.data, mats, len(materials),
+                                      _stream(stream), C.byref(h)))
+        self._h = h
+        self.n_nodes, self.n_elem = int(coords.shape[0]), int(conn.shape[0])
+        nd, nnz, rp, cp, nc = C.c_int64(), C.c_int64(), C.c_void_p(), C.c_void_p(), C.c_int32()
+        _check(lib.jetsci_mesh_info(h, C.byref(nd), C.byref(nnz), C.byref(rp), C.byref(cp), C.byref(nc)))
+        self.n_dof, self.nnz, self.n_colours = nd.value, nnz.value, nc.value
+        self._rowptr_ptr, self._col_ptr = rp.value, cp.value
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def of(cls, problem, stream=None):
+        return cls(problem.coords, problem.conn, problem.phase, problem.materials, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.jetsci_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def pattern(self, device="cuda", stream=None):
+        """Copies of the CSR pattern (rowptr int64 [n_dof+1], col int32 [nnz])."""
+        pin = device == "cpu"
+        rp = torch.empty(self.n_dof + 1, dtype=torch.int64, device=device, pin_memory=pin)
+        col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=device, pin_memory=pin)
+        _check(lib.jetsci_mesh_copy_pattern(self._h, _ptr(rp), _ptr(col), _stream(stream)))
+        return rp, col[:self.nnz]
+
+    def check(self):
+        """Reads and clears the device flag word; raises JetsciError if any bit was set."""
+        f = C.c_uint32()
+        st = lib.jetsci_mesh_check(self._h, C.byref(f))
+        if st != 0 and st != 5:
+            _check(st)
+        return f.value
+
+    # ------------------------------------------------------------------ compute calls
+    def new_vector(self):
+        return torch.empty(self.n_dof, dtype=torch.float64, device="cuda")
+
+    def new_values(self, precision=FP64):
+        return torch.empty(self.nnz, dtype=vals_dtype(precision), device="cuda")
+
+    def residual(self, u, R=None, precision=FP64, E_elem=None, stream=None):
+        _dev_f64(u, self.n_dof, "u")
+        R = self.new_vector() if R is None else _dev_f64(R, self.n_dof, "R")
+        _dev_f64(E_elem, self.n_elem, "E_elem")
+        _check(lib.jetsci_residual(self._h, _ptr(u), _ptr(R), precision, _ptr(E_elem), _stream(stream)))
+        return R
+
+    def tangent_csr(self, u, vals=None, R=None, precision=FP64, E_elem=None, stream=None):
+        _dev_f64(u, self.n_dof, "u")
+        vals = self.new_values(precision) if vals is None else vals
+        if vals.dtype != vals_dtype(precision) or vals.numel() != self.nnz or not vals.is_cuda:
+            raise ValueError("vals: wrong dtype/size/device for this precision")
+        _dev_f64(R, self.n_dof, "R")
+        _dev_f64(E_elem, self.n_elem, "E_elem")
+        _check(lib.jetsci_tangent_csr(self._h, _ptr(u), _ptr(vals), _ptr(R), precision, _ptr(E_elem),
+                                      _stream(stream)))
+        return vals
+
+    def apply_tangent(self, u, v, y=None, mode=MATRIX_FREE, vals=None, precision=FP64, E_elem=None,
+                      stream=None):
+        _dev_f64(v, self.n_dof, "v")
+        if mode == MATRIX_FREE:
+            _dev_f64(u, self.n_dof, "u")
+        y = self.new_vector() if y is None else _dev_f64(y, self.n_dof, "y")
+        if mode == CSR and (vals is None or vals.dtype != vals_dtype(precision) or vals.numel() != self.nnz):
+            raise ValueError("vals: wrong dtype/size for CSR mode")
+        _dev_f64(E_elem, self.n_elem, "E_elem")
+        _check(lib.jetsci_apply_tangent(self._h, _ptr(u), _ptr(v), _ptr(y), mode, _ptr(vals), precision,
+                                        _ptr(E_elem), _stream(stream)))
+        return y
+
+    def material_grad(self, u, R, E_elem=None, g=None, precision=FP64, stream=None):
+        _dev_f64(u, self.n_dof, "u")
+        _dev_f64(R, self.n_dof, "R")
+        _dev_f64(E_elem, self.n_elem, "E_elem")
+        g = torch.empty(self.n_elem, dtype=torch.float64, device="cuda") if g is None else g
+        _check(lib.jetsci_material_grad(self._h, _ptr(u), _ptr(E_elem), _ptr(R), _ptr(g), precision,
+                                        _stream(stream)))
+        return g
+
+    def norm2(self, x, out=None, stream=None):
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise ValueError("x: need a contiguous CUDA float64 tensor")
+        out = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
+        _check(lib.jetsci_norm2(self._h, _ptr(x), x.numel(), _ptr(out), _stream(stream)))
+        return out
+
+
+def version():
+    return lib.jetsci_version().decode()
+
+
+class MaterialGrad(torch.autograd.Function):
+    """L(E) = 1/2 ||R(u; E)||^2 with dL/dE from the library's adjoint kernel.
+
+    forward(mesh, u, E, precision) -> L (0-dim float64 CUDA tensor)."""
+
+    @staticmethod
+    def forward(ctx, E, mesh, u, precision=FP64):
+        R = mesh.residual(u, precision=precision, E_elem=E.detach().contiguous())
+        nrm = mesh.norm2(R)
+        ctx.mesh, ctx.precision = mesh, precision
+        ctx.save_for_backward(E, u, R)
+        return 0.5 * nrm[0] * nrm[0]
+
+    @staticmethod
+    def backward(ctx, gout):
+        E, u, R = ctx.saved_tensors
+        g = ctx.mesh.material_grad(u, R, E_elem=E.detach().contiguous(), precision=ctx.precision)
+        return g * gout, None, None, None

@@ -1,0 +1,54 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads, and exports every entry point
+declared in include/*.h; the product library links nothing from the oracle."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def J():
+    from paper_2604_22087_b300 import build
+    build.build()
+    from paper_2604_22087_b300 import jetsci
+    return jetsci
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:jetsci_status|const char\s*\*)\s*(jetsci_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_paper_calls():
+    names = declared_functions()
+    for n in ("jetsci_mesh_create", "jetsci_residual", "jetsci_tangent_csr", "jetsci_apply_tangent",
+              "jetsci_material_grad", "jetsci_norm2"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(J):
+    names = declared_functions()
+    assert names
+    for n in names:
+        assert hasattr(J.lib, n), n
+    assert sorted(J.EXPORTS) == names
+
+
+def test_version_and_error_string_without_gpu(J):
+    assert "sm_103a" in J.version()
+    assert isinstance(J.lib.jetsci_last_error(), bytes)
+
+
+def test_product_library_has_no_oracle_symbols(J):
+    out = subprocess.run(["nm", "-D", "--defined-only", J.LIB_PATH], capture_output=True, text=True).stdout
+    assert "or_element" not in out and "or_residual" not in out
+    syms = set(re.findall(r"\b(jetsci_\w+)\b", out))
+    assert set(declared_functions()) <= syms

@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Error metric: normwise max|x - x_ref| / max|x_ref| over the whole output (interior residual
+entries cancel to near zero, so entry-wise relative error is meaningless there).
+Tolerances: FP64 1e-12 (the target stated for the plain FP64 path).  FP32 element
+arithmetic: unit roundoff 6e-8 times the depth of the per-Gauss-point computation
+(~1e2 operations) times the cancellation between the 8 element contributions of a node
+(~10) gives ~6e-5; the tests use 2e-4 for R and K.v and 5e-5 for CSR values (no
+cross-element cancellation inside one entry beyond the 8-fold sum).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_22087_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def jetsci():
+    from paper_2604_22087_b300 import jetsci as J
+    return J
+
+
+def relerr(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(x - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def problems():
+    """(id, Problem) cases: the 16^3 two-phase sphere RVE (linear elastic), the same
+    geometry neo-Hookean, and a distorted ragged 5x7x3 neo-Hookean box."""
+    out = []
+    p = I.sphere_composite(16, seed=1, law=I.LAW_LINEAR_ELASTIC)
+    out.append(("sphere16_linear", p))
+    q = I.sphere_composite(16, seed=1, law=I.LAW_NEO_HOOKEAN)
+    q.u = I.uniform_field(q.coords.size, 1e-3, 11) + np.repeat(q.coords[:, :1] * 0.01, 3, 1).ravel() * \
+        np.tile([1.0, 0.0, 0.0], q.n_nodes)
+    out.append(("sphere16_neohookean_stretch", q))
+    coords, conn = I.box_mesh(5, 7, 3, distort=0.25, seed=3)
+    g = np.random.default_rng(3)
+    phase = (g.uniform(size=len(conn)) < 0.4).astype(np.int32)
+    r = I.Problem("ragged_5x7x3_neohookean", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                  g.uniform(-3e-3, 3e-3, coords.size), g.uniform(-1, 1, coords.size))
+    out.append(("ragged_neohookean", r))
+    return out
+
+
+PROBLEMS = problems()
+
+
+@pytest.fixture(scope="module", params=[p[0] for p in PROBLEMS])
+def case(request):
+    prob = dict(PROBLEMS)[request.param]
+    J = jetsci()
+    mesh = J.Mesh.of(prob)
+    om = oracle.Mesh.of(prob)
+    rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
+    ref = dict(R=R_ref, vals=vals_ref, rowptr=rp, col=col, y_mf=oracle.apply_tangent(om, prob.u, prob.v),
+               y_csr=oracle.spmv(rp, col, vals_ref, prob.v))
+    yield prob, mesh, om, ref
+    mesh.close()
+
+
+def test_pattern_matches_oracle_exactly(case):
+    prob, mesh, _, ref = case
+    rp, col = mesh.pattern()
+    assert mesh.nnz == len(ref["col"])
+    assert np.array_equal(rp.cpu().numpy(), ref["rowptr"])
+    assert np.array_equal(col.cpu().numpy(), ref["col"])
+
+
+def test_residual_fp64(case):
+    prob, mesh, _, ref = case
+    R = mesh.residual(cuda(prob.u))
+    assert relerr(R.cpu().numpy(), ref["R"]) <= FP64_TOL
+    assert mesh.check() == 0
+
+
+def test_tangent_csr_fp64_with_residual(case):
+    prob, mesh, _, ref = case
+    R = mesh.new_vector()
+    vals = mesh.tangent_csr(cuda(prob.u), R=R)
+    assert relerr(vals.cpu().numpy(), ref["vals"]) <= FP64_TOL
+    assert relerr(R.cpu().numpy(), ref["R"]) <= FP64_TOL
+
+
+def test_apply_tangent_matrix_free_fp64(case):
+    prob, mesh, _, ref = case
+    y = mesh.apply_tangent(cuda(prob.u), cuda(prob.v))
+    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= FP64_TOL
+
+
+def test_apply_tangent_csr_fp64(case):
+    prob, mesh, _, ref = case
+    vals = mesh.tangent_csr(cuda(prob.u))
+    y = mesh.apply_tangent(None, cuda(prob.v), mode=jetsci().CSR, vals=vals)
+    assert relerr(y.cpu().numpy(), ref["y_csr"]) <= FP64_TOL
+
+
+def test_norm2_fp64(case):
+    prob, mesh, _, ref = case
+    n = mesh.norm2(cuda(ref["R"])).item()
+    assert abs(n - oracle.norm2(ref["R"])) <= 1e-14 * oracle.norm2(ref["R"])
+
+
+def test_fp32_bounds(case):
+    prob, mesh, _, ref = case
+    J = jetsci()
+    u = cuda(prob.u)
+    R = mesh.residual(u, precision=J.FP32)
+    assert relerr(R.cpu().numpy(), ref["R"]) <= 2e-4
+    R2 = mesh.new_vector()
+    vals = mesh.tangent_csr(u, R=R2, precision=J.FP32)
+    assert vals.dtype == torch.float32
+    assert relerr(vals.cpu().numpy(), ref["vals"]) <= 5e-5
+    assert relerr(R2.cpu().numpy(), ref["R"]) <= 2e-4
+    y = mesh.apply_tangent(u, cuda(prob.v), precision=J.FP32)
+    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= 2e-4
+    yc = mesh.apply_tangent(None, cuda(prob.v), mode=J.CSR, vals=vals, precision=J.FP32)
+    assert relerr(yc.cpu().numpy(), ref["y_csr"]) <= 2e-4
+
+
+def test_bitwise_determinism(case):
+    prob, mesh, _, _ = case
+    u, v = cuda(prob.u), cuda(prob.v)
+    a = [mesh.tangent_csr(u), mesh.residual(u), mesh.apply_tangent(u, v)]
+    b = [mesh.tangent_csr(u), mesh.residual(u), mesh.apply_tangent(u, v)]
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_material_gradient_fp64():
+    prob = I.lognormal_problem(12, seed=4)
+    J = jetsci()
+    mesh = J.Mesh.of(prob)
+    om = oracle.Mesh.of(prob)
+    u, E = cuda(prob.u), cuda(prob.E_elem)
+    R = mesh.residual(u, E_elem=E)
+    R_ref = oracle.residual(om, prob.u)
+    assert relerr(R.cpu().numpy(), R_ref) <= FP64_TOL
+    g = mesh.material_grad(u, R, E_elem=E)
+    g_ref = oracle.material_grad(om, prob.u, R_ref)
+    assert relerr(g.cpu().numpy(), g_ref) <= FP64_TOL
+    # through torch.autograd
+    Et = E.clone().requires_grad_(True)
+    L = J.MaterialGrad.apply(Et, mesh, u)
+    L.backward()
+    assert relerr(Et.grad.cpu().numpy(), g_ref) <= FP64_TOL
+    assert abs(L.item() - 0.5 * oracle.norm2(R_ref) ** 2) <= 1e-13 * L.item()
+
+
+def test_empty_mesh():
+    J = jetsci()
+    coords = np.zeros((4, 3))
+    mesh = J.Mesh(coords, np.zeros((0, 8), np.int32), None, [(1e9, 0.3, 0)])
+    assert mesh.nnz == 0 and mesh.n_dof == 12
+    u = torch.ones(12, dtype=torch.float64, device="cuda")
+    R = torch.full((12,), 7.0, dtype=torch.float64, device="cuda")
+    mesh.residual(u, R=R)
+    assert torch.count_nonzero(R).item() == 0
+    y = mesh.apply_tangent(u, u.clone())
+    assert torch.count_nonzero(y).item() == 0
+    assert mesh.norm2(u).item() == pytest.approx(np.sqrt(12.0), rel=1e-15)
+
+
+def test_host_argument_errors():
+    J = jetsci()
+    coords, conn = I.box_mesh(2)
+    with pytest.raises(J.JetsciError) as ei:
+        J.Mesh(coords, conn + 100, None, [(1e9, 0.3, 0)])
+    assert ei.value.status == 4
+    with pytest.raises(J.JetsciError) as ei:
+        J.Mesh(coords, conn, None, [(1e9, 0.7, 0)])
+    assert ei.value.status == 1
+    bad = conn.copy(); bad[0, 1] = bad[0, 0]
+    with pytest.raises(J.JetsciError):
+        J.Mesh(coords, bad, None, [(1e9, 0.3, 0)])
+    mesh = J.Mesh(coords, conn, None, [(1e9, 0.3, 0)])
+    u = torch.zeros(mesh.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(J.JetsciError):
+        J._check(J.lib.jetsci_residual(mesh.handle, J._ptr(u), J._ptr(u), 99, None, J._stream()))
+    with pytest.raises(J.JetsciError):
+        J._check(J.lib.jetsci_apply_tangent(mesh.handle, J._ptr(u), J._ptr(u), J._ptr(u), 0, None, 0, None,
+                                            J._stream()))
+
+
+def test_inverted_element_sets_flag_not_fault():
+    """An inverted element is reported through the flag word; the kernel completes."""
+    J = jetsci()
+    coords, conn = I.box_mesh(2)
+    conn = conn.copy()
+    conn[0, [0, 1]] = conn[0, [1, 0]]
+    mesh = J.Mesh(coords, conn, None, [(1e9, 0.3, 0)])
+    u = torch.zeros(mesh.n_dof, dtype=torch.float64, device="cuda")
+    mesh.residual(u)
+    assert mesh.check() & J.FLAG_BAD_ELEMENT
+    assert mesh.check() == 0  # cleared
+
+
+def test_full_size_fibre_rve_sampled_rows():
+    """128^3 fibre RVE, neo-Hookean, 1% stretch: sampled rows of R, K and K.v (FP64)
+    against the oracle computed element by element, in the bench's launch configuration."""
+    prob = I.fibre_composite(128, seed=2)
+    J = jetsci()
+    mesh = J.Mesh.of(prob)
+    u, v = cuda(prob.u), cuda(prob.v)
+    R = mesh.new_vector()
+    vals = mesh.tangent_csr(u, R=R)
+    y = mesh.apply_tangent(u, v)
+    ycsr = mesh.apply_tangent(None, v, mode=J.CSR, vals=vals)
+    rp, col = mesh.pattern()
+    rp, col, vals_h = rp.cpu().numpy(), col.cpu().numpy(), vals.cpu().numpy()
+    R_h, y_h, yc_h = R.cpu().numpy(), y.cpu().numpy(), ycsr.cpu().numpy()
+    om = oracle.Mesh.of(prob)
+    g = np.random.default_rng(0)
+    nodes = np.concatenate([[0, prob.n_nodes - 1], g.choice(prob.n_nodes, 40, replace=False)])
+    rows = oracle.sampled_rows(om, prob.u, prob.v, nodes)
+    scale_R = max(np.max(np.abs(rows[n][0])) for n in nodes)
+    scale_y = max(np.max(np.abs(rows[n][1])) for n in nodes)
+    for n in nodes:
+        Rn, Kvn, krow = rows[n]
+        assert np.max(np.abs(R_h[3 * n:3 * n + 3] - Rn)) <= FP64_TOL * scale_R
+        assert np.max(np.abs(y_h[3 * n:3 * n + 3] - Kvn)) <= FP64_TOL * scale_y
+        assert np.max(np.abs(yc_h[3 * n:3 * n + 3] - Kvn)) <= FP64_TOL * scale_y
+        for i in range(3):
+            r = 3 * n + i
+            cs = col[rp[r]:rp[r + 1]]
+            assert sorted(krow) == list(cs)
+            kref = np.array([krow[c][i] for c in cs])
+            assert np.max(np.abs(vals_h[rp[r]:rp[r + 1]] - kref)) <= FP64_TOL * np.max(np.abs(kref))
+    assert mesh.check() == 0
+    mesh.close()
