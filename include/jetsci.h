@@ -186,6 +186,24 @@ jetsci_status jetsci_material_grad(jetsci_mesh mesh, const double *u_dev,
 jetsci_status jetsci_norm2(jetsci_mesh mesh, const double *x_dev, int64_t n, double *out_dev,
                            void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free ||x||_2 (no counterpart in the paper; a service for callers that
+ * cannot allocate device memory when they need the norm -- their device memory is
+ * reserved up front by another runtime's pool, or a cudaMalloc and its implicit device
+ * synchronisation is not acceptable in their loop -- and that may hold no mesh).
+ * Same arithmetic and fixed reduction shape as jetsci_norm2, so the results are
+ * bitwise equal.  Scratch: a fixed file-scope device array of 4096 doubles (32 KiB) that
+ * every GPU which loads the library holds until the process exits; the call allocates
+ * nothing and frees nothing.  n is limited to 4096 * 8192 = 33,554,432 entries; larger
+ * n returns JETSCI_ERR_ARG with a message.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current, so make that
+ * first call before any stream capture.  All calls on one device share the array: calls
+ * that overlap on the GPU (e.g. on two streams at once) race; the array keeps the last
+ * call's partial sums, which the next call overwrites before reading.
+ * x_dev [n] FP64 device, out_dev[0] FP64 device.
+ */
+jetsci_status jetsci_norm2_static(const double *x_dev, int64_t n, double *out_dev, void *stream);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *jetsci_last_error(void);
 

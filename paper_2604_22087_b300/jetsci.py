@@ -29,7 +29,7 @@ EXPORTS = [
     "jetsci_mesh_create", "jetsci_mesh_destroy", "jetsci_mesh_info", "jetsci_mesh_check",
     "jetsci_mesh_copy_pattern",
     "jetsci_residual", "jetsci_tangent_csr", "jetsci_apply_tangent", "jetsci_material_grad",
-    "jetsci_norm2", "jetsci_last_error", "jetsci_version",
+    "jetsci_norm2", "jetsci_norm2_static", "jetsci_last_error", "jetsci_version",
 ]
 
 
@@ -63,6 +63,7 @@ def _load():
         "jetsci_apply_tangent": [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp],
         "jetsci_material_grad": [_vp, _vp, _vp, _vp, _vp, i32, _vp],
         "jetsci_norm2": [_vp, _vp, i64, _vp, _vp],
+        "jetsci_norm2_static": [_vp, i64, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
