@@ -187,6 +187,74 @@ jetsci_status jetsci_norm2(jetsci_mesh mesh, const double *x_dev, int64_t n, dou
                            void *stream);
 
 /* ---------------------------------------------------------------------------
+ * MLP constitutive surrogate (the paper notes that a surrogate model can replace the
+ * explicit material function and that its Jacobian is extracted the same way,
+ * Section III-B).  Network: x = [E_voigt / in_scale (6), one-hot phase (2)] ->
+ * 3 x (Linear 64 + SiLU) -> Linear 6 -> y; S_c = y_c * out_scale[phase][c] +
+ * out_shift[phase][c] (second Piola-Kirchhoff stress, Voigt [11,22,33,23,13,12], tensor
+ * shear); the tangent dS/dE (w.r.t. the tensor components of the Green-Lagrange strain E)
+ * is the network's input-Jacobian.  All GEMMs run on tensor cores in BF16 with FP32
+ * accumulation; master weights and Adam state are FP32.  Two phases (0, 1) are supported.
+ *
+ * Parameter vector (FP64 on the host, FP32 on the device), 9286 entries in this order:
+ * W1 [64][8], b1 [64], W2 [64][64], b2 [64], W3 [64][64], b3 [64], W4 [6][64], b4 [6]
+ * (W[out][in]).
+ */
+typedef struct {
+    double in_scale;         /* strain scale of the inputs (> 0)                          */
+    double range;            /* fallback to the plain law if any |E_ij| > range (> 0)     */
+    double out_scale[2][6];  /* per phase and component, non-zero                         */
+    double out_shift[2][6];
+} jetsci_surrogate_config;
+
+#define JETSCI_MLP_PARAMS 9286
+
+/* Creates a surrogate on the current device from params_host [9286] (copied).  Synchronises. */
+jetsci_status jetsci_surrogate_create(const double *params_host, const jetsci_surrogate_config *cfg,
+                                      void *stream, jetsci_surrogate *out);
+jetsci_status jetsci_surrogate_destroy(jetsci_surrogate s);
+/* Copies the current FP32 master weights into params_host [9286] (as double).  Synchronises. */
+jetsci_status jetsci_surrogate_get_params(jetsci_surrogate s, double *params_host);
+
+/* Training labels from the plain compressible neo-Hookean update, in FP64 on the device:
+ * S6_dev [n][6] = S(E) for E6_dev [n][6] (Voigt, tensor shear) and phase_dev [n] in {0,1},
+ * with the Lame constants of mats[phase] (n_mats 1 or 2).  A phase out of range or
+ * det(I + 2E) <= 0 sets bits 2 / 4 in *err_flag_dev (device uint32, caller-owned). */
+jetsci_status jetsci_surrogate_label(const jetsci_material *mats, int32_t n_mats, const double *E6_dev,
+                                     const int32_t *phase_dev, int64_t n, double *S6_dev,
+                                     uint32_t *err_flag_dev, void *stream);
+
+/* n_steps Adam steps on minibatches of `batch` samples (a positive multiple of 128, at most
+ * 131072): step k uses samples order_dev[k*batch .. (k+1)*batch) of the training set
+ * (E6_dev [n_samples][6], phase_dev [n_samples], S6_dev [n_samples][6] labels).  Loss =
+ * mean squared error of the normalised outputs.  Learning rate follows a cosine from lr_max
+ * to lr_min over the call's steps; Adam (0.9, 0.999, 1e-8) with bias correction continues
+ * across calls.  loss_dev [n_steps] (FP32, device) or NULL.  Gradients are summed over
+ * 128-sample tiles in a fixed order (deterministic).  Synchronises (reads the error word). */
+jetsci_status jetsci_surrogate_train(jetsci_surrogate s, const double *E6_dev, const int32_t *phase_dev,
+                                     const double *S6_dev, int64_t n_samples, const int32_t *order_dev,
+                                     int64_t order_len, int64_t n_steps, int32_t batch, double lr_max,
+                                     double lr_min, float *loss_dev, void *stream);
+
+/* Gradient of the loss of one minibatch (samples order_dev[0..batch)) with respect to the
+ * parameter vector, into grad_dev [9286] (FP32), and the loss into loss_dev[0]; weights
+ * unchanged.  Synchronises. */
+jetsci_status jetsci_surrogate_gradient(jetsci_surrogate s, const double *E6_dev, const int32_t *phase_dev,
+                                        const double *S6_dev, int64_t n_samples, const int32_t *order_dev,
+                                        int32_t batch, float *grad_dev, float *loss_dev, void *stream);
+
+/* Network stress S6_dev [n][6] and, if D36_dev != NULL, tangent D36_dev [n][6][6]
+ * (D[c][d] = dS_c / dE_d) at E6_dev [n][6], phase_dev [n].  Synchronises. */
+jetsci_status jetsci_surrogate_eval(jetsci_surrogate s, const double *E6_dev, const int32_t *phase_dev,
+                                    int64_t n, double *S6_dev, double *D36_dev, void *stream);
+
+/* Attaches (or with NULL detaches) a surrogate to a mesh; residual and tangent calls with
+ * precision JETSCI_SURROGATE then take S and dS/dE from it at every Gauss point whose
+ * strain is within range, and from the phase's plain law elsewhere.  The mesh does not
+ * own the surrogate; keep it alive while attached. */
+jetsci_status jetsci_mesh_set_surrogate(jetsci_mesh mesh, jetsci_surrogate s);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free ||x||_2 (no counterpart in the paper; a service for callers that
  * cannot allocate device memory when they need the norm -- their device memory is
  * reserved up front by another runtime's pool, or a cudaMalloc and its implicit device

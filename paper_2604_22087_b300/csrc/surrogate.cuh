@@ -1,0 +1,161 @@
+// MLP constitutive surrogate: parameter layout, BF16 operand images and the tensor-core
+// forward / input-Jacobian pass shared by the standalone evaluation kernel and the fused
+// element kernels.
+//
+// Network (a reading of the paper's remark that a surrogate model can replace the explicit
+// material function, Section III-B): x = [E_voigt / in_scale (6), one-hot phase (2)] ->
+// 3 x (Linear 64 + SiLU) -> Linear 6 -> normalised S; S_c = y_c * out_scale[p][c] +
+// out_shift[p][c].  The tangent dS/dE is the input-Jacobian, propagated forward through the
+// layers as 6 tangent vectors per point: T1 = silu'(z1) (.) W1[:, :6], T_l = silu'(z_l) (.)
+// (W_l T_{l-1}), J = W4 T3.  For a tile of 128 points every hidden layer is one GEMM for the
+// activations plus six for the tangents (M = 128, N = 64, K = 64, BF16 in, FP32 accumulate in
+// TMEM).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "tc.cuh"
+
+namespace jetsci {
+
+constexpr int kMlpIn = 8, kMlpH = 64, kMlpOut = 6;
+// FP32 parameter vector: W1[64][8], b1[64], W2[64][64], b2, W3[64][64], b3, W4[6][64], b4[6].
+constexpr int kOffW1 = 0, kOffB1 = 512, kOffW2 = 576, kOffB2 = 4672, kOffW3 = 4736, kOffB3 = 8832,
+              kOffW4 = 8896, kOffB4 = 9280, kNumParams = 9286;
+// BF16 operand image (bytes), K-major core-matrix tiles: W1p [64 n][16 k] (k >= 8 zero),
+// W2, W3 [64][64], W4p [16 n][64 k] (n >= 6 zero), W4Tp [64 n][16 k] (k >= 6 zero),
+// W3T, W2T [64][64] (transposes for the backward pass).
+constexpr int kImgW1 = 0, kImgW2 = 2048, kImgW3 = 10240, kImgW4 = 18432, kImgW4T = 20480, kImgW3T = 22528,
+              kImgW2T = 30720, kImgBytes = 38912, kImgFwdBytes = 20480;
+
+struct SurrogateConfig {
+    float in_scale;
+    float range;
+    float out_scale[2][6];
+    float out_shift[2][6];
+};
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_prime_f(float z) {
+    float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// Shared-memory workspace of one 128-point tile for the forward + input-Jacobian pass.
+struct __align__(128) MlpTileSmem {
+    unsigned char w[kImgFwdBytes];       // W1p, W2, W3, W4p
+    unsigned char x[128 * 16 * 2];       // inputs [128][16]
+    unsigned char act[128 * 64 * 2];     // activations [128][64]
+    unsigned char tan[6][128 * 64 * 2];  // tangent rows per input direction [128][64]
+    float b[3][64];
+    float b4[8];
+    float w1[64][8];                     // FP32 W1 (tangent seeds)
+    uint64_t mbar;
+    uint32_t tmem_base;
+};
+
+// Cooperative load of the forward weights into shared memory (all 128 threads).
+__device__ __forceinline__ void mlp_load_weights(MlpTileSmem &sm, const unsigned char *__restrict__ img,
+                                                 const float *__restrict__ params) {
+    const int t = threadIdx.x;
+    const uint4 *src = reinterpret_cast<const uint4 *>(img);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm.w);
+    for (int i = t; i < kImgFwdBytes / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = t; i < 64; i += blockDim.x) {
+        sm.b[0][i] = params[kOffB1 + i];
+        sm.b[1][i] = params[kOffB2 + i];
+        sm.b[2][i] = params[kOffB3 + i];
+    }
+    for (int i = t; i < 8; i += blockDim.x) sm.b4[i] = i < 6 ? params[kOffB4 + i] : 0.0f;
+    for (int i = t; i < 512; i += blockDim.x) sm.w1[i >> 3][i & 7] = params[kOffW1 + i];
+}
+
+// Commits the MMAs issued by thread 0 and waits (all threads) with a bound.  `phase` is a
+// per-thread copy of the mbarrier's completed-phase count, advanced in lockstep by every
+// thread.  Returns false on timeout.
+__device__ __forceinline__ bool mma_sync_bounded(uint64_t *mbar, uint32_t &phase) {
+    if (threadIdx.x == 0) tc::mma_commit(mbar);
+    bool ok = tc::mbar_wait_bounded(mbar, phase & 1);
+    phase++;
+    tc::fence_after_sync();
+    return ok;
+}
+
+// Runs the forward and input-Jacobian pass for the tile whose inputs are already in sm.x
+// (row t = point t).  On return thread t holds y[6] (normalised outputs) and Jm[6][6]
+// (dy/dx, column d = input direction d).  Returns false if a tensor-core wait timed out.
+__device__ bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, float y[6], float Jm[6][6]) {
+    const int t = threadIdx.x;
+    const uint32_t tm = sm.tmem_base;
+    bool ok = true;
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // layer 1: z1 = x W1^T (K = 16, zero-padded)
+    if (t == 0) tc::gemm_bf16_128xN(tm, sm.x, sm.w + kImgW1, 64, 16);
+    ok = mma_sync_bounded(&sm.mbar, phase) && ok;
+    for (int layer = 0; layer < 3; layer++) {
+        // epilogue of layer `layer`: activation and tangent rows
+        float s[64];
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float z[16];
+            tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                float zz = z[j] + sm.b[layer][c0 + j];
+                s[c0 + j] = silu_prime_f(zz);
+                tc::st_bf16(sm.act, t, c0 + j, 64, silu_f(zz));
+            }
+        }
+        if (layer == 0) {
+#pragma unroll
+            for (int d = 0; d < 6; d++)
+#pragma unroll 8
+                for (int j = 0; j < 64; j++) tc::st_bf16(sm.tan[d], t, j, 64, s[j] * sm.w1[j][d]);
+        } else {
+#pragma unroll
+            for (int d = 0; d < 6; d++) {
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float uu[16];
+                    tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (d + 1) + c0), uu);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) tc::st_bf16(sm.tan[d], t, c0 + j, 64, s[c0 + j] * uu[j]);
+                }
+            }
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+            if (layer < 2) {
+                const unsigned char *W = sm.w + (layer == 0 ? kImgW2 : kImgW3);
+                tc::gemm_bf16_128xN(tm, sm.act, W, 64, 64);
+                for (int d = 0; d < 6; d++) tc::gemm_bf16_128xN(tm + 64 * (d + 1), sm.tan[d], W, 64, 64);
+            } else {
+                tc::gemm_bf16_128xN(tm, sm.act, sm.w + kImgW4, 16, 64);
+                for (int d = 0; d < 6; d++) tc::gemm_bf16_128xN(tm + 64 * (d + 1), sm.tan[d], sm.w + kImgW4, 16, 64);
+            }
+        }
+        ok = mma_sync_bounded(&sm.mbar, phase) && ok;
+    }
+    {
+        float v[16];
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 0), v);
+#pragma unroll
+        for (int c = 0; c < 6; c++) y[c] = v[c] + sm.b4[c];
+#pragma unroll
+        for (int d = 0; d < 6; d++) {
+            tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (d + 1)), v);
+#pragma unroll
+            for (int c = 0; c < 6; c++) Jm[c][d] = v[c];
+        }
+    }
+    return ok;
+}
+
+}  // namespace jetsci

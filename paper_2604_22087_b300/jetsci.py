@@ -237,3 +237,152 @@ class MaterialGrad(torch.autograd.Function):
         E, u, R = ctx.saved_tensors
         g = ctx.mesh.material_grad(u, R, E_elem=E.detach().contiguous(), precision=ctx.precision)
         return g * gout, None, None, None
+
+
+# ---------------------------------------------------------------------- MLP surrogate
+MLP_PARAMS = 9286
+
+
+class SurrogateConfig(C.Structure):
+    _fields_ = [("in_scale", C.c_double), ("range", C.c_double), ("out_scale", C.c_double * 12),
+                ("out_shift", C.c_double * 12)]
+
+
+def _load_surrogate(lib):
+    i64, i32 = C.c_int64, C.c_int32
+    sig = {
+        "jetsci_surrogate_create": [_vp, C.POINTER(SurrogateConfig), _vp, C.POINTER(_vp)],
+        "jetsci_surrogate_destroy": [_vp],
+        "jetsci_surrogate_get_params": [_vp, _vp],
+        "jetsci_surrogate_label": [C.POINTER(Material), i32, _vp, _vp, i64, _vp, _vp, _vp],
+        "jetsci_surrogate_train": [_vp, _vp, _vp, _vp, i64, _vp, i64, i64, i32, C.c_double, C.c_double, _vp, _vp],
+        "jetsci_surrogate_gradient": [_vp, _vp, _vp, _vp, i64, _vp, i32, _vp, _vp, _vp],
+        "jetsci_surrogate_eval": [_vp, _vp, _vp, i64, _vp, _vp, _vp],
+        "jetsci_mesh_set_surrogate": [_vp, _vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+
+
+_load_surrogate(lib)
+EXPORTS += ["jetsci_surrogate_create", "jetsci_surrogate_destroy", "jetsci_surrogate_get_params",
+            "jetsci_surrogate_label", "jetsci_surrogate_train", "jetsci_surrogate_gradient",
+            "jetsci_surrogate_eval", "jetsci_mesh_set_surrogate"]
+
+
+def pack_layers(layers):
+    """[(W [out,in], b [out])] * 4 -> flat FP64 parameter vector in the library's order."""
+    parts = []
+    for W, b in layers:
+        parts += [np.asarray(W, dtype=np.float64).ravel(), np.asarray(b, dtype=np.float64).ravel()]
+    p = np.concatenate(parts)
+    if p.size != MLP_PARAMS:
+        raise ValueError(f"expected {MLP_PARAMS} parameters, got {p.size}")
+    return p
+
+
+def unpack_layers(p):
+    p = np.asarray(p, dtype=np.float64)
+    shapes = [(64, 8), (64, 64), (64, 64), (6, 64)]
+    out, o = [], 0
+    for r, c in shapes:
+        W = p[o:o + r * c].reshape(r, c)
+        o += r * c
+        b = p[o:o + r]
+        o += r
+        out.append((W.copy(), b.copy()))
+    return out
+
+
+def _dev(t, dtype, n, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() == n):
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor of {n} entries")
+    return t
+
+
+class Surrogate:
+    """The MLP surrogate on the current CUDA device (wraps jetsci_surrogate)."""
+
+    def __init__(self, layers, in_scale, range_, out_scale, out_shift, stream=None):
+        cfg = SurrogateConfig()
+        cfg.in_scale, cfg.range = float(in_scale), float(range_)
+        cfg.out_scale[:] = [float(v) for v in np.asarray(out_scale, dtype=np.float64).ravel()]
+        cfg.out_shift[:] = [float(v) for v in np.asarray(out_shift, dtype=np.float64).ravel()]
+        self.cfg = cfg
+        p = np.ascontiguousarray(pack_layers(layers) if isinstance(layers, (list, tuple)) else layers,
+                                 dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib.jetsci_surrogate_create(p.ctypes.data, C.byref(cfg), _stream(stream), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.jetsci_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self):
+        p = np.zeros(MLP_PARAMS)
+        _check(lib.jetsci_surrogate_get_params(self._h, p.ctypes.data))
+        return p
+
+    def layers(self):
+        return unpack_layers(self.params())
+
+    @staticmethod
+    def label(materials, E6, phase, stream=None):
+        n = phase.numel()
+        _dev(E6, torch.float64, 6 * n, "E6")
+        _dev(phase, torch.int32, n, "phase")
+        mats = (Material * len(materials))(*[Material(float(E), float(nu), int(law), 0) for E, nu, law in materials])
+        S6 = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        _check(lib.jetsci_surrogate_label(mats, len(materials), _ptr(E6), _ptr(phase), n, _ptr(S6), _ptr(err),
+                                          _stream(stream)))
+        if int(err.item()) != 0:
+            raise JetsciError(5, f"label error flags {int(err.item())}")
+        return S6
+
+    def train(self, E6, phase, S6, order, n_steps, batch=4096, lr_max=1e-3, lr_min=1e-5, stream=None):
+        n = phase.numel()
+        _dev(E6, torch.float64, 6 * n, "E6")
+        _dev(S6, torch.float64, 6 * n, "S6")
+        _dev(phase, torch.int32, n, "phase")
+        _dev(order, torch.int32, order.numel(), "order")
+        loss = torch.empty(max(n_steps, 1), dtype=torch.float32, device="cuda")
+        _check(lib.jetsci_surrogate_train(self._h, _ptr(E6), _ptr(phase), _ptr(S6), n, _ptr(order), order.numel(),
+                                          n_steps, batch, lr_max, lr_min, _ptr(loss), _stream(stream)))
+        return loss[:n_steps]
+
+    def gradient(self, E6, phase, S6, order, batch, stream=None):
+        n = phase.numel()
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(lib.jetsci_surrogate_gradient(self._h, _ptr(E6), _ptr(phase), _ptr(S6), n, _ptr(order), batch,
+                                             _ptr(grad), _ptr(loss), _stream(stream)))
+        return grad, loss
+
+    def eval(self, E6, phase, tangent=True, stream=None):
+        n = phase.numel()
+        _dev(E6, torch.float64, 6 * n, "E6")
+        _dev(phase, torch.int32, n, "phase")
+        S6 = torch.empty(n, 6, dtype=torch.float64, device="cuda")
+        D = torch.empty(n, 6, 6, dtype=torch.float64, device="cuda") if tangent else None
+        _check(lib.jetsci_surrogate_eval(self._h, _ptr(E6), _ptr(phase), n, _ptr(S6), _ptr(D), _stream(stream)))
+        return (S6, D) if tangent else S6
+
+
+def attach_surrogate(mesh, surrogate):
+    _check(lib.jetsci_mesh_set_surrogate(mesh.handle, None if surrogate is None else surrogate.handle))
+    mesh._surrogate = surrogate  # keep it alive while attached
