@@ -254,6 +254,10 @@ jetsci_status jetsci_surrogate_eval(jetsci_surrogate s, const double *E6_dev, co
  * own the surrogate; keep it alive while attached. */
 jetsci_status jetsci_mesh_set_surrogate(jetsci_mesh mesh, jetsci_surrogate s);
 
+/* Number of Gauss points that fell back to the plain law (strain out of the surrogate's
+ * range) in the mesh's last JETSCI_SURROGATE residual/tangent call.  Synchronises. */
+jetsci_status jetsci_mesh_surrogate_fallbacks(jetsci_mesh mesh, uint32_t *count_host);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free ||x||_2 (no counterpart in the paper; a service for callers that
  * cannot allocate device memory when they need the norm -- their device memory is

@@ -319,6 +319,8 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
         residual_colours<double>(m, A, u, R, s);
     else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
         residual_colours<float>(m, A, u, R, s);
+    else if (precision == JETSCI_SURROGATE)
+        return launch_surrogate(m, u, nullptr, R, s);
     else
         return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the residual");
     JETSCI_CUDA_TRY(cudaGetLastError());
@@ -354,6 +356,7 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
         return tangent_colours<float, float>(m, A, u, (float *)vals, R, s);
     }
+    if (precision == JETSCI_SURROGATE) return launch_surrogate(m, u, (float *)vals, R, s);
     return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the tangent");
 }
 

@@ -46,6 +46,7 @@ struct jetsci_mesh_s {
     jetsci::Material *d_mats = nullptr; // [kMaxPhases]
     double *d_norm_partials = nullptr;  // [kNormMaxPartials]
     uint32_t *d_flags = nullptr;        // [1]
+    uint32_t *d_fallback = nullptr;     // [1] Gauss points that used the plain law in the last surrogate call
     cudaStream_t last_stream = nullptr;
     jetsci_surrogate surrogate = nullptr;
 };
@@ -78,6 +79,7 @@ jetsci_status launch_spmv(jetsci_mesh m, const void *vals, bool fp32, const doub
                           double *y, cudaStream_t s);
 jetsci_status launch_norm2(const double *x, int64_t n, double *partials, int64_t cap,
                            double *out, cudaStream_t s);
+jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, double *R, cudaStream_t s);
 jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
                                    const double *R, double *g, int precision, cudaStream_t s);
 

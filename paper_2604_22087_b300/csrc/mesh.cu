@@ -100,6 +100,7 @@ static void free_mesh(jetsci_mesh m) {
     cudaFree(m->d_mats);
     cudaFree(m->d_norm_partials);
     cudaFree(m->d_flags);
+    cudaFree(m->d_fallback);
     delete m;
 }
 
@@ -236,6 +237,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     if ((st = dev_alloc(&m->d_mats, kMaxPhases))) return st;
     if ((st = dev_alloc(&m->d_norm_partials, kNormMaxPartials))) return st;
     if ((st = dev_alloc(&m->d_flags, 1))) return st;
+    if ((st = dev_alloc(&m->d_fallback, 1))) return st;
     int64_t *d_nbr_ptr = nullptr;
     int32_t *d_nbr = nullptr;
     if ((st = dev_alloc(&d_nbr_ptr, n_nodes + 1))) return st;
@@ -264,6 +266,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
 #undef UP
     {
         cudaError_t e = cudaMemsetAsync(m->d_flags, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->d_fallback, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) { cleanup_tmp(); return cuda_fail(e, "memset flags"); }
     }
     if (n_nodes > 0) {
@@ -364,6 +367,16 @@ extern "C" jetsci_status jetsci_mesh_check(jetsci_mesh m, uint32_t *flags_host) 
     JETSCI_CUDA_TRY(cudaMemset(m->d_flags, 0, sizeof(uint32_t)));
     *flags_host = f;
     if (f) return fail(JETSCI_ERR_NONFINITE, "kernel flags 0x" + std::to_string(f));
+    return JETSCI_OK;
+}
+
+extern "C" jetsci_status jetsci_mesh_surrogate_fallbacks(jetsci_mesh m, uint32_t *count_host) {
+    cudaStream_t s;
+    jetsci_status st = enter(m, m ? (void *)m->last_stream : nullptr, &s);
+    if (st) return st;
+    if (!count_host) return fail(JETSCI_ERR_ARG, "count_host is NULL");
+    JETSCI_CUDA_TRY(cudaStreamSynchronize(s));
+    JETSCI_CUDA_TRY(cudaMemcpy(count_host, m->d_fallback, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     return JETSCI_OK;
 }
 

@@ -26,6 +26,9 @@ struct jetsci_surrogate_s {
 namespace jetsci {
 
 jetsci_surrogate mesh_surrogate(jetsci_mesh m) { return m->surrogate; }
+const unsigned char *surrogate_image(jetsci_surrogate s) { return s->d_img; }
+const float *surrogate_params(jetsci_surrogate s) { return s->d_params; }
+SurrogateConfig surrogate_config(jetsci_surrogate s) { return s->cfg; }
 
 // ------------------------------------------------------------------ weight image
 __global__ void k_pack_weights(const float *__restrict__ p, unsigned char *__restrict__ img) {

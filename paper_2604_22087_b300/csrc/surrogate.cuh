@@ -85,7 +85,7 @@ __device__ __forceinline__ bool mma_sync_bounded(uint64_t *mbar, uint32_t &phase
 // Runs the forward and input-Jacobian pass for the tile whose inputs are already in sm.x
 // (row t = point t).  On return thread t holds y[6] (normalised outputs) and Jm[6][6]
 // (dy/dx, column d = input direction d).  Returns false if a tensor-core wait timed out.
-__device__ bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, float y[6], float Jm[6][6]) {
+__device__ inline bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, float y[6], float Jm[6][6]) {
     const int t = threadIdx.x;
     const uint32_t tm = sm.tmem_base;
     bool ok = true;

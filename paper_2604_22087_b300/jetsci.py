@@ -259,6 +259,7 @@ def _load_surrogate(lib):
         "jetsci_surrogate_gradient": [_vp, _vp, _vp, _vp, i64, _vp, i32, _vp, _vp, _vp],
         "jetsci_surrogate_eval": [_vp, _vp, _vp, i64, _vp, _vp, _vp],
         "jetsci_mesh_set_surrogate": [_vp, _vp],
+        "jetsci_mesh_surrogate_fallbacks": [_vp, C.POINTER(C.c_uint32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -269,7 +270,7 @@ def _load_surrogate(lib):
 _load_surrogate(lib)
 EXPORTS += ["jetsci_surrogate_create", "jetsci_surrogate_destroy", "jetsci_surrogate_get_params",
             "jetsci_surrogate_label", "jetsci_surrogate_train", "jetsci_surrogate_gradient",
-            "jetsci_surrogate_eval", "jetsci_mesh_set_surrogate"]
+            "jetsci_surrogate_eval", "jetsci_mesh_set_surrogate", "jetsci_mesh_surrogate_fallbacks"]
 
 
 def pack_layers(layers):
@@ -381,6 +382,12 @@ class Surrogate:
         D = torch.empty(n, 6, 6, dtype=torch.float64, device="cuda") if tangent else None
         _check(lib.jetsci_surrogate_eval(self._h, _ptr(E6), _ptr(phase), n, _ptr(S6), _ptr(D), _stream(stream)))
         return (S6, D) if tangent else S6
+
+
+def surrogate_fallbacks(mesh):
+    c = C.c_uint32()
+    _check(lib.jetsci_mesh_surrogate_fallbacks(mesh.handle, C.byref(c)))
+    return c.value
 
 
 def attach_surrogate(mesh, surrogate):

@@ -414,3 +414,30 @@ def test_surrogate_tangent_scaling():
         fd = (mlp.surrogate_stress(layers, E6 + d, ph, 0.05, sc, sh)[0]
               - mlp.surrogate_stress(layers, E6 - d, ph, 0.05, sc, sh)[0]) / (2 * h)
         assert np.allclose(fd, D[:, :, c], rtol=1e-6, atol=1e-6)
+
+
+def test_surrogate_oracle_tangent_is_fd_of_its_residual():
+    from oracle import surrogate_fem
+    coords, conn = I.box_mesh(2, 2, 1, distort=0.2, seed=4)
+    g = np.random.default_rng(4)
+    phase = np.array([0, 1, 1, 0], np.int32)
+    M = oracle.Mesh(coords, conn, phase, I.composite_materials(NH))
+    layers = _tiny_layers(9)
+    sc = np.array([[2e8] * 6, [3e9] * 6]); sh = np.zeros((2, 6))
+    u = g.uniform(-3e-3, 3e-3, coords.size)
+    K, R, fb, _ = surrogate_fem.assemble(M, u, layers, 0.05, 0.05, sc, sh)
+    assert fb == 0
+    v = g.uniform(-1, 1, coords.size)
+    h = 1e-7
+    Rp = surrogate_fem.assemble(M, u + h * v, layers, 0.05, 0.05, sc, sh)[1]
+    Rm = surrogate_fem.assemble(M, u - h * v, layers, 0.05, 0.05, sc, sh)[1]
+    assert rel((Rp - Rm) / (2 * h), K @ v) < 1e-6
+    # all points out of range: the plain neo-Hookean oracle
+    K0, R0, fb0, _ = surrogate_fem.assemble(M, u, layers, 0.05, 1e-12, sc, sh)
+    assert fb0 == 8 * len(conn)
+    rp, col = oracle.csr_pattern(conn, len(coords))
+    vals, Rref = oracle.tangent_csr(M, u, rp, col)
+    Kref = np.zeros_like(K0)
+    for r in range(len(Kref)):
+        Kref[r, col[rp[r]:rp[r + 1]]] = vals[rp[r]:rp[r + 1]]
+    assert rel(R0, Rref) < 1e-13 and rel(K0, Kref) < 1e-13
