@@ -259,6 +259,33 @@ jetsci_status jetsci_mesh_set_surrogate(jetsci_mesh mesh, jetsci_surrogate s);
 jetsci_status jetsci_mesh_surrogate_fallbacks(jetsci_mesh mesh, uint32_t *count_host);
 
 /* ---------------------------------------------------------------------------
+ * Newton's method for R(u) = 0 with a Jacobi-preconditioned conjugate-gradient solve of
+ * K du = -R per step (the paper's outer Newton iteration with a Krylov solve per step,
+ * Sections II-A and V; the paper's PETSc solver stack itself is not reproduced).  A driver
+ * for end-to-end use and iteration counts, not a tuned solver.
+ * u_dev [n_dof] (in: initial guess, out: solution); the n_bc DOFs bc_dofs_dev (int64,
+ * device or host) are fixed to bc_vals_dev and excluded from the residual and the Krylov
+ * space.  The residual and its norm are FP64; tangent_precision (FP64, FP32 or TF32) sets
+ * the tangent's arithmetic (FP32/TF32 make it an inexact Newton method).  Converged when
+ * ||R_free|| <= rtol * ||R_free(u_0)||; each CG stops at ||r|| <= cg_rtol ||r_0|| or max_cg.
+ * Allocates its own workspace (about 7 n_dof doubles plus one CSR value array) and
+ * synchronises.  Returns JETSCI_ERR_NOT_CONVERGED after max_newton steps, with *info filled.
+ */
+typedef struct {
+    int32_t newton_iters;         /* Newton steps taken                                  */
+    int32_t cg_iters_total;       /* CG iterations over all steps                        */
+    int32_t cg_capped;            /* steps whose CG hit max_cg                           */
+    int32_t reserved;
+    double final_rel_residual;    /* ||R_free(u)|| / ||R_free(u_0)||                      */
+    double residual_history[32];  /* relative residual before step k (k < 32)            */
+} jetsci_newton_info;
+
+jetsci_status jetsci_newton_solve(jetsci_mesh mesh, double *u_dev, int64_t n_bc, const int64_t *bc_dofs_dev,
+                                  const double *bc_vals_dev, int32_t tangent_precision, double rtol,
+                                  int32_t max_newton, double cg_rtol, int32_t max_cg, void *stream,
+                                  jetsci_newton_info *info);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free ||x||_2 (no counterpart in the paper; a service for callers that
  * cannot allocate device memory when they need the norm -- their device memory is
  * reserved up front by another runtime's pool, or a cudaMalloc and its implicit device

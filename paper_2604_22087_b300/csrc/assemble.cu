@@ -356,6 +356,7 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
         return tangent_colours<float, float>(m, A, u, (float *)vals, R, s);
     }
+    if (precision == JETSCI_TF32) return launch_tf32(m, u, nullptr, (float *)vals, R, nullptr, E_elem, s);
     if (precision == JETSCI_SURROGATE) return launch_surrogate(m, u, (float *)vals, R, s);
     return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the tangent");
 }
@@ -374,11 +375,12 @@ static void apply_colours(jetsci_mesh m, ElemArgs A, const double *u, const doub
 
 jetsci_status launch_apply_mf(jetsci_mesh m, const double *u, const double *v, double *y, int precision,
                               const double *E_elem, cudaStream_t s) {
+    if (precision == JETSCI_TF32) return launch_tf32(m, u, v, nullptr, nullptr, y, E_elem, s);
     JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     ElemArgs A = make_args(m, E_elem);
     if (precision == JETSCI_FP64)
         apply_colours<double>(m, A, u, v, y, s);
-    else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
+    else if (precision == JETSCI_FP32)
         apply_colours<float>(m, A, u, v, y, s);
     else
         return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the matrix-free product");

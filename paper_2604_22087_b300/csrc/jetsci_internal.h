@@ -79,6 +79,8 @@ jetsci_status launch_spmv(jetsci_mesh m, const void *vals, bool fp32, const doub
                           double *y, cudaStream_t s);
 jetsci_status launch_norm2(const double *x, int64_t n, double *partials, int64_t cap,
                            double *out, cudaStream_t s);
+jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float *vals, double *R, double *y,
+                          const double *E_elem, cudaStream_t s);
 jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, double *R, cudaStream_t s);
 jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
                                    const double *R, double *g, int precision, cudaStream_t s);

@@ -131,7 +131,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// TMEM address of column `col` in the lane quarter of the calling warp.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// TMEM address of column `col` in the lane quarter of the calling warp (the column must be
+// the same for all 32 threads of the warp: tcgen05.ld is warp-collective).
 __device__ __forceinline__ uint32_t tmem_lane_addr(uint32_t base, int col) {
     const uint32_t quarter = (threadIdx.x >> 5) & 3;
     return base + ((quarter * 32u) << 16) + (uint32_t)col;

@@ -258,3 +258,19 @@ def lognormal_problem(n: int = 64, seed: int = 4) -> Problem:
     v = uniform_field(coords.size, 1.0, seed + 20)
     return Problem(f"lognormal_E_{n}^3", coords, conn, phase, [(1.0e10, 0.3, LAW_LINEAR_ELASTIC)],
                    u, v, E_elem=E)
+
+
+def roller_bcs(coords: np.ndarray, stretch: float = 0.01, tol: float = 1e-12):
+    """Uniaxial-stretch Dirichlet set: u1 = 0 on X1 = 0, u1 = stretch on X1 = 1, u2 = 0 on
+    X2 = 0, u3 = 0 on X3 = 0 (rollers).  Returns (dofs int64, values float64)."""
+    x = coords
+    dofs, vals = [], []
+    for n in np.where(np.abs(x[:, 0]) < tol)[0]:
+        dofs.append(3 * n); vals.append(0.0)
+    for n in np.where(np.abs(x[:, 0] - 1.0) < tol)[0]:
+        dofs.append(3 * n); vals.append(stretch)
+    for n in np.where(np.abs(x[:, 1]) < tol)[0]:
+        dofs.append(3 * n + 1); vals.append(0.0)
+    for n in np.where(np.abs(x[:, 2]) < tol)[0]:
+        dofs.append(3 * n + 2); vals.append(0.0)
+    return np.array(dofs, dtype=np.int64), np.array(vals, dtype=np.float64)

@@ -393,3 +393,29 @@ def surrogate_fallbacks(mesh):
 def attach_surrogate(mesh, surrogate):
     _check(lib.jetsci_mesh_set_surrogate(mesh.handle, None if surrogate is None else surrogate.handle))
     mesh._surrogate = surrogate  # keep it alive while attached
+
+
+# ---------------------------------------------------------------------- Newton driver
+class NewtonInfo(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("cg_iters_total", C.c_int32), ("cg_capped", C.c_int32),
+                ("reserved", C.c_int32), ("final_rel_residual", C.c_double), ("residual_history", C.c_double * 32)]
+
+
+lib.jetsci_newton_solve.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, C.c_int32, C.c_double, C.c_int32, C.c_double,
+                                    C.c_int32, _vp, C.POINTER(NewtonInfo)]
+lib.jetsci_newton_solve.restype = C.c_int
+EXPORTS += ["jetsci_newton_solve"]
+
+
+def newton_solve(mesh, u, bc_dofs, bc_vals, tangent_precision=FP64, rtol=1e-10, max_newton=20, cg_rtol=1e-8,
+                 max_cg=20000, stream=None, raise_on_fail=True):
+    """Newton + Jacobi-CG on the device; u (CUDA float64) is updated in place.  Returns NewtonInfo."""
+    _dev_f64(u, mesh.n_dof, "u")
+    d = torch.as_tensor(np.ascontiguousarray(bc_dofs, dtype=np.int64)).cuda()
+    v = torch.as_tensor(np.ascontiguousarray(bc_vals, dtype=np.float64)).cuda()
+    info = NewtonInfo()
+    st = lib.jetsci_newton_solve(mesh.handle, _ptr(u), d.numel(), _ptr(d), _ptr(v), tangent_precision, rtol,
+                                 max_newton, cg_rtol, max_cg, _stream(stream), C.byref(info))
+    if st != 0 and (raise_on_fail or st != 6):
+        _check(st)
+    return info

@@ -240,3 +240,60 @@ def test_full_size_fibre_rve_sampled_rows():
             assert np.max(np.abs(vals_h[rp[r]:rp[r + 1]] - kref)) <= FP64_TOL * np.max(np.abs(kref))
     assert mesh.check() == 0
     mesh.close()
+
+
+def test_tf32_tensor_core_bounds(case):
+    """TF32 keeps 10 mantissa bits (u = 2^-11): both GEMM operands are rounded, so each
+    product carries ~2u; the CSR entries sum 8 elements' contributions and K.v sums 81
+    entries per row with cancellation, giving the 3e-3 (values) and 1e-2 (K.v) bounds."""
+    prob, mesh, _, ref = case
+    J = jetsci()
+    u = cuda(prob.u)
+    R = mesh.new_vector()
+    vals = mesh.tangent_csr(u, R=R, precision=J.TF32)
+    assert relerr(vals.cpu().numpy(), ref["vals"]) <= 3e-3
+    assert relerr(R.cpu().numpy(), ref["R"]) <= 2e-4
+    y = mesh.apply_tangent(u, cuda(prob.v), precision=J.TF32)
+    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= 1e-2
+    assert mesh.check() == 0
+
+
+def _oracle_newton(prob, dofs, vals, rtol=1e-12):
+    """Oracle Newton: own assembly, direct sparse solve of the free block (library step)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    om = oracle.Mesh.of(prob)
+    rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    u = np.zeros(prob.n_dof)
+    u[dofs] = vals
+    free = np.ones(prob.n_dof, bool)
+    free[dofs] = False
+    r0 = None
+    for _ in range(30):
+        v, R = oracle.tangent_csr(om, u, rp, col)
+        nr = np.linalg.norm(R[free])
+        r0 = nr if r0 is None else r0
+        if nr <= rtol * r0:
+            break
+        K = sp.csr_matrix((v, col, rp), shape=(prob.n_dof, prob.n_dof))[free][:, free]
+        u[free] -= spla.spsolve(K.tocsc(), R[free])
+    return u
+
+
+@pytest.mark.parametrize("tp", ["fp64", "fp32", "tf32"])
+def test_newton_cg_jacobi_converges_to_oracle_solution(tp):
+    J = jetsci()
+    coords, conn = I.box_mesh(5, 4, 4, distort=0.15, seed=2)
+    g = np.random.default_rng(2)
+    phase = (g.uniform(size=len(conn)) < 0.4).astype(np.int32)
+    prob = I.Problem("newton_box", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                     np.zeros(coords.size), np.zeros(coords.size))
+    dofs, vals = I.roller_bcs(coords, 0.01)
+    mesh = J.Mesh.of(prob)
+    u = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    info = J.newton_solve(mesh, u, dofs, vals, tangent_precision={"fp64": J.FP64, "fp32": J.FP32, "tf32": J.TF32}[tp],
+                          rtol=1e-10, cg_rtol=1e-10)
+    assert info.final_rel_residual <= 1e-10
+    assert info.newton_iters <= (6 if tp == "fp64" else 12)
+    u_ref = _oracle_newton(prob, dofs, vals)
+    assert relerr(u.cpu().numpy(), u_ref) <= 1e-8
