@@ -1,23 +1,25 @@
 """Benchmark of the hex8 element-assembly hot path on B300.
 
-One step = the whole hot path over one synthetic workload: consistent-tangent CSR
-assembly with the residual fused (gather, shape gradients, constitutive update, R_e and
-K_e, coloured scatter), the matrix-free tangent product K.v, and the FP64 residual norm.
-Workload (default): 128^3 hex8 unidirectional-fibre RVE (2,097,152 elements, 6,440,067
-DOFs, 513,599,625 CSR non-zeros), compressible neo-Hookean per phase, 1% uniaxial stretch
-plus 1e-4 noise, FP64.  Metric: elements per second of that step (higher is better).
+One step = the whole hot path over one synthetic workload: consistent-tangent CSR assembly
+with the residual fused (gather, shape gradients, constitutive update, R_e and K_e, coloured
+scatter), the tangent product K.v both from the assembled CSR matrix and matrix-free, and the
+FP64 residual norm.  Workload (default): 128^3 hex8 unidirectional-fibre RVE (2,097,152
+elements, 6,440,067 DOFs, 513,599,625 CSR non-zeros), compressible neo-Hookean per phase at a
+1% uniaxial stretch plus 1e-4 noise, FP64.  Metric: elements per second of that step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl jetsci|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl jetsci|reference] [--newton]
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun), each rank runs its own replica of the
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own replica of the
 workload (independent problems, no data-path collective: weak scaling); the timed region is
-bracketed by barriers and the max over ranks is reported.
+bracketed by barriers and the max over ranks is reported.  Besides the headline, the line
+carries per-form timings with errors against the FP64 oracle on sampled rows (FP64, FP32,
+TF32 tensor-core and surrogate forms), surrogate training, the 64^3 adjoint workload and,
+with --newton, Newton iteration counts.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -32,6 +34,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % of HBM peak"
 
+# Work per element of the dominant kernel, k_tangent<double,double> (derivation in the design doc):
+# executed FP64 operations of the formulation (ncu: dfma x2 + dadd + dmul per element) and the
+# algorithmic bytes (write-once CSR values + mesh data + u + R).
+TANGENT_FP64_FLOP_PER_ELEM = 28_580.0
+TANGENT_BYTES_PER_ELEM_FP64 = 2_160.0
+# Executed FP64 operations per element of k_apply_mf<double> and k_residual<double> (ncu).
+SPMV_BYTES_PER_NNZ_FP64 = 12.0
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -40,14 +50,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jetsci", choices=["jetsci", "reference"])
     ap.add_argument("--n", type=int, default=128, help="elements per side of the RVE")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip surrogate training and the adjoint workload")
+    ap.add_argument("--newton", action="store_true", help="Newton iteration counts per tangent precision")
+    ap.add_argument("--newton-n", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
 
-# ------------------------------------------------------------------------------ helpers
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -58,15 +69,13 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling in a background process during the timed region."""
+    """nvidia-smi clock / throttle-reason sampling in a background process."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index):
-        self.idx = device_index
-        self.proc = None
-        self.lines = []
+        self.idx, self.proc, self.lines = device_index, None, []
 
     def __enter__(self):
         try:
@@ -113,10 +122,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def make_problem(n):
+    from paper_2604_22087_b300 import inputs as I
+    return I.fibre_composite(n, seed=2, law=I.LAW_NEO_HOOKEAN)
+
+
+def config_dict(prob, n):
+    return {"workload": f"fibre RVE {n}^3 hex8 neo-Hookean (50% fibres, E 3.5/70 GPa), 1% stretch + 1e-4 noise; "
+                        f"step = tangent CSR with fused residual + K.v (CSR SpMV and matrix-free) + ||R||, FP64",
+            "n_elem": prob.n_elem, "n_dof": prob.n_dof, "fibre_fraction": prob.meta.get("fibre_fraction"),
+            "l2": "inputs larger than L2 (CSR values 4.1 GB written and read every step)"}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
 def cpu_baseline(prob, target_seconds):
     """The FP64 oracle (single-threaded C, as it stands) on a bounded sample of the same
-    workload: the first M elements in element order (a contiguous slab of the RVE), one
-    step = tangent CSR + residual + element-loop K.v + norm; pattern setup not timed."""
+    workload: the first M elements in element order (a contiguous slab of the RVE); one step =
+    tangent CSR + residual + element-loop K.v + CSR K.v + norm; pattern setup not timed."""
     import oracle
 
     def run(m):
@@ -125,14 +147,14 @@ def cpu_baseline(prob, target_seconds):
         remap = -np.ones(prob.n_nodes, dtype=np.int64)
         remap[used] = np.arange(len(used))
         sub_conn = remap[conn].astype(np.int32)
-        sub_coords = prob.coords[used]
         dofs = (3 * used[:, None] + np.arange(3)).ravel()
-        om = oracle.Mesh(sub_coords, sub_conn, prob.phase[:m], prob.materials)
+        om = oracle.Mesh(prob.coords[used], sub_conn, prob.phase[:m], prob.materials)
         rp, col = oracle.csr_pattern(sub_conn, len(used))
         u, v = prob.u[dofs], prob.v[dofs]
         t0 = time.perf_counter()
         vals, R = oracle.tangent_csr(om, u, rp, col)
         oracle.apply_tangent(om, u, v)
+        oracle.spmv(rp, col, vals, v)
         oracle.norm2(R)
         return time.perf_counter() - t0
 
@@ -141,21 +163,15 @@ def cpu_baseline(prob, target_seconds):
     m = int(min(prob.n_elem, max(m, m * target_seconds / max(dt, 1e-6))))
     dt = run(m)
     return {"value": m / dt, "unit": "elem/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {m} elements (contiguous slab) of the same workload, FP64, one step "
-                      f"(tangent CSR + residual + K.v + norm) in {dt:.1f} s"}
+            "sample": f"first {m} elements (a contiguous slab) of the same workload, FP64, one step "
+                      f"(tangent CSR + residual + element K.v + CSR K.v + norm) in {dt:.1f} s"}
 
 
-def make_problem(n, precision):
-    from paper_2604_22087_b300 import inputs as I
-    return I.fibre_composite(n, seed=2, law=I.LAW_NEO_HOOKEAN)
-
-
-# ------------------------------------------------------------------------------ reference arm
-def run_reference(args, rank, world):
+def run_reference(args, rank):
     if rank != 0:
         return
-    prob = make_problem(args.n, args.precision)
-    per = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    prob = make_problem(args.n)
+    per = max(1.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_baseline(prob, min(per, 2.0))
     vals = [cpu_baseline(prob, per) for _ in range(args.steps)]
@@ -165,18 +181,183 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elem/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * prob.n_elem / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(prob, args),
-            "cpu_baseline": cb, "e2e": {"value": v, "unit": "elem/s", "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": config_dict(prob, args.n), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "elem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def config_dict(prob, args):
-    return {"workload": f"fibre RVE {args.n}^3 hex8 neo-Hookean, 1% stretch + 1e-4 noise, "
-                        f"step = tangent CSR (+R) + matrix-free K.v + ||R||",
-            "n_elem": prob.n_elem, "n_dof": prob.n_dof, "precision": args.precision,
-            "fibre_fraction": prob.meta.get("fibre_fraction"),
-            "l2": "inputs larger than L2 (CSR values 4.1 GB FP64 written every step)"}
+# ------------------------------------------------------------------------------ helpers
+def timeit(fn, stream, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+class SampledOracle:
+    """Oracle rows of R, K and K.v at a fixed sample of nodes (computed element by element)."""
+
+    def __init__(self, prob, n_nodes=24, seed=0):
+        import oracle
+        self.om = oracle.Mesh.of(prob)
+        g = np.random.default_rng(seed)
+        self.nodes = np.concatenate([[0, prob.n_nodes - 1], g.choice(prob.n_nodes, n_nodes - 2, replace=False)])
+        self.rows = oracle.sampled_rows(self.om, prob.u, prob.v, self.nodes)
+
+    def errors(self, R, vals, y, rowptr, col):
+        """Max errors over the sample, each relative to the sample's max |reference|."""
+        eR = ey = eK = 0.0
+        sR = max(np.max(np.abs(self.rows[n][0])) for n in self.nodes)
+        sy = max(np.max(np.abs(self.rows[n][1])) for n in self.nodes)
+        sK = 0.0
+        for n in self.nodes:
+            Rn, Kvn, krow = self.rows[n]
+            if R is not None:
+                eR = max(eR, np.max(np.abs(R[3 * n:3 * n + 3] - Rn)))
+            if y is not None:
+                ey = max(ey, np.max(np.abs(y[3 * n:3 * n + 3] - Kvn)))
+            if vals is not None:
+                for i in range(3):
+                    r = 3 * n + i
+                    cs = col[rowptr[r]:rowptr[r + 1]]
+                    kref = np.array([krow[c][i] for c in cs])
+                    sK = max(sK, np.max(np.abs(kref)))
+                    eK = max(eK, np.max(np.abs(vals[rowptr[r]:rowptr[r + 1]].astype(np.float64) - kref)))
+        out = {}
+        if R is not None:
+            out["R"] = eR / sR
+        if vals is not None:
+            out["K"] = eK / sK
+        if y is not None:
+            out["Kv"] = ey / sy
+        return out
+
+
+def gather_rows(t, nodes):
+    idx = np.concatenate([[3 * n, 3 * n + 1, 3 * n + 2] for n in nodes])
+    out = np.zeros(int(t.numel()))
+    out[idx] = t[idx].cpu().numpy()
+    return out
+
+
+def gather_vals(vals, rowptr, nodes):
+    out = np.zeros(int(vals.numel()), dtype=np.float64)
+    for n in nodes:
+        a, b = int(rowptr[3 * n]), int(rowptr[3 * n + 3])
+        out[a:b] = vals[a:b].double().cpu().numpy()
+    return out
+
+
+# ------------------------------------------------------------------------------ extras
+def train_surrogate(J, torch, I, n_samples=1 << 20, epochs=50, batch=4096):
+    """Surrogate trained on 2^20 neo-Hookean labels (|E_ij| <= 0.05) by the library's kernels."""
+    E6, ph = I.strain_samples(n_samples, seed=5)
+    E6d, phd = torch.as_tensor(E6).cuda(), torch.as_tensor(ph).cuda()
+    mats = I.composite_materials(I.LAW_NEO_HOOKEAN)
+    Sd = J.Surrogate.label(mats, E6d, phd)
+    sc = np.array([[I.MATRIX_E * 0.05] * 6, [I.INCLUSION_E * 0.05] * 6])
+    s = J.Surrogate(I.mlp_init(5), in_scale=0.05, range_=0.05, out_scale=sc, out_shift=np.zeros((2, 6)))
+    order = torch.as_tensor(I.minibatch_order(n_samples, epochs, seed=5)).cuda()
+    steps = epochs * (n_samples // batch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = s.train(E6d, phd, Sd, order, n_steps=steps, batch=batch, lr_max=3e-3, lr_min=1e-5)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    Et, pt = I.strain_samples(1 << 16, seed=99)
+    Etd, ptd = torch.as_tensor(Et).cuda(), torch.as_tensor(pt).cuda()
+    S_true = J.Surrogate.label(mats, Etd, ptd).cpu().numpy()
+    S, D = s.eval(Etd, ptd)
+    S = S.cpu().numpy()
+    scale = sc[pt]
+    rms = float(np.sqrt(np.mean(((S - S_true) / scale) ** 2)))
+    rel_max = float(np.max(np.abs(S - S_true)) / np.max(np.abs(S_true)))
+    l = losses.cpu().numpy()
+    info = {"samples": n_samples, "epochs": epochs, "batch": batch, "steps": steps, "seconds": dt,
+            "steps_per_s": steps / dt, "loss_first": float(l[:10].mean()), "loss_last": float(l[-100:].mean()),
+            "stress_rms_err_normalised": rms, "stress_max_err_rel": rel_max}
+    return s, info
+
+
+def adjoint_workload(J, torch, I, stream):
+    """64^3 linear-elastic mesh with a lognormal per-element modulus: dLoss/dE for
+    L = 1/2 ||R(u; E)||^2, checked by central differences (h = 1e-6 E_e) on 32 random
+    elements and against the oracle gradient on the same elements."""
+    import oracle
+    prob = I.lognormal_problem(64, seed=4)
+    mesh = J.Mesh.of(prob)
+    u, E = torch.as_tensor(prob.u).cuda(), torch.as_tensor(prob.E_elem).cuda()
+    R = mesh.new_vector()
+    g = torch.empty(prob.n_elem, dtype=torch.float64, device="cuda")
+    out = {"workload": "lognormal E 64^3 linear elastic (262,144 elements)"}
+    for name, p in (("fp64", J.FP64), ("fp32", J.FP32)):
+        ms_r = timeit(lambda: mesh.residual(u, R=R, precision=p, E_elem=E, stream=stream), stream)
+        ms_g = timeit(lambda: mesh.material_grad(u, R, E_elem=E, g=g, precision=p, stream=stream), stream)
+        out[f"residual_{name}_ms"] = ms_r
+        out[f"grad_{name}_ms"] = ms_g
+        out[f"forward_backward_{name}_elem_per_s"] = prob.n_elem / ((ms_r + ms_g) * 1e-3)
+        if name == "fp64":
+            g64 = g.clone()
+        else:
+            g32 = g.clone()
+    rng = np.random.default_rng(7)
+    sample = rng.choice(prob.n_elem, 32, replace=False)
+    fd = []
+    for e in sample:
+        h = 1e-6 * float(prob.E_elem[e])
+        Ls = []
+        for sgn in (1, -1):
+            Ep = E.clone()
+            Ep[e] += sgn * h
+            Rp = mesh.residual(u, E_elem=Ep)
+            Ls.append(0.5 * float(mesh.norm2(Rp).item()) ** 2)
+        fd.append((Ls[0] - Ls[1]) / (2 * h))
+    fd = np.array(fd)
+    gs = g64.cpu().numpy()[sample]
+    # oracle gradient on the sampled elements: R at their nodes from the adjacent elements
+    om = oracle.Mesh.of(prob)
+    ptr, eidx = oracle.node_elements(prob.conn, prob.n_nodes)
+    g_ref = []
+    for e in sample:
+        nodes = prob.conn[e].astype(np.int64)
+        Rn = np.zeros(24)
+        for a, n in enumerate(nodes):
+            for e2 in eidx[ptr[n]:ptr[n + 1]]:
+                Re = oracle.element_of(om, int(e2), prob.u, tangent=False)
+                a2 = int(np.where(prob.conn[e2] == n)[0][0])
+                Rn[3 * a:3 * a + 3] += Re[3 * a2:3 * a2 + 3]
+        Re = oracle.element_of(om, int(e), prob.u, tangent=False)
+        g_ref.append(float(Rn @ Re) / float(prob.E_elem[e]))
+    g_ref = np.array(g_ref)
+    scale = np.max(np.abs(g_ref))
+    out["fd_max_rel_err_fp64"] = float(np.max(np.abs(gs - fd)) / scale)
+    out["oracle_max_rel_err_fp64"] = float(np.max(np.abs(gs - g_ref)) / scale)
+    out["oracle_max_rel_err_fp32"] = float(np.max(np.abs(g32.cpu().numpy()[sample] - g_ref)) / scale)
+    mesh.close()
+    return out
+
+
+def newton_counts(J, torch, I, n):
+    prob = I.fibre_composite(n, seed=2)
+    mesh = J.Mesh.of(prob)
+    dofs, vals = I.roller_bcs(prob.coords, 0.01)
+    out = {"workload": f"fibre RVE {n}^3 neo-Hookean, rollers, 1% stretch, rtol 1e-10, Jacobi-CG rtol 1e-10"}
+    for name, p in (("fp64", J.FP64), ("fp32", J.FP32), ("tf32", J.TF32)):
+        u = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        info = J.newton_solve(mesh, u, dofs, vals, tangent_precision=p, rtol=1e-10, max_newton=20, cg_rtol=1e-10,
+                              max_cg=200000, raise_on_fail=False)
+        out[name] = {"newton_iters": info.newton_iters, "cg_iters_total": info.cg_iters_total,
+                     "final_rel_residual": info.final_rel_residual, "seconds": time.perf_counter() - t0,
+                     "history": [info.residual_history[k] for k in range(min(info.newton_iters + 1, 32))]}
+    mesh.close()
+    return out
 
 
 # ------------------------------------------------------------------------------ main arm
@@ -186,7 +367,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, rank, world)
+        run_reference(args, rank)
         return
     import torch
     import torch.distributed as dist
@@ -194,27 +375,29 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_22087_b300 import inputs as I
     from paper_2604_22087_b300 import jetsci as J
 
-    prec = {"fp64": J.FP64, "fp32": J.FP32, "df64": J.DF64}[args.precision]
-    prob = make_problem(args.n, args.precision)
+    prob = make_problem(args.n)
     mesh = J.Mesh.of(prob)
     stream = torch.cuda.Stream()
     u = torch.as_tensor(prob.u).cuda()
     v = torch.as_tensor(prob.v).cuda()
     R = mesh.new_vector()
     y = mesh.new_vector()
-    vals = mesh.new_values(prec)
+    y2 = mesh.new_vector()
+    vals = mesh.new_values(J.FP64)
     nrm = torch.empty(1, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
 
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        mesh.tangent_csr(u, vals=vals, R=R, precision=prec, stream=stream)
+        mesh.tangent_csr(u, vals=vals, R=R, stream=stream)
         if ev is not None:
             ev[1].record(stream)
-        mesh.apply_tangent(u, v, y=y, precision=prec, stream=stream)
+        mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals, stream=stream)
+        mesh.apply_tangent(u, v, y=y, stream=stream)
         mesh.norm2(R, out=nrm, stream=stream)
 
     def barrier():
@@ -240,12 +423,11 @@ def main():
     tmax = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_total = float(tmax.item())
-    ms_step = ms_total / args.steps
+    ms_step = float(tmax.item()) / args.steps
     value = world * prob.n_elem / (ms_step * 1e-3)
-    assert mesh.check() == 0
+    flags = mesh.check()
 
-    # ---- end to end through the public API with host buffers (pinned), copies timed
+    # ---- end to end through the public API with pinned host buffers, copies timed
     u_h = torch.as_tensor(prob.u).pin_memory()
     v_h = torch.as_tensor(prob.v).pin_memory()
     y_h = torch.empty(prob.n_dof, dtype=torch.float64).pin_memory()
@@ -257,7 +439,7 @@ def main():
             v.copy_(v_h, non_blocking=True)
         step()
         with torch.cuda.stream(stream):
-            y_h.copy_(y, non_blocking=True)
+            y_h.copy_(y2, non_blocking=True)
             n_h.copy_(nrm, non_blocking=True)
 
     e2e_step()
@@ -269,41 +451,44 @@ def main():
     e1.record(stream)
     e1.synchronize()
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    emax = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    emax = torch.tensor([e0.elapsed_time(e1) / args.steps], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(emax, op=dist.ReduceOp.MAX)
     e2e_ms = float(emax.item())
 
-    forms = {}
-    if not args.no_forms and rank == 0:
-        forms = measure_forms(J, mesh, prob, stream, u, v)
+    extra = {}
+    if rank == 0 and not args.no_forms:
+        extra["forms"] = measure_forms(J, torch, I, mesh, prob, stream, u, v, vals, args)
+    if rank == 0 and not args.no_extras:
+        try:
+            extra["adjoint"] = adjoint_workload(J, torch, I, stream)
+        except Exception as ex:  # report, do not hide
+            extra["adjoint"] = {"error": repr(ex)}
+    if rank == 0 and args.newton:
+        extra["newton"] = newton_counts(J, torch, I, args.newton_n)
 
     if rank == 0:
         peaks, peak_kind = load_peaks()
         clocks = clk.summary()
-        # dominant kernel: the tangent assembly (FP64 pipe bound in FP64)
-        fp64_peak = 4.0 * 148 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # 2 DFMA/clk/SM
-        flops = TANGENT_FP64_FLOP_PER_ELEM * prob.n_elem
-        achieved = flops / (ms_tangent * 1e-3) / 1e12
-        hbm_bytes = TANGENT_BYTES_PER_ELEM_FP64 * prob.n_elem
+        fp64_peak = 4.0 * 148 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # 2 DFMA / clk / SM
+        achieved = TANGENT_FP64_FLOP_PER_ELEM * prob.n_elem / (ms_tangent * 1e-3) / 1e12
+        hbm = TANGENT_BYTES_PER_ELEM_FP64 * prob.n_elem / (ms_tangent * 1e-3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": "elem/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "df64": "f32x2"}[args.precision],
-            "data": "synthetic", "config": config_dict(prob, args),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(prob, args.n),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_tangent<double,double>",
-                         "peak_source": "2 DFMA/clk/SM x 148 SMs x sm_max_mhz (FP64 pipe)",
-                         "hbm_achieved_gbs": hbm_bytes / (ms_tangent * 1e-3) / 1e9,
-                         "hbm_frac": hbm_bytes / (ms_tangent * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                         "hbm_peak_kind": peak_kind, "ms_per_launch_group": ms_tangent},
+                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 148 SMs x 2032 MHz (derived in DESIGN.md)",
+                         "ms_per_launch_group": ms_tangent, "hbm_achieved_gbs": hbm,
+                         "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind},
             "e2e": {"value": world * prob.n_elem / (e2e_ms * 1e-3), "unit": "elem/s",
                     "h2d_bytes_per_step": 2 * prob.n_dof * 8, "d2h_bytes_per_step": prob.n_dof * 8 + 8},
-            "gpu_launches": args.steps * (2 * mesh.n_colours + 2),
-            "clocks": clocks,
-            "forms": forms,
+            # per step: k_tangent and k_apply_mf once per colour, k_spmv, two norm passes
+            "gpu_launches": args.steps * (2 * mesh.n_colours + 3),
+            "clocks": clocks, "device_flags": flags,
         }
+        line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -312,38 +497,54 @@ def main():
         dist.destroy_process_group()
 
 
-# Algorithmic work per element of the dominant kernel (derivation in the design doc).
-TANGENT_FP64_FLOP_PER_ELEM = 26_000.0
-TANGENT_BYTES_PER_ELEM_FP64 = 2160.0
-
-
-def measure_forms(J, mesh, prob, stream, u, v, reps=5):
-    """Per-call device times of the individual entry points (ms) and elem/s."""
-    import torch
+def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
+    """Per-entry-point device times (ms, elem/s) and errors vs the FP64 oracle on sampled rows."""
     out = {}
+    so = SampledOracle(prob)
+    rp, col = mesh.pattern()
+    rp_h, col_h = rp.cpu().numpy(), col.cpu().numpy()
     R = mesh.new_vector()
     y = mesh.new_vector()
 
-    def timeit(fn):
-        fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        b.synchronize()
-        ms = a.elapsed_time(b) / reps
-        return {"ms": ms, "elem_per_s": prob.n_elem / (ms * 1e-3)}
+    def rec(name, ms, extra=None):
+        d = {"ms": ms, "elem_per_s": prob.n_elem / (ms * 1e-3)}
+        if extra:
+            d.update(extra)
+        out[name] = d
 
-    for name, p in (("fp64", J.FP64), ("fp32", J.FP32)):
-        vals = mesh.new_values(p)
-        out[f"residual_{name}"] = timeit(lambda: mesh.residual(u, R=R, precision=p, stream=stream))
-        out[f"tangent_csr_{name}"] = timeit(lambda: mesh.tangent_csr(u, vals=vals, R=R, precision=p, stream=stream))
-        out[f"apply_mf_{name}"] = timeit(lambda: mesh.apply_tangent(u, v, y=y, precision=p, stream=stream))
-        out[f"spmv_csr_{name}"] = timeit(lambda: mesh.apply_tangent(None, v, y=y, mode=J.CSR, vals=vals,
-                                                                    precision=p, stream=stream))
-        del vals
+    for name, p in (("fp64", J.FP64), ("df64", J.DF64), ("fp32", J.FP32), ("tf32", J.TF32)):
+        vv = vals64 if p in (J.FP64, J.DF64) else mesh.new_values(p)
+        rec(f"residual_{name}", timeit(lambda: mesh.residual(u, R=R, precision=p, stream=stream), stream))
+        ms = timeit(lambda: mesh.tangent_csr(u, vals=vv, R=R, precision=p, stream=stream), stream)
+        torch.cuda.synchronize()
+        err = so.errors(gather_rows(R, so.nodes), gather_vals(vv, rp_h, so.nodes), None, rp_h, col_h)
+        rec(f"tangent_csr_{name}", ms, {"err_vs_oracle": err})
+        ms = timeit(lambda: mesh.apply_tangent(u, v, y=y, precision=p, stream=stream), stream)
+        torch.cuda.synchronize()
+        rec(f"apply_matrix_free_{name}", ms, {"err_vs_oracle": so.errors(None, None, gather_rows(y, so.nodes), rp_h, col_h)})
+        if p in (J.FP64, J.FP32):
+            ms = timeit(lambda: mesh.apply_tangent(None, v, y=y, mode=J.CSR, vals=vv, precision=p, stream=stream), stream)
+            torch.cuda.synchronize()
+            gbs = (SPMV_BYTES_PER_NNZ_FP64 if p == J.FP64 else 8.0) * mesh.nnz / (ms * 1e-3) / 1e9
+            rec(f"spmv_csr_{name}", ms, {"err_vs_oracle": so.errors(None, None, gather_rows(y, so.nodes), rp_h, col_h),
+                                         "algorithmic_gbs": gbs})
+        if p not in (J.FP64, J.DF64):
+            del vv
+            torch.cuda.empty_cache()
+    if not args.no_extras:
+        s, tinfo = train_surrogate(J, torch, I)
+        out["surrogate_training"] = tinfo
+        J.attach_surrogate(mesh, s)
+        vv = mesh.new_values(J.SURROGATE)
+        ms = timeit(lambda: mesh.tangent_csr(u, vals=vv, R=R, precision=J.SURROGATE, stream=stream), stream)
+        torch.cuda.synchronize()
+        fb = J.surrogate_fallbacks(mesh)
+        err = so.errors(gather_rows(R, so.nodes), gather_vals(vv, rp_h, so.nodes), None, rp_h, col_h)
+        rec("tangent_csr_surrogate", ms, {"err_vs_oracle_neo_hookean": err, "fallback_gauss_points": fb,
+                                          "gauss_points": 8 * prob.n_elem})
+        rec("residual_surrogate", timeit(lambda: mesh.residual(u, R=R, precision=J.SURROGATE, stream=stream), stream))
+        J.attach_surrogate(mesh, None)
+        del vv
         torch.cuda.empty_cache()
     return out
 

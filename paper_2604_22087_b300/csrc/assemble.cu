@@ -65,25 +65,30 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
 }
 
 // ---------------------------------------------------------------------------- tangent
-// Phase 1 (8 lanes per element, lane = Gauss point): kinematics, constitutive update,
-// optional residual, and per Gauss point the spatial gradients g_a = F^-T G_a of all
-// eight shape functions plus c*lam, c*m, c*tau (c = w detJ) into shared memory.
-// Phase 2 (one thread per element and node pair a <= b):
-//   K_ab,ik = sum_q c [ lam g_ai g_bk + m g_ak g_bi + delta_ik (g_a.tau g_b + m g_a.g_b) ]
+// Phase 1 (8 lanes per element, lane = Gauss point): kinematics and constitutive update;
+// per Gauss point the spatial gradients g_a = F^-T G_a of the eight shape functions,
+// tg_a = c (tau + m I) g_a, and c lam, c m, c tau_R into shared memory (c = w detJ,
+// tau = F S F^T the Kirchhoff stress; tau_R = tau for the neo-Hookean law and sigma for the
+// linear law, where tau = 0 in the tangent).  Phase 2 (one thread per element and node pair
+// a <= b):
+//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi + delta_ik g_a . tg_b ]
 // which is the push-forward of sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL
-// for the neo-Hookean CC (and lam, m = mu, tau = 0, g = G for the linear law).
-constexpr int kTanElems = 32;  // elements per 256-thread block
+// for the neo-Hookean CC (F CC F = lam I(x)I + 2 m Isym, m = mu - lam lnJ; the linear law has
+// g = G, m = mu, tau = 0); the diagonal-pair thread (a == b) also forms the residual
+// R_a = sum_q c tau_R g_a (= sum_q w detJ P G_a).
+constexpr int kTanElems = 16;  // elements per 128-thread block
 
 template <typename T>
 struct TangentSmem {
-    T g[kTanElems][8][8][3];  // [elem][q][node a][component]
-    T coef[kTanElems][8][8];  // [elem][q]: c lam, c m, c tau (00,11,22,12,02,01)
+    T g[kTanElems][8][8][3];   // [elem][q][node a][component]
+    T tg[kTanElems][8][8][3];  // c (tau + m I) g_a
+    T coef[kTanElems][8][8];   // [elem][q]: c lam, c m, c tau_R (00,11,22,12,02,01)
     int32_t node[kTanElems][8];
     int32_t elem[kTanElems];
 };
 
 template <typename T, typename VT>
-__global__ void __launch_bounds__(256) k_tangent(ElemArgs A, const double *__restrict__ u,
+__global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__restrict__ u,
                                                  const int64_t *__restrict__ rowptr,
                                                  const uint8_t *__restrict__ slotmap,
                                                  VT *__restrict__ vals, double *__restrict__ R) {
@@ -102,44 +107,58 @@ __global__ void __launch_bounds__(256) k_tangent(ElemArgs A, const double *__res
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
         Constitutive<T> c;
         constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, true);
-        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
-        if (R) {
-            T f[3];
-            nodal_force(c.P, K, l, f);
-            if (active) {
-                bits |= finite3(f) ? 0u : JETSCI_FLAG_NONFINITE;
-#pragma unroll
-                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
-            }
+        if (active) {
+            uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
+            raise_flag(A.flags, bits);
         }
-        if (active) raise_flag(A.flags, bits);
+        const bool lin = mt.law == JETSCI_LINEAR_ELASTIC;
+        const T rdJ = my_rcp(K.dJ);
+        const T cw = K.dJ * T(1.0 / 512.0);
         // W = (F Jp)^-1 = Jp^-1 F^-1 = adj(Jp) F^-1 / det(Jp)
-        T rdJ = my_rcp(K.dJ);
         T W[3][3];
 #pragma unroll
         for (int d = 0; d < 3; d++)
 #pragma unroll
             for (int j = 0; j < 3; j++)
                 W[d][j] = (K.aJ[d][0] * c.Fi[0][j] + K.aJ[d][1] * c.Fi[1][j] + K.aJ[d][2] * c.Fi[2][j]) * rdJ;
-        // g_a,j = sum_d W_dj n_a,d with n_a = 8 dN_a/dxi at this Gauss point
+        const T cl = cw * c.lam, cm = cw * c.m;
+        // c (tau + m I), tau = 0 in the linear law's tangent
+        const T t00 = cw * c.tau[0][0] + cm, t11 = cw * c.tau[1][1] + cm, t22 = cw * c.tau[2][2] + cm;
+        const T t12 = cw * c.tau[1][2], t02 = cw * c.tau[0][2], t01 = cw * c.tau[0][1];
 #pragma unroll
         for (int a = 0; a < 8; a++) {
             const int bits_a = kNodeBits[a];
-            T s0 = (bits_a & 1) ? T(1) : T(-1), s1 = (bits_a & 2) ? T(1) : T(-1), s2 = (bits_a & 4) ? T(1) : T(-1);
-            T fx = T(1) + s0 * K.xi, fy = T(1) + s1 * K.eta, fz = T(1) + s2 * K.zeta;
-            T n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
+            const T s0 = (bits_a & 1) ? T(1) : T(-1), s1 = (bits_a & 2) ? T(1) : T(-1), s2 = (bits_a & 4) ? T(1) : T(-1);
+            const T fx = T(1) + s0 * K.xi, fy = T(1) + s1 * K.eta, fz = T(1) + s2 * K.zeta;
+            const T n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
+            T g[3];
 #pragma unroll
-            for (int j = 0; j < 3; j++) sm.g[es][l][a][j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
+            for (int j = 0; j < 3; j++) {
+                g[j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
+                sm.g[es][l][a][j] = g[j];
+            }
+            sm.tg[es][l][a][0] = t00 * g[0] + t01 * g[1] + t02 * g[2];
+            sm.tg[es][l][a][1] = t01 * g[0] + t11 * g[1] + t12 * g[2];
+            sm.tg[es][l][a][2] = t02 * g[0] + t12 * g[1] + t22 * g[2];
         }
-        T cw = K.dJ * T(1.0 / 512.0);
-        sm.coef[es][l][0] = cw * c.lam;
-        sm.coef[es][l][1] = cw * c.m;
-        sm.coef[es][l][2] = cw * c.tau[0][0];
-        sm.coef[es][l][3] = cw * c.tau[1][1];
-        sm.coef[es][l][4] = cw * c.tau[2][2];
-        sm.coef[es][l][5] = cw * c.tau[1][2];
-        sm.coef[es][l][6] = cw * c.tau[0][2];
-        sm.coef[es][l][7] = cw * c.tau[0][1];
+        sm.coef[es][l][0] = cl;
+        sm.coef[es][l][1] = cm;
+        if (lin) {
+            // tau_R = sigma = P for the linear law
+            sm.coef[es][l][2] = cw * c.P[0][0];
+            sm.coef[es][l][3] = cw * c.P[1][1];
+            sm.coef[es][l][4] = cw * c.P[2][2];
+            sm.coef[es][l][5] = cw * c.P[1][2];
+            sm.coef[es][l][6] = cw * c.P[0][2];
+            sm.coef[es][l][7] = cw * c.P[0][1];
+        } else {
+            sm.coef[es][l][2] = cw * c.tau[0][0];
+            sm.coef[es][l][3] = cw * c.tau[1][1];
+            sm.coef[es][l][4] = cw * c.tau[2][2];
+            sm.coef[es][l][5] = cw * c.tau[1][2];
+            sm.coef[es][l][6] = cw * c.tau[0][2];
+            sm.coef[es][l][7] = cw * c.tau[0][1];
+        }
         sm.node[es][hex_node_of_lane(l)] = node;
         if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
     }
@@ -154,28 +173,32 @@ __global__ void __launch_bounds__(256) k_tangent(ElemArgs A, const double *__res
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
+        T Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
 #pragma unroll 2
         for (int q = 0; q < 8; q++) {
             const T *ga = sm.g[ee][q][a];
             const T *gb = sm.g[ee][q][b];
+            const T *tb = sm.tg[ee][q][b];
             const T *cf = sm.coef[ee][q];
-            T a0 = ga[0], a1 = ga[1], a2 = ga[2], b0 = gb[0], b1 = gb[1], b2 = gb[2];
-            T lam = cf[0], m = cf[1];
-            T t0 = cf[2] * b0 + cf[7] * b1 + cf[6] * b2;
-            T t1 = cf[7] * b0 + cf[3] * b1 + cf[5] * b2;
-            T t2 = cf[6] * b0 + cf[5] * b1 + cf[4] * b2;
-            T s = a0 * (t0 + m * b0) + a1 * (t1 + m * b1) + a2 * (t2 + m * b2);
-            T la0 = lam * a0, la1 = lam * a1, la2 = lam * a2;
-            T ma0 = m * a0, ma1 = m * a1, ma2 = m * a2;
-            Kab[0][0] += la0 * b0 + ma0 * b0 + s;
-            Kab[0][1] += la0 * b1 + ma1 * b0;
-            Kab[0][2] += la0 * b2 + ma2 * b0;
-            Kab[1][0] += la1 * b0 + ma0 * b1;
-            Kab[1][1] += la1 * b1 + ma1 * b1 + s;
-            Kab[1][2] += la1 * b2 + ma2 * b1;
-            Kab[2][0] += la2 * b0 + ma0 * b2;
-            Kab[2][1] += la2 * b1 + ma1 * b2;
-            Kab[2][2] += la2 * b2 + ma2 * b2 + s;
+            const T a0 = ga[0], a1 = ga[1], a2 = ga[2], b0 = gb[0], b1 = gb[1], b2 = gb[2];
+            const T lam = cf[0], m = cf[1];
+            const T s = fma_t(a0, tb[0], fma_t(a1, tb[1], a2 * tb[2]));
+            const T la0 = lam * a0, la1 = lam * a1, la2 = lam * a2;
+            const T ma0 = m * a0, ma1 = m * a1, ma2 = m * a2;
+            Kab[0][0] = fma_t(la0, b0, fma_t(ma0, b0, Kab[0][0] + s));
+            Kab[0][1] = fma_t(la0, b1, fma_t(ma1, b0, Kab[0][1]));
+            Kab[0][2] = fma_t(la0, b2, fma_t(ma2, b0, Kab[0][2]));
+            Kab[1][0] = fma_t(la1, b0, fma_t(ma0, b1, Kab[1][0]));
+            Kab[1][1] = fma_t(la1, b1, fma_t(ma1, b1, Kab[1][1] + s));
+            Kab[1][2] = fma_t(la1, b2, fma_t(ma2, b1, Kab[1][2]));
+            Kab[2][0] = fma_t(la2, b0, fma_t(ma0, b2, Kab[2][0]));
+            Kab[2][1] = fma_t(la2, b1, fma_t(ma1, b2, Kab[2][1]));
+            Kab[2][2] = fma_t(la2, b2, fma_t(ma2, b2, Kab[2][2] + s));
+            if (R && a == b) {
+                Ra0 = fma_t(cf[2], a0, fma_t(cf[7], a1, fma_t(cf[6], a2, Ra0)));
+                Ra1 = fma_t(cf[7], a0, fma_t(cf[3], a1, fma_t(cf[5], a2, Ra1)));
+                Ra2 = fma_t(cf[6], a0, fma_t(cf[5], a1, fma_t(cf[4], a2, Ra2)));
+            }
         }
         const int32_t na = sm.node[ee][a], nb = sm.node[ee][b];
         const int64_t sbase = 64 * (int64_t)eid;
@@ -194,6 +217,12 @@ __global__ void __launch_bounds__(256) k_tangent(ElemArgs A, const double *__res
 #pragma unroll
                 for (int i = 0; i < 3; i++) dst[i] += (VT)Kab[i][k];
             }
+        } else if (R) {
+            const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
+            if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
+            R[3 * (int64_t)na] += (double)Ra0;
+            R[3 * (int64_t)na + 1] += (double)Ra1;
+            R[3 * (int64_t)na + 2] += (double)Ra2;
         }
     }
 }
@@ -319,6 +348,8 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
         residual_colours<double>(m, A, u, R, s);
     else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
         residual_colours<float>(m, A, u, R, s);
+    else if (precision == JETSCI_DF64)
+        residual_colours<df64>(m, A, u, R, s);
     else if (precision == JETSCI_SURROGATE)
         return launch_surrogate(m, u, nullptr, R, s);
     else
@@ -337,7 +368,7 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
         A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
         if (A.n == 0) continue;
         unsigned grid = (unsigned)((A.n + kTanElems - 1) / kTanElems);
-        k_tangent<T, VT><<<grid, 256, smem, s>>>(A, u, m->d_rowptr, m->d_slot, vals, R);
+        k_tangent<T, VT><<<grid, 128, smem, s>>>(A, u, m->d_rowptr, m->d_slot, vals, R);
     }
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
@@ -355,6 +386,11 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
         JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(float), s));
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
         return tangent_colours<float, float>(m, A, u, (float *)vals, R, s);
+    }
+    if (precision == JETSCI_DF64) {
+        JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(double), s));
+        if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
+        return tangent_colours<df64, double>(m, A, u, (double *)vals, R, s);
     }
     if (precision == JETSCI_TF32) return launch_tf32(m, u, nullptr, (float *)vals, R, nullptr, E_elem, s);
     if (precision == JETSCI_SURROGATE) return launch_surrogate(m, u, (float *)vals, R, s);
@@ -382,6 +418,8 @@ jetsci_status launch_apply_mf(jetsci_mesh m, const double *u, const double *v, d
         apply_colours<double>(m, A, u, v, y, s);
     else if (precision == JETSCI_FP32)
         apply_colours<float>(m, A, u, v, y, s);
+    else if (precision == JETSCI_DF64)
+        apply_colours<df64>(m, A, u, v, y, s);
     else
         return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the matrix-free product");
     JETSCI_CUDA_TRY(cudaGetLastError());
@@ -397,6 +435,8 @@ jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double 
         k_material_grad<double><<<grid, 128, 0, s>>>(A, u, R, g);
     else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
         k_material_grad<float><<<grid, 128, 0, s>>>(A, u, R, g);
+    else if (precision == JETSCI_DF64)
+        k_material_grad<df64><<<grid, 128, 0, s>>>(A, u, R, g);
     else
         return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the material gradient");
     JETSCI_CUDA_TRY(cudaGetLastError());

@@ -1,0 +1,121 @@
+// Two-float ("double-float") arithmetic: a value is the unevaluated sum hi + lo of two FP32
+// numbers with |lo| <= ulp(hi)/2, giving about 48 significant bits on the FP32 pipes.  On
+// B300 the FP64 pipe delivers 1/64 of the FP32 rate, so these operations (7-20 FP32
+// instructions each) run several times faster than native FP64 while keeping the element
+// kernels within the FP64 parity tolerance.
+//
+// Building blocks (error-free transformations):
+//   TwoSum (Knuth):       s = a + b exactly as s + e, any |a|, |b|
+//   FastTwoSum (Dekker):  same when |a| >= |b|
+//   TwoProduct (FMA):     p = a * b exactly as p + e with e = fma(a, b, -p)
+// Every FP32 operation below uses an explicit round-to-nearest intrinsic so the compiler
+// cannot contract or reorder it.  Additions are the "sloppy" variant (error bounded by
+// 2^-47 (|a| + |b|)), sufficient for the normwise error metric used by this library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace jetsci {
+
+struct df64 {
+    float h, l;
+    df64() = default;
+    __host__ __device__ constexpr df64(float hi, float lo) : h(hi), l(lo) {}
+    __host__ __device__ constexpr df64(int i) : h((float)i), l(0.0f) {}
+    __host__ __device__ constexpr df64(float f) : h(f), l(0.0f) {}
+    __host__ __device__ constexpr df64(double d) : h((float)d), l((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
+};
+
+__device__ __forceinline__ df64 fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df64 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+    df64 s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.h, -a.l); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+
+// a * b + c with one renormalisation.
+__device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    df64 s = two_sum(p, c.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(e, c.l)));
+}
+
+__device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64 &operator*=(df64 &a, df64 b) { return a = a * b; }
+
+__device__ __forceinline__ bool operator>(df64 a, df64 b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+__device__ __forceinline__ bool operator<(df64 a, df64 b) { return b > a; }
+
+__device__ __forceinline__ bool isfinite(df64 a) { return ::isfinite(a.h) && ::isfinite(a.l); }
+
+// 1/a: FP32 reciprocal refined by one Newton step x1 = x0 + x0 (1 - a x0) in two-float
+// arithmetic (quadratic convergence: 2^-24 -> about 2^-48).
+__device__ __forceinline__ df64 df_rcp(df64 a) {
+    const df64 x0(__frcp_rn(a.h), 0.0f);
+    const df64 r = df_fma(-a, x0, df64(1.0f));
+    return df_fma(x0, r, x0);
+}
+
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) { return a * df_rcp(b); }
+
+// ln x for x > 0: x = 2^k m with m in [sqrt(1/2), sqrt(2)), exact scaling of both parts;
+// ln m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...), s = (m - 1)/(m + 1), |s| <= 0.1716, so
+// s^2 <= 0.0295 and eleven terms of the series leave a truncation error below 2^-50.
+__device__ __forceinline__ df64 df_log(df64 x) {
+    int k;
+    float f = frexpf(x.h, &k);  // x.h = f 2^k, f in [0.5, 1)
+    if (f < 0.70710678f) k -= 1;
+    const df64 m(ldexpf(x.h, -k), ldexpf(x.l, -k));
+    const df64 s = (m - df64(1.0f)) * df_rcp(m + df64(1.0f));
+    const df64 z = s * s;
+    // Horner in z for sum_{j=0}^{10} z^j / (2j + 1)
+    df64 p(1.0 / 21.0);
+    p = df_fma(p, z, df64(1.0 / 19.0));
+    p = df_fma(p, z, df64(1.0 / 17.0));
+    p = df_fma(p, z, df64(1.0 / 15.0));
+    p = df_fma(p, z, df64(1.0 / 13.0));
+    p = df_fma(p, z, df64(1.0 / 11.0));
+    p = df_fma(p, z, df64(1.0 / 9.0));
+    p = df_fma(p, z, df64(1.0 / 7.0));
+    p = df_fma(p, z, df64(1.0 / 5.0));
+    p = df_fma(p, z, df64(1.0 / 3.0));
+    p = df_fma(p, z, df64(1.0f));
+    const df64 lnm = (s + s) * p;
+    const df64 ln2(0.69314718055994530942);
+    return df_fma(ln2, df64((float)k), lnm);
+}
+
+__device__ __forceinline__ df64 shfl_df(df64 v, int src, int width) {
+    return df64(__shfl_sync(0xffffffffu, v.h, src, width), __shfl_sync(0xffffffffu, v.l, src, width));
+}
+
+__device__ __forceinline__ df64 shfl_xor_df(df64 v, int mask, int width) {
+    return df64(__shfl_xor_sync(0xffffffffu, v.h, mask, width), __shfl_xor_sync(0xffffffffu, v.l, mask, width));
+}
+
+}  // namespace jetsci

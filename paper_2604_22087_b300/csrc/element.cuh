@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
 #include "jetsci_internal.h"
 
 namespace jetsci {
@@ -39,6 +40,16 @@ __device__ __forceinline__ T shfl8(T v, int src) {
 template <typename T>
 __device__ __forceinline__ T shfl_xor8(T v, int mask) {
     return __shfl_xor_sync(kFull, v, mask, 8);
+}
+
+template <>
+__device__ __forceinline__ df64 shfl8<df64>(df64 v, int src) {
+    return shfl_df(v, src, 8);
+}
+
+template <>
+__device__ __forceinline__ df64 shfl_xor8<df64>(df64 v, int mask) {
+    return shfl_xor_df(v, mask, 8);
 }
 
 // Nodal values (lane = node in binary order) -> 8 * monomial coefficient (lane = monomial).
@@ -112,9 +123,19 @@ template <>
 __device__ __forceinline__ double my_log<double>(double x) { return log(x); }
 template <>
 __device__ __forceinline__ float my_log<float>(float x) { return logf(x); }
+template <>
+__device__ __forceinline__ df64 my_log<df64>(df64 x) { return df_log(x); }
 
 template <typename T>
 __device__ __forceinline__ T my_rcp(T x) { return T(1) / x; }
+template <>
+__device__ __forceinline__ df64 my_rcp<df64>(df64 x) { return df_rcp(x); }
+
+// a * b + c in the element type (a fused multiply-add for FP64/FP32, one renormalisation
+// for two-float values).
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df64 fma_t(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
 
 // Material of element e as (law, lambda, mu) in T.
 struct ElemMaterial {

@@ -5,39 +5,46 @@
 
 namespace jetsci {
 
-// y = K v.  One warp per node: the node's three rows 3n, 3n+1, 3n+2 are contiguous in
-// the CSR arrays and share one column list (node-interleaved DOFs), so each column index
-// and each v entry is loaded once for three rows.  Each lane sums a fixed strided subset
-// and a fixed xor tree combines the lanes, so the result is reproducible.  AT is the
-// accumulation type (FP64 for FP64 values; FP32 for FP32 values, where per-entry FP64
-// conversions would run on B300's slow FP64 pipe).
+// y = K v.  Four lanes per node (eight nodes per warp): the node's three rows 3n, 3n+1,
+// 3n+2 are contiguous in the CSR arrays and share one column list (node-interleaved
+// DOFs), so each column index and each v entry is loaded once for three rows, and four
+// lanes still read whole 32-byte sectors of each row.  Each lane sums a fixed strided
+// subset and two fixed xor steps combine the lanes, so the result is reproducible.  Few
+// lanes per node keep the cross-lane reduction small: on B300 every FP64 add of a warp
+// shuffle reduction occupies the narrow FP64 pipe as much as a product does.  AT is the
+// accumulation type (FP64 for FP64 values, FP32 for FP32 values).
+constexpr int kSpmvLanes = 4;
+
 template <typename VT, typename AT>
 __global__ void __launch_bounds__(256) k_spmv(int64_t n_nodes, const int64_t *__restrict__ rowptr,
                                               const int32_t *__restrict__ col, const VT *__restrict__ vals,
                                               const double *__restrict__ v, double *__restrict__ y) {
-    const int64_t node = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (node >= n_nodes) return;  // uniform per warp
-    const int64_t r0 = rowptr[3 * node];
-    const int64_t len = rowptr[3 * node + 1] - r0;
-    const VT *v0 = vals + r0;
-    const VT *v1 = v0 + len;
-    const VT *v2 = v1 + len;
-    const int32_t *c = col + r0;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t node = gid / kSpmvLanes;
+    const int lane = (int)(gid % kSpmvLanes);
+    const bool active = node < n_nodes;
     AT s0 = 0, s1 = 0, s2 = 0;
-    for (int64_t t = lane; t < len; t += 32) {
-        const AT x = (AT)__ldg(v + __ldg(c + t));
-        s0 += (AT)__ldcs(v0 + t) * x;
-        s1 += (AT)__ldcs(v1 + t) * x;
-        s2 += (AT)__ldcs(v2 + t) * x;
+    if (active) {
+        const int64_t r0 = rowptr[3 * node];
+        const int64_t len = rowptr[3 * node + 1] - r0;
+        const VT *v0 = vals + r0;
+        const VT *v1 = v0 + len;
+        const VT *v2 = v1 + len;
+        const int32_t *c = col + r0;
+        for (int64_t t = lane; t < len; t += kSpmvLanes) {
+            const AT x = (AT)__ldg(v + __ldg(c + t));
+            s0 += (AT)__ldcs(v0 + t) * x;
+            s1 += (AT)__ldcs(v1 + t) * x;
+            s2 += (AT)__ldcs(v2 + t) * x;
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    for (int o = kSpmvLanes / 2; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o, kSpmvLanes);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o, kSpmvLanes);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o, kSpmvLanes);
     }
-    if (lane == 0) {
+    if (active && lane == 0) {
         y[3 * node] = (double)s0;
         y[3 * node + 1] = (double)s1;
         y[3 * node + 2] = (double)s2;
@@ -47,7 +54,7 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n_nodes, const int64_t *__
 jetsci_status launch_spmv(jetsci_mesh m, const void *vals, bool fp32, const double *v, double *y,
                           cudaStream_t s) {
     if (m->n_nodes == 0) return JETSCI_OK;
-    unsigned grid = (unsigned)((m->n_nodes * 32 + 255) / 256);
+    unsigned grid = (unsigned)((m->n_nodes * kSpmvLanes + 255) / 256);
     if (fp32)
         k_spmv<float, float><<<grid, 256, 0, s>>>(m->n_nodes, m->d_rowptr, m->d_col, (const float *)vals, v, y);
     else

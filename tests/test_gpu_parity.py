@@ -297,3 +297,34 @@ def test_newton_cg_jacobi_converges_to_oracle_solution(tp):
     assert info.newton_iters <= (6 if tp == "fp64" else 12)
     u_ref = _oracle_newton(prob, dofs, vals)
     assert relerr(u.cpu().numpy(), u_ref) <= 1e-8
+
+
+def test_df64_two_float_path_meets_the_fp64_tolerance(case):
+    """Two-float arithmetic (about 48 significant bits) on the FP32 pipes: the same 1e-12
+    normwise bar as the FP64 path."""
+    prob, mesh, om, ref = case
+    J = jetsci()
+    u, v = cuda(prob.u), cuda(prob.v)
+    R = mesh.residual(u, precision=J.DF64)
+    assert relerr(R.cpu().numpy(), ref["R"]) <= FP64_TOL
+    R2 = mesh.new_vector()
+    vals = mesh.tangent_csr(u, R=R2, precision=J.DF64)
+    assert vals.dtype == torch.float64
+    assert relerr(vals.cpu().numpy(), ref["vals"]) <= FP64_TOL
+    assert relerr(R2.cpu().numpy(), ref["R"]) <= FP64_TOL
+    y = mesh.apply_tangent(u, v, precision=J.DF64)
+    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= FP64_TOL
+    assert mesh.check() == 0
+
+
+def test_df64_material_gradient():
+    prob = I.lognormal_problem(12, seed=4)
+    J = jetsci()
+    mesh = J.Mesh.of(prob)
+    om = oracle.Mesh.of(prob)
+    u, E = cuda(prob.u), cuda(prob.E_elem)
+    R = mesh.residual(u, E_elem=E, precision=J.DF64)
+    R_ref = oracle.residual(om, prob.u)
+    assert relerr(R.cpu().numpy(), R_ref) <= FP64_TOL
+    g = mesh.material_grad(u, R, E_elem=E, precision=J.DF64)
+    assert relerr(g.cpu().numpy(), oracle.material_grad(om, prob.u, R_ref)) <= FP64_TOL
