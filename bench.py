@@ -35,12 +35,14 @@ sys.path.insert(0, ROOT)
 METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % of HBM peak"
 
 # Work per element of the dominant kernel, k_tangent<double,double> (derivation in the design doc):
-# executed FP64 operations of the formulation (ncu: dfma x2 + dadd + dmul per element) and the
+# executed FP64 operations of the formulation (ncu: 8,800 DFMA x 2 + 1,960 DADD + 3,584 DMUL per
+# element) and the
 # algorithmic bytes (write-once CSR values + mesh data + u + R).
-TANGENT_FP64_FLOP_PER_ELEM = 28_580.0
+TANGENT_FP64_FLOP_PER_ELEM = 23_144.0
 TANGENT_BYTES_PER_ELEM_FP64 = 2_160.0
-# Executed FP64 operations per element of k_apply_mf<double> and k_residual<double> (ncu).
-SPMV_BYTES_PER_NNZ_FP64 = 12.0
+# Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
+# index (a node's three rows share one column list); v and y are per-row and stay in L2.
+SPMV_BYTES_PER_NNZ = {"fp64": 8.0 + 4.0 / 3.0, "fp32": 4.0 + 4.0 / 3.0}
 
 
 def parse():
@@ -525,7 +527,7 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
         if p in (J.FP64, J.FP32):
             ms = timeit(lambda: mesh.apply_tangent(None, v, y=y, mode=J.CSR, vals=vv, precision=p, stream=stream), stream)
             torch.cuda.synchronize()
-            gbs = (SPMV_BYTES_PER_NNZ_FP64 if p == J.FP64 else 8.0) * mesh.nnz / (ms * 1e-3) / 1e9
+            gbs = SPMV_BYTES_PER_NNZ[name] * mesh.nnz / (ms * 1e-3) / 1e9
             rec(f"spmv_csr_{name}", ms, {"err_vs_oracle": so.errors(None, None, gather_rows(y, so.nodes), rp_h, col_h),
                                          "algorithmic_gbs": gbs})
         if p not in (J.FP64, J.DF64):

@@ -1,15 +1,17 @@
 // Element residual and tangent with the MLP surrogate fused into the element kernel.
 //
-// One CTA = 16 elements x 8 Gauss points = one 128-point tile.  Phase 1 (thread = Gauss
-// point, FP32): kinematics, Green-Lagrange strain E = 1/2 (F^T F - I), surrogate inputs.
-// Phase 2: the MLP forward and input-Jacobian pass on the tensor cores (BF16, FP32
-// accumulate in TMEM) gives S and D = dS/dE; points with any |E_ij| > range take S and D of
-// the plain neo-Hookean law instead.  Phase 3a (thread = Gauss point): residual
-// contribution and, per node b, B_b = dE/du_b (Voigt, tensor components), c W D and c S
-// (c = w detJ, W = diag(1,1,1,2,2,2)) into shared memory.  Phase 3b (thread = element node
-// a): K_ab = sum_q [ B_a^T (c W D) B_b + (G_a . c S G_b) I ], the consistent tangent
-// sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL written with the Voigt
-// tangent; it is not symmetric for the surrogate, so all 64 node pairs are formed.
+// One CTA = 16 elements x 8 Gauss points = one 128-point tile (two CTAs per SM).  Phase 1
+// (thread = Gauss point, FP32): kinematics, Green-Lagrange strain E = 1/2 (F^T F - I),
+// surrogate inputs.  Phase 2: the MLP forward and input-Jacobian pass on the tensor cores
+// (BF16, FP32 accumulate in TMEM) gives S and D = dS/dE; points with any |E_ij| > range take
+// S and D of the plain neo-Hookean law instead.  Phase 3a (thread = Gauss point): residual
+// contribution, and F, G_b (all nodes), c W D and c S (c = w detJ, W = diag(1,1,1,2,2,2))
+// into shared memory.  Phase 3b (thread = element node a):
+//   K_ab = sum_q [ B_a^T (c W D) B_b + (G_a . c S G_b) I ]
+// with B_b = dE/du_b (Voigt, tensor components, B_b[v][k] = sym(F_k (x) G_b)_v), evaluated as
+// K_ab[i][k] += (F Y_i G_b)_k where Y_i is the symmetric 3x3 form of row i of B_a^T (c W D).
+// This is the consistent tangent sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL
+// with the Voigt tangent; it is not symmetric for the surrogate, so all 64 node pairs are formed.
 #include <cuda_runtime.h>
 
 #include "element.cuh"
@@ -33,35 +35,33 @@ struct SurArgs {
     const int32_t *__restrict__ elems;
     int64_t n;
     uint32_t *flags;
-    uint32_t *fallback_count;  // number of Gauss points that used the plain law (may be NULL)
+    uint32_t *fallback_count;  // Gauss points that used the plain law (may be NULL)
 };
 
-// Per-point phase-3 record in the (reused) activation / tangent region of the tile smem.
+// Per-point phase-3 record, in the (reused) input / activation / tangent region of the tile.
 struct PointRec {
+    float F[3][3];
     float G[8][3];
-    float B[8][6][3];
     float cWD[6][6];
     float cS[6];
 };
-static_assert(sizeof(PointRec) * 128 <= 128 * 16 * 2 + 128 * 64 * 2 + 6 * 128 * 64 * 2, "phase-3 records do not fit");
+static_assert(sizeof(PointRec) * 128 <= 128 * 16 * 2 + 128 * 64 * 2 + 3 * 128 * 64 * 2, "phase-3 records do not fit");
 
-__constant__ int8_t kVoigtI[6] = {0, 1, 2, 1, 0, 0};
-__constant__ int8_t kVoigtJ[6] = {0, 1, 2, 2, 2, 1};
 
 template <bool TANGENT>
-__global__ void __launch_bounds__(128) k_elem_surrogate(SurArgs A, const double *__restrict__ u,
-                                                        const unsigned char *__restrict__ img,
-                                                        const float *__restrict__ params, SurrogateConfig cfg,
-                                                        const int64_t *__restrict__ rowptr,
-                                                        const uint8_t *__restrict__ slotmap, float *__restrict__ vals,
-                                                        double *__restrict__ R) {
+__global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const double *__restrict__ u,
+                                                           const unsigned char *__restrict__ img,
+                                                           const float *__restrict__ params, SurrogateConfig cfg,
+                                                           const int64_t *__restrict__ rowptr,
+                                                           const uint8_t *__restrict__ slotmap,
+                                                           float *__restrict__ vals, double *__restrict__ R) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpTileSmem &sm = *reinterpret_cast<MlpTileSmem *>(smem_raw);
     __shared__ int32_t s_node[16][8];
     __shared__ int32_t s_elem[16];
     const int t = threadIdx.x;
     const int l = t & 7, es = t >> 3;
-    if (t < 32) tc::tmem_alloc(&sm.tmem_base, 512);
+    if (t < 32) tc::tmem_alloc(&sm.tmem_base, kMlpTmemCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
         tc::fence_mbar_init();
@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(128) k_elem_surrogate(SurArgs A, const double 
     GaussKinematics<float> K;
     float cu[3];
     gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
-    const Material mt = A.mats[A.phase[e]];
-    int ph = A.phase[e];
+    const int ph = A.phase[e];
+    const Material mt = A.mats[ph];
     float F[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -85,38 +85,38 @@ __global__ void __launch_bounds__(128) k_elem_surrogate(SurArgs A, const double 
     float E6[6];
 #pragma unroll
     for (int a = 0; a < 6; a++) {
-        const int I = kVoigtI[a], Jj = kVoigtJ[a];
-        float c = F[0][I] * F[0][Jj] + F[1][I] * F[1][Jj] + F[2][I] * F[2][Jj];
+        const int I = voigt_i(a), Jj = voigt_j(a);
+        const float c = F[0][I] * F[0][Jj] + F[1][I] * F[1][Jj] + F[2][I] * F[2][Jj];
         E6[a] = 0.5f * (c - (I == Jj ? 1.0f : 0.0f));
     }
     bool in_range = ph == 0 || ph == 1;
 #pragma unroll
     for (int a = 0; a < 6; a++) in_range = in_range && fabsf(E6[a]) <= cfg.range;
+    {
+        float xv[16];
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-        float xv = 0.0f;
-        if (k < 6) xv = E6[k] / cfg.in_scale;
-        if (k == 6) xv = ph == 0 ? 1.0f : 0.0f;
-        if (k == 7) xv = ph == 1 ? 1.0f : 0.0f;
-        tc::st_bf16(sm.x, t, k, 16, xv);
+        for (int k = 0; k < 16; k++) xv[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 6; k++) xv[k] = E6[k] / cfg.in_scale;
+        xv[6] = ph == 0 ? 1.0f : 0.0f;
+        xv[7] = ph == 1 ? 1.0f : 0.0f;
+        st_bf16x8(sm.x, t, 0, 16, xv);
+        st_bf16x8(sm.x, t, 1, 16, xv + 8);
     }
     s_node[es][hex_node_of_lane(l)] = node;
     if (l == 0) s_elem[es] = active ? (int32_t)e : -1;
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
     // ---------------- phase 2
     uint32_t phase_ctr = 0;
     float y[6], Jm[6][6];
-    bool ok = mlp_forward_jacobian(sm, phase_ctr, y, Jm);
+    const bool ok = mlp_forward_jacobian(sm, phase_ctr, y, Jm);
     float S[6], D[6][6];
     bool ok_state = true;
     const int phs = ph == 1 ? 1 : 0;
     if (in_range) {
 #pragma unroll
         for (int c = 0; c < 6; c++) {
-            const float sc = cfg.out_scale[phs][c];
-            S[c] = y[c] * sc + cfg.out_shift[phs][c];
+            const float sc = phs ? cfg.out_scale[1][c] : cfg.out_scale[0][c];
+            S[c] = y[c] * sc + (phs ? cfg.out_shift[1][c] : cfg.out_shift[0][c]);
 #pragma unroll
             for (int d = 0; d < 6; d++) D[c][d] = Jm[c][d] * sc / cfg.in_scale;
         }
@@ -142,64 +142,62 @@ __global__ void __launch_bounds__(128) k_elem_surrogate(SurArgs A, const double 
         const float m = mu - lam * lnJ;
 #pragma unroll
         for (int a = 0; a < 6; a++) {
-            const int I = kVoigtI[a], Jj = kVoigtJ[a];
+            const int I = voigt_i(a), Jj = voigt_j(a);
             S[a] = (lam * lnJ - mu) * Ci[I][Jj] + (I == Jj ? mu : 0.0f);
 #pragma unroll
             for (int b = 0; b < 6; b++) {
-                const int Kk = kVoigtI[b], L = kVoigtJ[b];
-                float v = lam * Ci[I][Jj] * Ci[Kk][L] + m * (Ci[I][Kk] * Ci[Jj][L] + Ci[I][L] * Ci[Jj][Kk]);
+                const int Kk = voigt_i(b), L = voigt_j(b);
+                const float v = lam * Ci[I][Jj] * Ci[Kk][L] + m * (Ci[I][Kk] * Ci[Jj][L] + Ci[I][L] * Ci[Jj][Kk]);
                 D[a][b] = (Kk == L) ? v : 2.0f * v;
             }
         }
         if (active && A.fallback_count) atomicAdd(A.fallback_count, 1u);
     }
     // ---------------- phase 3a: residual and per-point records
-    float Smat[3][3] = {{S[0], S[5], S[4]}, {S[5], S[1], S[3]}, {S[4], S[3], S[2]}};
-    float P[3][3];
+    {
+        const float Smat[3][3] = {{S[0], S[5], S[4]}, {S[5], S[1], S[3]}, {S[4], S[3], S[2]}};
+        float P[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int J2 = 0; J2 < 3; J2++) P[i][J2] = F[i][0] * Smat[0][J2] + F[i][1] * Smat[1][J2] + F[i][2] * Smat[2][J2];
-    float f[3];
-    nodal_force(P, K, l, f);
-    if (active) {
-        uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok_state ? 0u : JETSCI_FLAG_BAD_STATE) |
-                        (isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]) ? 0u : JETSCI_FLAG_NONFINITE) |
-                        (ok ? 0u : JETSCI_FLAG_NONFINITE);
-        if (bits) atomicOr(A.flags, bits);
-        if (R)
+            for (int J2 = 0; J2 < 3; J2++)
+                P[i][J2] = F[i][0] * Smat[0][J2] + F[i][1] * Smat[1][J2] + F[i][2] * Smat[2][J2];
+        float f[3];
+        nodal_force(P, K, l, f);
+        if (active) {
+            const uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok_state ? 0u : JETSCI_FLAG_BAD_STATE) |
+                                  (isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]) ? 0u : JETSCI_FLAG_NONFINITE) |
+                                  (ok ? 0u : JETSCI_FLAG_NONFINITE);
+            if (bits) atomicOr(A.flags, bits);
+            if (R)
 #pragma unroll
-            for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
+                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
+        }
     }
     if (!TANGENT) {
         tc::fence_before_sync();
         __syncthreads();
-        if (t < 32) tc::tmem_dealloc(sm.tmem_base, 512);
+        if (t < 32) tc::tmem_dealloc(sm.tmem_base, kMlpTmemCols);
         return;
     }
-    __syncthreads();  // all MLP tiles consumed: the region becomes the point records
+    __syncthreads();  // every MLP tile consumed: the region becomes the point records
     PointRec *rec = reinterpret_cast<PointRec *>(sm.x);
-    PointRec &me = rec[t];
     {
+        PointRec &me = rec[t];
         const float rdJ = 1.0f / K.dJ;
         const float c = K.dJ * (1.0f / 512.0f);
 #pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) me.F[i][j] = F[i][j];
+#pragma unroll
         for (int a = 0; a < 8; a++) {
-            const int nb = hex_node_of_lane(a);  // the map is an involution: also node -> sign bits
+            const int nb = hex_node_of_lane(a);  // the map is an involution: node -> sign bits
             const float s0 = (nb & 1) ? 1.0f : -1.0f, s1 = (nb & 2) ? 1.0f : -1.0f, s2 = (nb & 4) ? 1.0f : -1.0f;
             const float fx = 1.0f + s0 * K.xi, fy = 1.0f + s1 * K.eta, fz = 1.0f + s2 * K.zeta;
             const float n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
-            float G[3];
 #pragma unroll
-            for (int j = 0; j < 3; j++) G[j] = (K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2) * rdJ;
-#pragma unroll
-            for (int j = 0; j < 3; j++) me.G[a][j] = G[j];
-#pragma unroll
-            for (int v = 0; v < 6; v++) {
-                const int I = kVoigtI[v], Jj = kVoigtJ[v];
-#pragma unroll
-                for (int i = 0; i < 3; i++) me.B[a][v][i] = 0.5f * (F[i][I] * G[Jj] + F[i][Jj] * G[I]);
-            }
+            for (int j = 0; j < 3; j++) me.G[a][j] = (K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2) * rdJ;
         }
 #pragma unroll
         for (int v = 0; v < 6; v++) {
@@ -211,7 +209,7 @@ __global__ void __launch_bounds__(128) k_elem_surrogate(SurArgs A, const double 
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (t < 32) tc::tmem_dealloc(sm.tmem_base, 512);
+    if (t < 32) tc::tmem_dealloc(sm.tmem_base, kMlpTmemCols);
     // ---------------- phase 3b: thread = (element es, node a = l)
     const int32_t eid = s_elem[es];
     if (eid < 0) return;
@@ -223,34 +221,57 @@ __global__ void __launch_bounds__(128) k_elem_surrogate(SurArgs A, const double 
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int k = 0; k < 3; k++) Kab[b][i][k] = 0.0f;
+#pragma unroll 1
     for (int q = 0; q < 8; q++) {
         const PointRec &r = rec[8 * es + q];
-        float Y[3][6];
+        float Fq[3][3], ga[3];
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 3; i++) {
+            ga[i] = r.G[a][i];
 #pragma unroll
-            for (int bb = 0; bb < 6; bb++) {
-                float s = 0.0f;
+            for (int j = 0; j < 3; j++) Fq[i][j] = r.F[i][j];
+        }
+        // B_a[v][i] (Voigt tensor component v of sym(F_i (x) G_a))
+        float Ba[6][3];
 #pragma unroll
-                for (int v = 0; v < 6; v++) s += r.B[a][v][i] * r.cWD[v][bb];
-                Y[i][bb] = s;
+        for (int v = 0; v < 6; v++) {
+            const int I = voigt_i(v), Jj = voigt_j(v);
+#pragma unroll
+            for (int i = 0; i < 3; i++) Ba[v][i] = 0.5f * (Fq[i][I] * ga[Jj] + Fq[i][Jj] * ga[I]);
+        }
+        // M_i = F Yhat_i with Yhat_i the symmetric form of Y_i = B_a^T (c W D) row i
+        float M[3][3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            float Y[6];
+#pragma unroll
+            for (int w = 0; w < 6; w++) {
+                float sacc = 0.0f;
+#pragma unroll
+                for (int v = 0; v < 6; v++) sacc += Ba[v][i] * r.cWD[v][w];
+                Y[w] = sacc;
             }
-        const float ga0 = r.G[a][0], ga1 = r.G[a][1], ga2 = r.G[a][2];
-        const float sg0 = r.cS[0] * ga0 + r.cS[5] * ga1 + r.cS[4] * ga2;
-        const float sg1 = r.cS[5] * ga0 + r.cS[1] * ga1 + r.cS[3] * ga2;
-        const float sg2 = r.cS[4] * ga0 + r.cS[3] * ga1 + r.cS[2] * ga2;
+            const float Yh[3][3] = {{Y[0], 0.5f * Y[5], 0.5f * Y[4]},
+                                    {0.5f * Y[5], Y[1], 0.5f * Y[3]},
+                                    {0.5f * Y[4], 0.5f * Y[3], Y[2]}};
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+#pragma unroll
+                for (int J2 = 0; J2 < 3; J2++)
+                    M[i][k][J2] = Fq[k][0] * Yh[0][J2] + Fq[k][1] * Yh[1][J2] + Fq[k][2] * Yh[2][J2];
+        }
+        const float sg0 = r.cS[0] * ga[0] + r.cS[5] * ga[1] + r.cS[4] * ga[2];
+        const float sg1 = r.cS[5] * ga[0] + r.cS[1] * ga[1] + r.cS[3] * ga[2];
+        const float sg2 = r.cS[4] * ga[0] + r.cS[3] * ga[1] + r.cS[2] * ga[2];
 #pragma unroll
         for (int b = 0; b < 8; b++) {
-            const float geo = sg0 * r.G[b][0] + sg1 * r.G[b][1] + sg2 * r.G[b][2];
+            const float g0 = r.G[b][0], g1 = r.G[b][1], g2 = r.G[b][2];
+            const float geo = sg0 * g0 + sg1 * g1 + sg2 * g2;
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    float s = (i == k) ? geo : 0.0f;
-#pragma unroll
-                    for (int v = 0; v < 6; v++) s += Y[i][v] * r.B[b][v][k];
-                    Kab[b][i][k] += s;
-                }
+                for (int k = 0; k < 3; k++)
+                    Kab[b][i][k] += M[i][k][0] * g0 + M[i][k][1] * g1 + M[i][k][2] * g2 + (i == k ? geo : 0.0f);
         }
     }
     const int32_t na = s_node[es][a];
@@ -290,10 +311,9 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
     if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     JETSCI_CUDA_TRY(cudaMemsetAsync(m->d_fallback, 0, sizeof(uint32_t), s));
     const SurrogateConfig cfg = surrogate_config(sg);
-    for (int c = 0; c < m->n_colours; c++) {
-        A.elems = m->d_colour_elems + m->colour_ptr[c];
-        A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
-        if (A.n == 0) continue;
+    for_colour_chunks(m, 1, [&](const int32_t *elems, int64_t n) {
+        A.elems = elems;
+        A.n = n;
         unsigned grid = (unsigned)((A.n + 15) / 16);
         if (vals)
             k_elem_surrogate<true><<<grid, 128, smem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
@@ -301,7 +321,7 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
         else
             k_elem_surrogate<false><<<grid, 128, smem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
                                                             m->d_rowptr, m->d_slot, nullptr, R);
-    }
+    });
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
 }

@@ -19,8 +19,14 @@ namespace jetsci {
 constexpr int kTfElems = 16;           // elements per CTA (8 Gauss points each = 128 threads)
 constexpr int kTfGroups = 4;           // MMA groups of 4 elements
 constexpr int kTfK = 48;               // 8 Gauss points x 6 Voigt components
-constexpr int kTfATile = 128 * kTfK * 4;  // bytes, rows 96..127 zero
-constexpr int kTfBTile = 96 * kTfK * 4;
+// Operand tiles use padded core-matrix strides: 144 B between core matrices along K (16 B of
+// padding) and 12 x 144 B between 8-row blocks.  With the fill pattern below (four elements x
+// eight Gauss points per warp, one 4-byte store per lane) this leaves at most 2-way shared-
+// memory bank conflicts instead of 16-way with the dense 128 B / 1536 B strides.
+constexpr uint32_t kTfLBO = 144;
+constexpr uint32_t kTfSBO = (kTfK / 4) * kTfLBO;
+constexpr int kTfATile = 16 * kTfSBO;  // 128 rows (rows 96..127 zero)
+constexpr int kTfBTile = 12 * kTfSBO;  // 96 rows
 
 struct __align__(128) Tf32Smem {
     unsigned char A[kTfGroups][kTfATile];
@@ -35,7 +41,7 @@ struct __align__(128) Tf32Smem {
 
 __device__ __forceinline__ uint32_t tf32_offset(int r, int k) {
     // K-major core matrices of 8 rows x 16 bytes (4 x 32-bit); 12 core matrices along K = 48
-    return (uint32_t)((((r >> 3) * (kTfK / 4)) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+    return (uint32_t)((r >> 3) * kTfSBO + (k >> 2) * kTfLBO + (r & 7) * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -44,8 +50,6 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-__constant__ int8_t kVI[6] = {0, 1, 2, 1, 0, 0};
-__constant__ int8_t kVJ[6] = {0, 1, 2, 2, 2, 1};
 
 struct Tf32Args {
     const int32_t *__restrict__ conn;
@@ -118,10 +122,10 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
                 Ci[I][Kk] = c.Fi[I][0] * c.Fi[Kk][0] + c.Fi[I][1] * c.Fi[Kk][1] + c.Fi[I][2] * c.Fi[Kk][2];
 #pragma unroll
         for (int a = 0; a < 6; a++) {
-            const int I = kVI[a], Jj = kVJ[a];
+            const int I = voigt_i(a), Jj = voigt_j(a);
 #pragma unroll
             for (int b = 0; b < 6; b++) {
-                const int Kk = kVI[b], L = kVJ[b];
+                const int Kk = voigt_i(b), L = voigt_j(b);
                 float w = c.lam * Ci[I][Jj] * Ci[Kk][L] + c.m * (Ci[I][Kk] * Ci[Jj][L] + Ci[I][L] * Ci[Jj][Kk]);
                 D[a][b] = (Kk == L) ? w : 2.0f * w;
             }
@@ -130,11 +134,11 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     const float cw = K.dJ * (1.0f / 512.0f);
     const float rdJ = 1.0f / K.dJ;
 #pragma unroll
-    for (int a = 0; a < 6; a++) sm.cS[es][l][a] = lin ? 0.0f : cw * c.S[kVI[a]][kVJ[a]];
+    for (int a = 0; a < 6; a++) sm.cS[es][l][a] = lin ? 0.0f : cw * c.S[voigt_i(a)][voigt_j(a)];
     // B_b and Z_b = c W D B_b for every node b, written at k = 6q + alpha
     unsigned char *At = sm.A[grp];
     unsigned char *Bt = sm.B[grp];
-#pragma unroll 1
+#pragma unroll
     for (int b = 0; b < 8; b++) {
         const int nb = hex_node_of_lane(b);
         const float s0 = (nb & 1) ? 1.0f : -1.0f, s1 = (nb & 2) ? 1.0f : -1.0f, s2 = (nb & 4) ? 1.0f : -1.0f;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         float Bb[6][3];
 #pragma unroll
         for (int a = 0; a < 6; a++) {
-            const int I = kVI[a], Jj = kVJ[a];
+            const int I = voigt_i(a), Jj = voigt_j(a);
 #pragma unroll
             for (int i = 0; i < 3; i++) Bb[a][i] = 0.5f * (c.F[i][I] * G[Jj] + c.F[i][Jj] * G[I]);
         }
@@ -175,12 +179,12 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     const uint32_t tm = sm.tmem_base;
     if (t == 0) {
         const uint32_t id = tc::idesc_tf32(128, 96);
-        const uint32_t sboA = (kTfK / 4) * 128u, sboB = (kTfK / 4) * 128u;
         for (int g = 0; g < kTfGroups; g++) {
             const uint32_t a0 = tc::smem_addr(sm.A[g]), b0 = tc::smem_addr(sm.B[g]);
+            // one MMA of K = 8 covers two core matrices along K
             for (int kk = 0; kk < kTfK / 8; kk++)
-                tc::mma_tf32(tm + 96 * g, tc::smem_desc(a0 + kk * 256u, 128u, sboA),
-                             tc::smem_desc(b0 + kk * 256u, 128u, sboB), id, kk > 0 ? 1u : 0u);
+                tc::mma_tf32(tm + 96 * g, tc::smem_desc(a0 + kk * 2 * kTfLBO, kTfLBO, kTfSBO),
+                             tc::smem_desc(b0 + kk * 2 * kTfLBO, kTfLBO, kTfSBO), id, kk > 0 ? 1u : 0u);
         }
     }
     uint32_t ph = 0;
@@ -226,7 +230,10 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
 #pragma unroll
             for (int b = 0; b < 8; b++) {
                 const float *gb = sm.G[ee][q][b];
-                rowv[3 * b + i] += sg0 * gb[0] + sg1 * gb[1] + sg2 * gb[2];
+                const float geo = sg0 * gb[0] + sg1 * gb[1] + sg2 * gb[2];
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    if (k == i) rowv[3 * b + k] += geo;  // compile-time index, predicated
             }
         }
         const int32_t na = sm.node[ee][a];
@@ -273,16 +280,15 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
         JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     }
-    for (int c = 0; c < m->n_colours; c++) {
-        A.elems = m->d_colour_elems + m->colour_ptr[c];
-        A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
-        if (A.n == 0) continue;
+    for_colour_chunks(m, 1, [&](const int32_t *elems, int64_t n) {
+        A.elems = elems;
+        A.n = n;
         unsigned grid = (unsigned)((A.n + kTfElems - 1) / kTfElems);
         if (vals)
             k_tf32<0><<<grid, 128, smem, s>>>(A, u, nullptr, m->d_rowptr, m->d_slot, vals, R, nullptr);
         else
             k_tf32<1><<<grid, 128, smem, s>>>(A, u, v, m->d_rowptr, m->d_slot, nullptr, nullptr, y);
-    }
+    });
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
 }

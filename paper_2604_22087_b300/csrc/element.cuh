@@ -27,6 +27,11 @@ namespace jetsci {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Voigt component a in [11, 22, 33, 23, 13, 12] -> tensor indices (I, J); constexpr so that
+// unrolled loops index register arrays with compile-time indices.
+__host__ __device__ constexpr int voigt_i(int a) { return a == 1 ? 1 : a == 2 ? 2 : a == 3 ? 1 : 0; }
+__host__ __device__ constexpr int voigt_j(int a) { return a == 0 ? 0 : a == 1 ? 1 : a == 5 ? 1 : 2; }
+
 __device__ __forceinline__ int hex_node_of_lane(int l) {
     // binary (xi, eta, zeta) bit pattern -> hex8 local node number
     return (0x67542310 >> (4 * l)) & 0xF;

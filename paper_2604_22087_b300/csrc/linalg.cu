@@ -33,9 +33,9 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n_nodes, const int64_t *__
         const int32_t *c = col + r0;
         for (int64_t t = lane; t < len; t += kSpmvLanes) {
             const AT x = (AT)__ldg(v + __ldg(c + t));
-            s0 += (AT)__ldcs(v0 + t) * x;
-            s1 += (AT)__ldcs(v1 + t) * x;
-            s2 += (AT)__ldcs(v2 + t) * x;
+            s0 += (AT)__ldg(v0 + t) * x;
+            s1 += (AT)__ldg(v1 + t) * x;
+            s2 += (AT)__ldg(v2 + t) * x;
         }
     }
 #pragma unroll

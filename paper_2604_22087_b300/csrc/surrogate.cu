@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128) k_mlp_eval(const unsigned char *__restric
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpTileSmem &sm = *reinterpret_cast<MlpTileSmem *>(smem_raw);
     const int t = threadIdx.x;
-    if (t < 32) tc::tmem_alloc(&sm.tmem_base, 512);
+    if (t < 32) tc::tmem_alloc(&sm.tmem_base, kMlpTmemCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
         tc::fence_mbar_init();
@@ -363,8 +363,8 @@ __global__ void __launch_bounds__(128) k_mlp_eval(const unsigned char *__restric
     if (active) {
 #pragma unroll
         for (int c = 0; c < 6; c++) {
-            const float sc = cfg.out_scale[ph][c];
-            S6[6 * i + c] = (double)(y[c] * sc + cfg.out_shift[ph][c]);
+            const float sc = ph ? cfg.out_scale[1][c] : cfg.out_scale[0][c];
+            S6[6 * i + c] = (double)(y[c] * sc + (ph ? cfg.out_shift[1][c] : cfg.out_shift[0][c]));
             if (D36)
 #pragma unroll
                 for (int d = 0; d < 6; d++) D36[36 * i + 6 * c + d] = (double)(Jm[c][d] * sc / cfg.in_scale);
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(128) k_mlp_eval(const unsigned char *__restric
     if (!ok && t == 0) atomicOr(err, 1u);
     tc::fence_before_sync();
     __syncthreads();
-    if (t < 32) tc::tmem_dealloc(sm.tmem_base, 512);
+    if (t < 32) tc::tmem_dealloc(sm.tmem_base, kMlpTmemCols);
 }
 
 }  // namespace jetsci

@@ -42,12 +42,17 @@ __device__ __forceinline__ float silu_prime_f(float z) {
     return s * (1.0f + z * (1.0f - s));
 }
 
-// Shared-memory workspace of one 128-point tile for the forward + input-Jacobian pass.
+// Shared-memory workspace of one 128-point tile for the forward + input-Jacobian pass.  The
+// six Jacobian directions run in two rounds of three (the forward pass is recomputed in the
+// second round), so a tile needs 256 TMEM columns and about 91 KB of shared memory and two
+// CTAs fit on one SM.
+constexpr int kMlpTmemCols = 256;
+
 struct __align__(128) MlpTileSmem {
     unsigned char w[kImgFwdBytes];       // W1p, W2, W3, W4p
     unsigned char x[128 * 16 * 2];       // inputs [128][16]
     unsigned char act[128 * 64 * 2];     // activations [128][64]
-    unsigned char tan[6][128 * 64 * 2];  // tangent rows per input direction [128][64]
+    unsigned char tan[3][128 * 64 * 2];  // tangent rows of the round's three directions
     float b[3][64];
     float b4[8];
     float w1[64][8];                     // FP32 W1 (tangent seeds)
@@ -71,6 +76,21 @@ __device__ __forceinline__ void mlp_load_weights(MlpTileSmem &sm, const unsigned
     for (int i = t; i < 512; i += blockDim.x) sm.w1[i >> 3][i & 7] = params[kOffW1 + i];
 }
 
+// Stores 8 consecutive values (columns 8*c8 .. 8*c8+7 of row r) as one 16-byte core-matrix
+// row; a quarter-warp's eight rows then cover 128 contiguous bytes (no bank conflicts).
+__device__ __forceinline__ void st_bf16x8(unsigned char *tile, int r, int c8, int K, const float *v) {
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
+    uint4 q;
+    q.x = *reinterpret_cast<uint32_t *>(&p0);
+    q.y = *reinterpret_cast<uint32_t *>(&p1);
+    q.z = *reinterpret_cast<uint32_t *>(&p2);
+    q.w = *reinterpret_cast<uint32_t *>(&p3);
+    *reinterpret_cast<uint4 *>(tile + tc::core_offset(r, 8 * c8, K)) = q;
+}
+
 // Commits the MMAs issued by thread 0 and waits (all threads) with a bound.  `phase` is a
 // per-thread copy of the mbarrier's completed-phase count, advanced in lockstep by every
 // thread.  Returns false on timeout.
@@ -82,6 +102,13 @@ __device__ __forceinline__ bool mma_sync_bounded(uint64_t *mbar, uint32_t &phase
     return ok;
 }
 
+__device__ __forceinline__ void smem_to_tensor_sync() {
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
 // Runs the forward and input-Jacobian pass for the tile whose inputs are already in sm.x
 // (row t = point t).  On return thread t holds y[6] (normalised outputs) and Jm[6][6]
 // (dy/dx, column d = input direction d).  Returns false if a tensor-core wait timed out.
@@ -89,70 +116,73 @@ __device__ inline bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, fl
     const int t = threadIdx.x;
     const uint32_t tm = sm.tmem_base;
     bool ok = true;
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // layer 1: z1 = x W1^T (K = 16, zero-padded)
-    if (t == 0) tc::gemm_bf16_128xN(tm, sm.x, sm.w + kImgW1, 64, 16);
-    ok = mma_sync_bounded(&sm.mbar, phase) && ok;
-    for (int layer = 0; layer < 3; layer++) {
-        // epilogue of layer `layer`: activation and tangent rows
-        float s[64];
+#pragma unroll 1
+    for (int round = 0; round < 2; round++) {
+        smem_to_tensor_sync();
+        // layer 1: z1 = x W1^T (K = 16, zero-padded)
+        if (t == 0) tc::gemm_bf16_128xN(tm, sm.x, sm.w + kImgW1, 64, 16);
+        ok = mma_sync_bounded(&sm.mbar, phase) && ok;
+#pragma unroll 1
+        for (int layer = 0; layer < 3; layer++) {
+            // epilogue of layer `layer`: activation, silu' and the three tangent rows
+            float s[64];
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-            float z[16];
-            tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float z[16], a[16];
+                tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                float zz = z[j] + sm.b[layer][c0 + j];
-                s[c0 + j] = silu_prime_f(zz);
-                tc::st_bf16(sm.act, t, c0 + j, 64, silu_f(zz));
+                for (int j = 0; j < 16; j++) {
+                    const float zz = z[j] + sm.b[layer][c0 + j];
+                    s[c0 + j] = silu_prime_f(zz);
+                    a[j] = silu_f(zz);
+                }
+                st_bf16x8(sm.act, t, c0 / 8, 64, a);
+                st_bf16x8(sm.act, t, c0 / 8 + 1, 64, a + 8);
             }
-        }
-        if (layer == 0) {
 #pragma unroll
-            for (int d = 0; d < 6; d++)
-#pragma unroll 8
-                for (int j = 0; j < 64; j++) tc::st_bf16(sm.tan[d], t, j, 64, s[j] * sm.w1[j][d]);
-        } else {
-#pragma unroll
-            for (int d = 0; d < 6; d++) {
+            for (int dl = 0; dl < 3; dl++) {
+                const int d = 3 * round + dl;
 #pragma unroll
                 for (int c0 = 0; c0 < 64; c0 += 16) {
-                    float uu[16];
-                    tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (d + 1) + c0), uu);
+                    float u[16];
+                    if (layer == 0) {
 #pragma unroll
-                    for (int j = 0; j < 16; j++) tc::st_bf16(sm.tan[d], t, c0 + j, 64, s[c0 + j] * uu[j]);
+                        for (int j = 0; j < 16; j++) u[j] = s[c0 + j] * sm.w1[c0 + j][d];
+                    } else {
+                        tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (dl + 1) + c0), u);
+#pragma unroll
+                        for (int j = 0; j < 16; j++) u[j] *= s[c0 + j];
+                    }
+                    st_bf16x8(sm.tan[dl], t, c0 / 8, 64, u);
+                    st_bf16x8(sm.tan[dl], t, c0 / 8 + 1, 64, u + 8);
                 }
             }
-        }
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (t == 0) {
-            if (layer < 2) {
-                const unsigned char *W = sm.w + (layer == 0 ? kImgW2 : kImgW3);
-                tc::gemm_bf16_128xN(tm, sm.act, W, 64, 64);
-                for (int d = 0; d < 6; d++) tc::gemm_bf16_128xN(tm + 64 * (d + 1), sm.tan[d], W, 64, 64);
-            } else {
-                tc::gemm_bf16_128xN(tm, sm.act, sm.w + kImgW4, 16, 64);
-                for (int d = 0; d < 6; d++) tc::gemm_bf16_128xN(tm + 64 * (d + 1), sm.tan[d], sm.w + kImgW4, 16, 64);
+            smem_to_tensor_sync();
+            if (t == 0) {
+                const unsigned char *W = sm.w + (layer == 0 ? kImgW2 : layer == 1 ? kImgW3 : kImgW4);
+                const int N = layer < 2 ? 64 : 16;
+                tc::gemm_bf16_128xN(tm, sm.act, W, N, 64);
+                for (int dl = 0; dl < 3; dl++) tc::gemm_bf16_128xN(tm + 64 * (dl + 1), sm.tan[dl], W, N, 64);
             }
+            ok = mma_sync_bounded(&sm.mbar, phase) && ok;
         }
-        ok = mma_sync_bounded(&sm.mbar, phase) && ok;
-    }
-    {
         float v[16];
-        tc::tmem_ld16(tc::tmem_lane_addr(tm, 0), v);
+        if (round == 0) {
+            tc::tmem_ld16(tc::tmem_lane_addr(tm, 0), v);
 #pragma unroll
-        for (int c = 0; c < 6; c++) y[c] = v[c] + sm.b4[c];
+            for (int c = 0; c < 6; c++) y[c] = v[c] + sm.b4[c];
+        }
 #pragma unroll
-        for (int d = 0; d < 6; d++) {
-            tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (d + 1)), v);
+        for (int dl = 0; dl < 3; dl++) {
+            tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (dl + 1)), v);
+            // compile-time column indices keep Jm in registers
+            if (round == 0) {
 #pragma unroll
-            for (int c = 0; c < 6; c++) Jm[c][d] = v[c];
+                for (int c = 0; c < 6; c++) Jm[c][dl] = v[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; c++) Jm[c][3 + dl] = v[c];
+            }
         }
     }
     return ok;
