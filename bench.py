@@ -40,6 +40,10 @@ METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % o
 # algorithmic bytes (write-once CSR values + mesh data + u + R).
 TANGENT_FP64_FLOP_PER_ELEM = 23_144.0
 TANGENT_BYTES_PER_ELEM_FP64 = 2_160.0
+# DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
+# 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
+# coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
+TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 17_842.0
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
 # index (a node's three rows share one column list); v and y are per-row and stay in L2.
 SPMV_BYTES_PER_NNZ = {"fp64": 8.0 + 4.0 / 3.0, "fp32": 4.0 + 4.0 / 3.0}
@@ -122,6 +126,23 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(ms, world, device):
+    """The largest per-rank time (ms): every rank runs its own replica, so the job finishes
+    when the slowest rank does.  A plain all-reduce(MAX) over the default process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(n_elem_per_rank, world, ms_step):
+    """Whole-job throughput: the elements all ranks processed in one step over the slowest
+    rank's step time (elements per second)."""
+    return world * n_elem_per_rank / (ms_step * 1e-3)
 
 
 def make_problem(n):
@@ -420,13 +441,9 @@ def main():
         t1.record(stream)
         t1.synchronize()
     barrier()
-    ms_total = t0.elapsed_time(t1)
     ms_tangent = statistics.mean(a.elapsed_time(b) for a, b in evs)
-    tmax = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_step = float(tmax.item()) / args.steps
-    value = world * prob.n_elem / (ms_step * 1e-3)
+    ms_step = max_over_ranks(t0.elapsed_time(t1), world, "cuda") / args.steps
+    value = weak_scaling_value(prob.n_elem, world, ms_step)
     flags = mesh.check()
 
     # ---- end to end through the public API with pinned host buffers, copies timed
@@ -453,10 +470,7 @@ def main():
     e1.record(stream)
     e1.synchronize()
     barrier()
-    emax = torch.tensor([e0.elapsed_time(e1) / args.steps], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(emax, op=dist.ReduceOp.MAX)
-    e2e_ms = float(emax.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
 
     extra = {}
     if rank == 0 and not args.no_forms:
@@ -480,7 +494,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(prob, args.n),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_tangent<double,double>",
+                         "frac": achieved / fp64_peak,
+                         "traffic": TANGENT_DRAM_BYTES_PER_ELEM_FP64 * prob.n_elem,
+                         "traffic_note": "bytes per tangent call (8 colour launches), ncu at 64^3 scaled by elements",
+                         "kernel": "k_tangent<double,double>",
                          "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 148 SMs x 2032 MHz (derived in DESIGN.md)",
                          "ms_per_launch_group": ms_tangent, "hbm_achieved_gbs": hbm,
                          "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind},

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
     Constitutive<T> c;
-    constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, false);
+    constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, false);
     T f[3];
     nodal_force(c.P, K, l, f);
     if (active) {
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
                         (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
         raise_flag(A.flags, bits);
 #pragma unroll
-        for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
+        for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
     }
 }
 
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__res
         gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
         Constitutive<T> c;
-        constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, true);
+        constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, true);
         if (active) {
             uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
             raise_flag(A.flags, bits);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__res
         for (int i = 0; i < 3; i++) {
             VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
 #pragma unroll
-            for (int k = 0; k < 3; k++) dst[k] += (VT)Kab[i][k];
+            for (int k = 0; k < 3; k++) dst[k] += store_as<VT>(Kab[i][k]);
         }
         if (a != b) {
             const int sba = slotmap[sbase + 8 * b + a];
@@ -217,14 +217,14 @@ __global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__res
             for (int k = 0; k < 3; k++) {
                 VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
 #pragma unroll
-                for (int i = 0; i < 3; i++) dst[i] += (VT)Kab[i][k];
+                for (int i = 0; i < 3; i++) dst[i] += store_as<VT>(Kab[i][k]);
             }
         } else if (R) {
             const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
             if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
-            R[3 * (int64_t)na] += (double)Ra0;
-            R[3 * (int64_t)na + 1] += (double)Ra1;
-            R[3 * (int64_t)na + 2] += (double)Ra2;
+            R[3 * (int64_t)na] += to_double(Ra0);
+            R[3 * (int64_t)na + 1] += to_double(Ra1);
+            R[3 * (int64_t)na + 2] += to_double(Ra2);
         }
     }
 }
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
     T Y[3][3];
     bool ok = true;
     if (mt.law == JETSCI_LINEAR_ELASTIC) {
-        T lam = (T)mt.lam, mu = (T)mt.mu;
+        T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
         T tr = Hv[0][0] + Hv[1][1] + Hv[2][2];
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
             for (int j = 0; j < 3; j++) Y[i][j] = mu * (Hv[i][j] + Hv[j][i]) + ((i == j) ? lam * tr : T(0));
     } else {
         Constitutive<T> c;
-        constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, false);
+        constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, false);
         ok = c.ok;
         T h[3][3];
 #pragma unroll
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
                         (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
         raise_flag(A.flags, bits);
 #pragma unroll
-        for (int i = 0; i < 3; i++) y[3 * (int64_t)node + i] += (double)f[i];
+        for (int i = 0; i < 3; i++) y[3 * (int64_t)node + i] += to_double(f[i]);
     }
 }
 
@@ -303,11 +303,11 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
     gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, true);
     Constitutive<T> c;
-    constitutive<T>(mt.law, (T)mt.lam, (T)mt.mu, K.H, c, false);
+    constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, false);
     T f[3];
     nodal_force(c.P, K, l, f);
-    double d = R[3 * (int64_t)node] * (double)f[0] + R[3 * (int64_t)node + 1] * (double)f[1] +
-               R[3 * (int64_t)node + 2] * (double)f[2];
+    double d = R[3 * (int64_t)node] * to_double(f[0]) + R[3 * (int64_t)node + 1] * to_double(f[1]) +
+               R[3 * (int64_t)node + 2] * to_double(f[2]);
     d = allreduce8(d);
     if (active && l == 0) {
         uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE) |

@@ -110,6 +110,38 @@ __device__ __forceinline__ df64 df_log(df64 x) {
     return df_fma(ln2, df64((float)k), lnm);
 }
 
+// ---------------------------------------------------------------------------------------
+// Conversions by bit manipulation.  On B300 every FP64 instruction, conversions included,
+// issues on the narrow FP64 pipe; these use integer and FP32 instructions only.
+
+// float -> double, exact for normal floats and zero (subnormal floats flush to zero).
+__device__ __forceinline__ double f2d_bits(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long ex = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e - 127u + 1023u);
+    const unsigned long long man = (unsigned long long)(b & 0x7FFFFFu) << 29;
+    return __longlong_as_double((long long)(sign | (ex << 52) | man));
+}
+
+// double -> two-float: hi = the leading 24 significant bits (truncated), lo = the remaining
+// 29 bits rounded to float, so hi + lo carries about 48 bits.  Magnitudes below 2^-100 flush
+// to zero; magnitudes beyond the float range become infinities.
+__device__ __forceinline__ df64 split_double(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int ue = (int)((b >> 52) & 0x7FFull) - 1023;
+    const uint32_t s = (uint32_t)(b >> 63);
+    if (ue < -100) return df64(0.0f, 0.0f);
+    if (ue > 127) return df64(__uint_as_float((s << 31) | 0x7F800000u), 0.0f);
+    const unsigned long long man = b & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float((s << 31) | ((uint32_t)(ue + 127) << 23) | (uint32_t)(man >> 29));
+    float lo = ldexpf(__uint2float_rn((uint32_t)(man & 0x1FFFFFFFull)), ue - 52);
+    return df64(hi, s ? -lo : lo);
+}
+
+__device__ __forceinline__ double df_to_double(df64 x) { return f2d_bits(x.h) + f2d_bits(x.l); }
+
 __device__ __forceinline__ df64 shfl_df(df64 v, int src, int width) {
     return df64(__shfl_sync(0xffffffffu, v.h, src, width), __shfl_sync(0xffffffffu, v.l, src, width));
 }

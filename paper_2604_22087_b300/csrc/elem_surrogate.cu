@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
             if (bits) atomicOr(A.flags, bits);
             if (R)
 #pragma unroll
-                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
+                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
         }
     }
     if (!TANGENT) {

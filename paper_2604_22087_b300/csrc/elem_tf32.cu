@@ -33,6 +33,7 @@ struct __align__(128) Tf32Smem {
     unsigned char B[kTfGroups][kTfBTile];
     float G[kTfElems][8][8][3];  // [elem][q][node][comp]
     float cS[kTfElems][8][6];
+    float vnode[kTfElems][8][3];  // v at the element's nodes (matrix-free mode), FP32
     int32_t node[kTfElems][8];
     int32_t elem[kTfElems];
     uint64_t mbar;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         nodal_force(c.P, K, l, f);
         if (active)
 #pragma unroll
-            for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += (double)f[i];
+            for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
     }
     if (active) {
         uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
@@ -171,6 +172,9 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         }
     }
     sm.node[es][hex_node_of_lane(l)] = node;
+    if (MODE == 1)
+#pragma unroll
+        for (int k = 0; k < 3; k++) sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
     if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -249,12 +253,10 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         } else {
             float s = 0.0f;
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const int32_t nb = sm.node[ee][b];
+            for (int b = 0; b < 8; b++)
 #pragma unroll
-                for (int k = 0; k < 3; k++) s += rowv[3 * b + k] * (float)v[3 * (int64_t)nb + k];
-            }
-            y[3 * (int64_t)na + i] += (double)s;
+                for (int k = 0; k < 3; k++) s += rowv[3 * b + k] * sm.vnode[ee][b][k];
+            y[3 * (int64_t)na + i] += to_double(s);
         }
     }
     tc::fence_before_sync();

@@ -67,6 +67,50 @@ __device__ __forceinline__ double butterfly_forward(double v, int l) {
     return v;
 }
 
+// Conversions between double storage and the element type T.  For FP32 and two-float
+// elements they use integer/FP32 instructions only (B300's FP64 pipe is 1/64 of FP32).
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_double(df64 x) { return df_to_double(x); }
+
+template <typename T>
+__device__ __forceinline__ T from_double(double x);
+template <>
+__device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_double<float>(double x) {
+    const df64 s = split_double(x);
+    return __fadd_rn(s.h, s.l);
+}
+template <>
+__device__ __forceinline__ df64 from_double<df64>(double x) { return split_double(x); }
+
+template <typename VT, typename T>
+__device__ __forceinline__ VT store_as(T x) { return (VT)x; }
+template <>
+__device__ __forceinline__ double store_as<double, df64>(df64 x) { return df_to_double(x); }
+
+// 8 * monomial coefficient (lane = monomial) in the element type from nodal doubles (lane =
+// node).  FP64: the butterfly in FP64.  Two-float: FP64 butterfly, integer split.  FP32: the
+// butterfly in two-float arithmetic from integer-split inputs, rounded once at the end, so the
+// coefficients (differences of nearby nodal values) keep full FP32 relative accuracy.
+template <typename T>
+__device__ __forceinline__ T monomial_coeff(double v, int l);
+template <>
+__device__ __forceinline__ double monomial_coeff<double>(double v, int l) { return butterfly_forward(v, l); }
+template <>
+__device__ __forceinline__ df64 monomial_coeff<df64>(double v, int l) { return split_double(butterfly_forward(v, l)); }
+template <>
+__device__ __forceinline__ float monomial_coeff<float>(double v, int l) {
+    df64 x = split_double(v);
+#pragma unroll
+    for (int s = 1; s < 8; s <<= 1) {
+        const df64 p = shfl_xor_df(x, s, 8);
+        x = (l & s) ? x - p : x + p;
+    }
+    return __fadd_rn(x.h, x.l);
+}
+
 // Transpose of the forward butterfly: lane m holds a monomial moment, result at lane l
 // (node in binary order) is sum_m mono_m(node l) * moment_m.
 template <typename T>
@@ -196,8 +240,8 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
     T cx[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        cx[i] = (T)butterfly_forward(X[i], l);
-        cu[i] = (T)butterfly_forward(U[i], l);
+        cx[i] = monomial_coeff<T>(X[i], l);
+        cu[i] = monomial_coeff<T>(U[i], l);
     }
     const T g = (T)0.57735026918962576451;
     K.xi = (l & 1) ? g : -g;
@@ -225,7 +269,7 @@ __device__ __forceinline__ void field_gradient(const double *__restrict__ v, int
                                                const GaussKinematics<T> &K, T Hv[3][3]) {
     T cv[3], Dv[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) cv[i] = (T)butterfly_forward(v[3 * (int64_t)node + i], l);
+    for (int i = 0; i < 3; i++) cv[i] = monomial_coeff<T>(v[3 * (int64_t)node + i], l);
 #pragma unroll
     for (int i = 0; i < 3; i++) ref_gradient(cv[i], K.xi, K.eta, K.zeta, Dv[i]);
     T rdJ = my_rcp(K.dJ);
