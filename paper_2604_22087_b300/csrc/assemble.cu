@@ -31,16 +31,9 @@ __device__ __forceinline__ void raise_flag(uint32_t *flags, uint32_t bits) {
     if (bits) atomicOr(flags, bits);
 }
 
-// Upper-triangle node pairs (a <= b) of the 8x8 block structure of K_e.
-__constant__ int8_t kPairA[36] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2,
-                                  2, 2, 2, 3, 3, 3, 3, 3, 4, 4, 4, 4, 5, 5, 5, 6, 6, 7};
-__constant__ int8_t kPairB[36] = {0, 1, 2, 3, 4, 5, 6, 7, 1, 2, 3, 4, 5, 6, 7, 2, 3, 4,
-                                  5, 6, 7, 3, 4, 5, 6, 7, 4, 5, 6, 7, 5, 6, 7, 6, 7, 7};
-// Reference coordinates (+-1) of the hex8 local nodes, packed as bits (xi, eta, zeta).
-__constant__ int8_t kNodeBits[8] = {0, 1, 3, 2, 4, 5, 7, 6};
-
 // ---------------------------------------------------------------------------- residual
-// R_e(a,i) = sum_q w detJ P_iJ G_aJ, scattered into R (FP64 in every precision).
+// R_e(a,i) = sum_q w detJ P_iJ G_aJ, scattered into R (FP64 in every precision); the stress
+// moment comes from residual_moment (spatial form for the neo-Hookean law).
 template <typename T>
 __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__restrict__ u,
                                                   double *__restrict__ R) {
@@ -53,12 +46,12 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     T cu[3];
     gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
-    Constitutive<T> c;
-    constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, false);
+    T Q[3][3];
+    const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q);
     T f[3];
-    nodal_force(c.P, K, l, f);
+    nodal_force_of_moment(Q, K, l, f);
     if (active) {
-        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
                         (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
         raise_flag(A.flags, bits);
 #pragma unroll
@@ -67,24 +60,44 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
 }
 
 // ---------------------------------------------------------------------------- tangent
-// Phase 1 (8 lanes per element, lane = Gauss point): kinematics and constitutive update;
-// per Gauss point the spatial gradients g_a = F^-T G_a of the eight shape functions,
-// tg_a = c (tau + m I) g_a, and c lam, c m, c tau_R into shared memory (c = w detJ,
-// tau = F S F^T the Kirchhoff stress; tau_R = tau for the neo-Hookean law and sigma for the
-// linear law, where tau = 0 in the tangent).  Phase 2 (one thread per element and node pair
-// a <= b):
-//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi + delta_ik g_a . tg_b ]
-// which is the push-forward of sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL
-// for the neo-Hookean CC (F CC F = lam I(x)I + 2 m Isym, m = mu - lam lnJ; the linear law has
-// g = G, m = mu, tau = 0); the diagonal-pair thread (a == b) also forms the residual
-// R_a = sum_q c tau_R g_a (= sum_q w detJ P G_a).
+// Phase 1 (8 lanes per element, lane = Gauss point): kinematics and constitutive update; per
+// Gauss point the spatial gradients g_a = F^-T G_a of the eight shape functions, the vectors
+// tg_a = c (tau + m I) g_a and the coefficients c lam, c m and c Tg go to shared memory
+// (c = w detJ, tau = F S F^T the Kirchhoff stress, m = mu - lam lnJ; the linear law has g = G,
+// m = mu, tau = 0 and Tg = sigma).  Phase 2 (one thread per element and node pair a <= b):
+//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi ] + delta_ik sum_q tg_a . g_b
+// which is the push-forward of sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL for
+// the neo-Hookean CC (F CC F = lam I(x)I + 2 m Isym).  The diagonal-pair thread (a == b) also
+// forms the residual R_a = sum_q c Tg g_a (= sum_q w detJ P G_a).
+//
+// FP64 elements, bound by B300's FP64 pipe, also store c lam g_a and c m g_a, so that an
+// off-diagonal pair costs 21 multiply-adds per Gauss point instead of 27; FP32 and two-float
+// elements keep the smaller record, which leaves room for more resident blocks.
 constexpr int kTanElems = 16;  // elements per 128-thread block
+
+// Shared memory: one array per per-node vector (g, tg and, for FP64, c lam g and c m g), each
+// [element][Gauss point][node][3], nodes 3 entries apart, so that the eight nodes of an element
+// read in phase 2 fall on distinct banks.  Elements are 200 entries apart (8 mod 32 words for
+// FP32, 16 mod 32 for 8-byte types), which also spreads the up to four elements of one warp
+// over distinct banks.  For 8-byte types points are 25 entries apart (the eight Gauss-point
+// lanes of phase 1 on distinct banks); for FP32 24, keeping each lane's 24 values 16-byte
+// aligned for vector stores.
+template <typename T>
+struct TangentLayout {
+    static constexpr bool kPre = std::is_same<T, double>::value;
+    static constexpr int kNumVec = kPre ? 4 : 2;
+    static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
+    static constexpr int kElem = 200;
+    static constexpr int kArr = kTanElems * kElem;
+    // per (element, Gauss point): c lam, c m, c Tg (00,11,22,12,02,01); odd stride
+    static constexpr int kCoef = 9;
+    enum { kG = 0, kTG = 1, kLG = 2, kMG = 3 };
+};
 
 template <typename T>
 struct TangentSmem {
-    T g[kTanElems][8][8][3];   // [elem][q][node a][component]
-    T tg[kTanElems][8][8][3];  // c (tau + m I) g_a
-    T coef[kTanElems][8][8];   // [elem][q]: c lam, c m, c tau_R (00,11,22,12,02,01)
+    T v[TangentLayout<T>::kNumVec * TangentLayout<T>::kArr];
+    T coef[kTanElems * 8 * TangentLayout<T>::kCoef];
     int32_t node[kTanElems][8];
     int32_t elem[kTanElems];
 };
@@ -94,6 +107,7 @@ __global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__res
                                                  const int64_t *__restrict__ rowptr,
                                                  const uint8_t *__restrict__ slotmap,
                                                  VT *__restrict__ vals, double *__restrict__ R) {
+    using L = TangentLayout<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TangentSmem<T> &sm = *reinterpret_cast<TangentSmem<T> *>(smem_raw);
     const int l = threadIdx.x & 7;
@@ -107,131 +121,241 @@ __global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__res
         T cu[3];
         gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
-        Constitutive<T> c;
-        constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, true);
+        const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
+        // Per law: W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau of the geometric term,
+        // Tg (the stress paired with g in the residual) and m.
+        T W[3][3], tau[3][3], Tg[3][3], m;
+        bool ok = true;
+        if (mt.law == JETSCI_LINEAR_ELASTIC) {
+            // g = G: W = Jp^-1; sigma = lam tr(H) I + mu (H + H^T), H = Du Jp^-1; tau = 0
+            const T rdJ = my_rcp(K.dJ);
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) W[d][j] = K.aJ[d][j] * rdJ;
+            T H[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) H[i][j] = K.Du[i][0] * W[0][j] + K.Du[i][1] * W[1][j] + K.Du[i][2] * W[2][j];
+            const T ltr = lam * (H[0][0] + H[1][1] + H[2][2]);
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    Tg[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : T(0));
+                    tau[i][j] = T(0);
+                }
+            m = mu;
+        } else {
+            // Neo-Hookean: W = (F Jp)^-1 = j^-1 with j = Jp + Du the deformed Jacobian.
+            NeoHookeanState<T> st;
+            neo_hookean_state(K, lam, mu, st);
+            ok = st.ok;
+            m = st.m;
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    W[d][j] = st.aj[d][j] * st.rdj;
+                    tau[d][j] = st.tau[d][j];
+                    Tg[d][j] = st.tau[d][j];
+                }
+        }
         if (active) {
-            uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
+            uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE);
             raise_flag(A.flags, bits);
         }
-        const bool lin = mt.law == JETSCI_LINEAR_ELASTIC;
-        const T rdJ = my_rcp(K.dJ);
         const T cw = K.dJ * T(1.0 / 512.0);
-        // W = (F Jp)^-1 = Jp^-1 F^-1 = adj(Jp) F^-1 / det(Jp)
-        T W[3][3];
-#pragma unroll
-        for (int d = 0; d < 3; d++)
-#pragma unroll
-            for (int j = 0; j < 3; j++)
-                W[d][j] = (K.aJ[d][0] * c.Fi[0][j] + K.aJ[d][1] * c.Fi[1][j] + K.aJ[d][2] * c.Fi[2][j]) * rdJ;
-        const T cl = cw * c.lam, cm = cw * c.m;
+        const T cl = cw * lam, cm = cw * m;
         // c (tau + m I), tau = 0 in the linear law's tangent
-        const T t00 = cw * c.tau[0][0] + cm, t11 = cw * c.tau[1][1] + cm, t22 = cw * c.tau[2][2] + cm;
-        const T t12 = cw * c.tau[1][2], t02 = cw * c.tau[0][2], t01 = cw * c.tau[0][1];
+        const T t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
+        const T t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
+        // 1 +- xi, 1 +- eta, 1 +- zeta at the lane's Gauss point
+        const T xp = T(1) + K.xi, xm = T(1) - K.xi, yp = T(1) + K.eta, ym = T(1) - K.eta;
+        const T zp = T(1) + K.zeta, zm = T(1) - K.zeta;
+        T *pv = sm.v + es * L::kElem + l * L::kPoint;
 #pragma unroll
         for (int a = 0; a < 8; a++) {
-            const int bits_a = kNodeBits[a];
-            const T s0 = (bits_a & 1) ? T(1) : T(-1), s1 = (bits_a & 2) ? T(1) : T(-1), s2 = (bits_a & 4) ? T(1) : T(-1);
-            const T fx = T(1) + s0 * K.xi, fy = T(1) + s1 * K.eta, fz = T(1) + s2 * K.zeta;
-            const T n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
+            const int bits = hex_bits_of_node(a);
+            const T fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
+            const T yz = fy * fz, xz = fx * fz, xy = fx * fy;
+            // 8 dN_a/dxi at the Gauss point
+            const T n0 = (bits & 1) ? yz : -yz, n1 = (bits & 2) ? xz : -xz, n2 = (bits & 4) ? xy : -xy;
+            T *r = pv + 3 * a;
             T g[3];
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 g[j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
-                sm.g[es][l][a][j] = g[j];
+                r[L::kG * L::kArr + j] = g[j];
+                if constexpr (L::kPre) {
+                    r[L::kLG * L::kArr + j] = cl * g[j];
+                    r[L::kMG * L::kArr + j] = cm * g[j];
+                }
             }
-            sm.tg[es][l][a][0] = t00 * g[0] + t01 * g[1] + t02 * g[2];
-            sm.tg[es][l][a][1] = t01 * g[0] + t11 * g[1] + t12 * g[2];
-            sm.tg[es][l][a][2] = t02 * g[0] + t12 * g[1] + t22 * g[2];
+            r[L::kTG * L::kArr + 0] = t00 * g[0] + t01 * g[1] + t02 * g[2];
+            r[L::kTG * L::kArr + 1] = t01 * g[0] + t11 * g[1] + t12 * g[2];
+            r[L::kTG * L::kArr + 2] = t02 * g[0] + t12 * g[1] + t22 * g[2];
         }
-        sm.coef[es][l][0] = cl;
-        sm.coef[es][l][1] = cm;
-        if (lin) {
-            // tau_R = sigma = P for the linear law
-            sm.coef[es][l][2] = cw * c.P[0][0];
-            sm.coef[es][l][3] = cw * c.P[1][1];
-            sm.coef[es][l][4] = cw * c.P[2][2];
-            sm.coef[es][l][5] = cw * c.P[1][2];
-            sm.coef[es][l][6] = cw * c.P[0][2];
-            sm.coef[es][l][7] = cw * c.P[0][1];
-        } else {
-            sm.coef[es][l][2] = cw * c.tau[0][0];
-            sm.coef[es][l][3] = cw * c.tau[1][1];
-            sm.coef[es][l][4] = cw * c.tau[2][2];
-            sm.coef[es][l][5] = cw * c.tau[1][2];
-            sm.coef[es][l][6] = cw * c.tau[0][2];
-            sm.coef[es][l][7] = cw * c.tau[0][1];
-        }
+        T *pc = sm.coef + (es * 8 + l) * L::kCoef;
+        pc[0] = cl;
+        pc[1] = cm;
+        pc[2] = cw * Tg[0][0];
+        pc[3] = cw * Tg[1][1];
+        pc[4] = cw * Tg[2][2];
+        pc[5] = cw * Tg[1][2];
+        pc[6] = cw * Tg[0][2];
+        pc[7] = cw * Tg[0][1];
         sm.node[es][hex_node_of_lane(l)] = node;
         if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
     }
     __syncthreads();
+    // Work items, per group of 8 elements: first the 28 off-diagonal node pairs (a < b) of each
+    // element (7 warps), then their 8 diagonal pairs (2 warps).  Each warp holds items of one
+    // kind, so neither the residual (diagonal pairs only) nor the symmetric diagonal block leaves
+    // lanes predicated off, and an element's diagonal blocks follow its other blocks closely.
+    constexpr int kGroup = 8, kGroupItems = kGroup * 36, kGroupOff = kGroup * 28;
+    static_assert(kTanElems % kGroup == 0 && kGroupOff % 32 == 0 && kGroupItems % 32 == 0,
+                  "items of one kind per warp");
     for (int it = threadIdx.x; it < kTanElems * 36; it += blockDim.x) {
-        const int ee = it / 36, p = it - 36 * (it / 36);
+        const int grp = it / kGroupItems, r = it - kGroupItems * grp;
+        const bool off = r < kGroupOff;
+        int ee, a, b;
+        if (off) {
+            const int eg = r / 28;
+            const int p = r - 28 * eg;
+            ee = kGroup * grp + eg;
+            // p -> (a, b), a < b, in row order: row a starts at 7a - a(a-1)/2
+            a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
+            b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
+        } else {
+            const int j = r - kGroupOff;
+            ee = kGroup * grp + (j >> 3);
+            a = b = j & 7;
+        }
         const int32_t eid = sm.elem[ee];
         if (eid < 0) continue;
-        const int a = kPairA[p], b = kPairB[p];
-        T Kab[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
-        T Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
-#pragma unroll 2
-        for (int q = 0; q < 8; q++) {
-            const T *ga = sm.g[ee][q][a];
-            const T *gb = sm.g[ee][q][b];
-            const T *tb = sm.tg[ee][q][b];
-            const T *cf = sm.coef[ee][q];
-            const T a0 = ga[0], a1 = ga[1], a2 = ga[2], b0 = gb[0], b1 = gb[1], b2 = gb[2];
-            const T lam = cf[0], m = cf[1];
-            const T s = fma_t(a0, tb[0], fma_t(a1, tb[1], a2 * tb[2]));
-            const T la0 = lam * a0, la1 = lam * a1, la2 = lam * a2;
-            const T ma0 = m * a0, ma1 = m * a1, ma2 = m * a2;
-            Kab[0][0] = fma_t(la0, b0, fma_t(ma0, b0, Kab[0][0] + s));
-            Kab[0][1] = fma_t(la0, b1, fma_t(ma1, b0, Kab[0][1]));
-            Kab[0][2] = fma_t(la0, b2, fma_t(ma2, b0, Kab[0][2]));
-            Kab[1][0] = fma_t(la1, b0, fma_t(ma0, b1, Kab[1][0]));
-            Kab[1][1] = fma_t(la1, b1, fma_t(ma1, b1, Kab[1][1] + s));
-            Kab[1][2] = fma_t(la1, b2, fma_t(ma2, b1, Kab[1][2]));
-            Kab[2][0] = fma_t(la2, b0, fma_t(ma0, b2, Kab[2][0]));
-            Kab[2][1] = fma_t(la2, b1, fma_t(ma1, b2, Kab[2][1]));
-            Kab[2][2] = fma_t(la2, b2, fma_t(ma2, b2, Kab[2][2] + s));
-            if (R && a == b) {
-                Ra0 = fma_t(cf[2], a0, fma_t(cf[7], a1, fma_t(cf[6], a2, Ra0)));
-                Ra1 = fma_t(cf[7], a0, fma_t(cf[3], a1, fma_t(cf[5], a2, Ra1)));
-                Ra2 = fma_t(cf[6], a0, fma_t(cf[5], a1, fma_t(cf[4], a2, Ra2)));
-            }
-        }
-        const int32_t na = sm.node[ee][a], nb = sm.node[ee][b];
+        const T *pa = sm.v + ee * L::kElem + 3 * a;
+        const T *pb = sm.v + ee * L::kElem + 3 * b;
+        const T *pc = sm.coef + ee * 8 * L::kCoef;
+        const int32_t na = sm.node[ee][a];
         const int64_t sbase = 64 * (int64_t)eid;
-        const int sab = slotmap[sbase + 8 * a + b];
+        T Kab[3][3];
+        if (off) {
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
+            for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int k = 0; k < 3; k++) dst[k] += store_as<VT>(Kab[i][k]);
-        }
-        if (a != b) {
+                for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
+            T gs = T(0);
+#pragma unroll 2
+            for (int q = 0; q < 8; q++) {
+                const T *qa = pa + q * L::kPoint;
+                const T *qb = pb + q * L::kPoint;
+                const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
+                const T *ta = qa + L::kTG * L::kArr;
+                T l0, l1, l2, m0, m1, m2;
+                if constexpr (L::kPre) {
+                    const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
+                    l0 = la[0], l1 = la[1], l2 = la[2], m0 = ma[0], m1 = ma[1], m2 = ma[2];
+                } else {
+                    const T *cf = pc + q * L::kCoef;
+                    const T lam = cf[0], m = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
+                    l0 = lam * a0, l1 = lam * a1, l2 = lam * a2, m0 = m * a0, m1 = m * a1, m2 = m * a2;
+                }
+                gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
+                Kab[0][0] = fma_t(l0, b0, fma_t(m0, b0, Kab[0][0]));
+                Kab[0][1] = fma_t(l0, b1, fma_t(m1, b0, Kab[0][1]));
+                Kab[0][2] = fma_t(l0, b2, fma_t(m2, b0, Kab[0][2]));
+                Kab[1][0] = fma_t(l1, b0, fma_t(m0, b1, Kab[1][0]));
+                Kab[1][1] = fma_t(l1, b1, fma_t(m1, b1, Kab[1][1]));
+                Kab[1][2] = fma_t(l1, b2, fma_t(m2, b1, Kab[1][2]));
+                Kab[2][0] = fma_t(l2, b0, fma_t(m0, b2, Kab[2][0]));
+                Kab[2][1] = fma_t(l2, b1, fma_t(m1, b2, Kab[2][1]));
+                Kab[2][2] = fma_t(l2, b2, fma_t(m2, b2, Kab[2][2]));
+            }
+            Kab[0][0] += gs;
+            Kab[1][1] += gs;
+            Kab[2][2] += gs;
+            const int32_t nb = sm.node[ee][b];
+            const int sab = slotmap[sbase + 8 * a + b];
             const int sba = slotmap[sbase + 8 * b + a];
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
+#pragma unroll
+                for (int k = 0; k < 3; k++) dst[k] += store_as<VT>(Kab[i][k]);
+            }
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
 #pragma unroll
                 for (int i = 0; i < 3; i++) dst[i] += store_as<VT>(Kab[i][k]);
             }
-        } else if (R) {
-            const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
-            if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
-            R[3 * (int64_t)na] += to_double(Ra0);
-            R[3 * (int64_t)na + 1] += to_double(Ra1);
-            R[3 * (int64_t)na + 2] += to_double(Ra2);
+        } else {
+            // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
+            T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
+            T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
+#pragma unroll 2
+            for (int q = 0; q < 8; q++) {
+                const T *qa = pa + q * L::kPoint;
+                const T *cf = pc + q * L::kCoef;
+                const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
+                const T *ta = qa + L::kTG * L::kArr;
+                T s0, s1, s2;
+                if constexpr (L::kPre) {
+                    const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
+                    s0 = la[0] + ma[0], s1 = la[1] + ma[1], s2 = la[2] + ma[2];
+                } else {
+                    const T lm = cf[0] + cf[1];
+                    s0 = lm * b0, s1 = lm * b1, s2 = lm * b2;
+                }
+                gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
+                k00 = fma_t(s0, b0, k00);
+                k11 = fma_t(s1, b1, k11);
+                k22 = fma_t(s2, b2, k22);
+                k12 = fma_t(s1, b2, k12);
+                k02 = fma_t(s0, b2, k02);
+                k01 = fma_t(s0, b1, k01);
+                if (R) {
+                    Ra0 = fma_t(cf[2], b0, fma_t(cf[7], b1, fma_t(cf[6], b2, Ra0)));
+                    Ra1 = fma_t(cf[7], b0, fma_t(cf[3], b1, fma_t(cf[5], b2, Ra1)));
+                    Ra2 = fma_t(cf[6], b0, fma_t(cf[5], b1, fma_t(cf[4], b2, Ra2)));
+                }
+            }
+            Kab[0][0] = k00 + gs;
+            Kab[1][1] = k11 + gs;
+            Kab[2][2] = k22 + gs;
+            Kab[1][2] = Kab[2][1] = k12;
+            Kab[0][2] = Kab[2][0] = k02;
+            Kab[0][1] = Kab[1][0] = k01;
+            const int saa = slotmap[sbase + 9 * a];
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * saa;
+#pragma unroll
+                for (int k = 0; k < 3; k++) dst[k] += store_as<VT>(Kab[i][k]);
+            }
+            if (R) {
+                const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
+                if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
+                R[3 * (int64_t)na] += to_double(Ra0);
+                R[3 * (int64_t)na + 1] += to_double(Ra1);
+                R[3 * (int64_t)na + 2] += to_double(Ra2);
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------------------- K v, matrix-free
-// y_a += sum_q w detJ [ (Hv S) + tau' F^-T ] G_a with Hv = grad_X v, h = Hv F^-1,
-// tau' = lam tr(h) I + m (h + h^T)  (neo-Hookean);  y_a += sum_q w detJ sigma(Hv) G_a (linear).
+// y_a += sum_q w detJ Y G_a with Y the linearised first Piola-Kirchhoff stress in the direction
+// Hv = grad_X v:  Y = sigma(Hv) for the linear law;  for the neo-Hookean law, with
+// S = mu I - m C^-1 (m = mu - lam lnJ), C^-1 = F^-1 F^-T and h = Hv F^-1,
+//   Y = Hv S + (lam tr(h) I + m (h + h^T)) F^-T = mu Hv + (m h^T + lam tr(h) I) F^-T.
+// The neo-Hookean branch works with the deformed Jacobian j = Jp + Du = 8 dx/dxi, so that
+// F^-1 = Jp j^-1, J = det j / det Jp and h = Dv j^-1 (Dv = 8 dv/dxi), and forms the moment
+// Q = Y adj(Jp)^T directly:
+//   Q = (mu / det Jp) Dv adj(Jp) adj(Jp)^T + (det Jp / det j^2) M' adj(j)^T,
+//   M' = m h'^T + lam tr(h') I,  h' = Dv adj(j) = det j h.
 template <typename T>
 __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__restrict__ u,
                                                   const double *__restrict__ v, double *__restrict__ y) {
@@ -244,41 +368,67 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
     T cu[3];
     gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
-    T Hv[3][3];
-    field_gradient<T>(v, node, l, K, Hv);
-    T Y[3][3];
+    const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
+    T Dv[3][3];
+    field_ref_gradient<T>(v, node, l, K, Dv);
+    T Q[3][3];
     bool ok = true;
     if (mt.law == JETSCI_LINEAR_ELASTIC) {
-        T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
-        T tr = Hv[0][0] + Hv[1][1] + Hv[2][2];
+        const T rdJ = my_rcp(K.dJ);
+        T Hv[3][3], Y[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                Hv[i][j] = (Dv[i][0] * K.aJ[0][j] + Dv[i][1] * K.aJ[1][j] + Dv[i][2] * K.aJ[2][j]) * rdJ;
+        const T tr = Hv[0][0] + Hv[1][1] + Hv[2][2];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++) Y[i][j] = mu * (Hv[i][j] + Hv[j][i]) + ((i == j) ? lam * tr : T(0));
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) Q[i][d] = Y[i][0] * K.aJ[d][0] + Y[i][1] * K.aJ[d][1] + Y[i][2] * K.aJ[d][2];
     } else {
-        Constitutive<T> c;
-        constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, false);
-        ok = c.ok;
-        T h[3][3];
+        NeoHookeanState<T> st;
+        neo_hookean_state(K, lam, mu, st);
+        ok = st.ok;
+        const T m = st.m, rdj = st.rdj, rdJ = st.rdJ;
+        const T(&aj)[3][3] = st.aj;
+        T hp[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) h[i][j] = Hv[i][0] * c.Fi[0][j] + Hv[i][1] * c.Fi[1][j] + Hv[i][2] * c.Fi[2][j];
-        T trh = h[0][0] + h[1][1] + h[2][2];
-        T tp[3][3];
+            for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * aj[0][k] + Dv[i][1] * aj[1][k] + Dv[i][2] * aj[2][k];
+        const T ltr = lam * (hp[0][0] + hp[1][1] + hp[2][2]);
+        // A0 = adj(Jp) adj(Jp)^T (symmetric)
+        T A0[3][3];
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+        for (int n = 0; n < 3; n++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) tp[i][j] = c.m * (h[i][j] + h[j][i]) + ((i == j) ? c.lam * trh : T(0));
+            for (int d = n; d < 3; d++) {
+                const T t = K.aJ[n][0] * K.aJ[d][0] + K.aJ[n][1] * K.aJ[d][1] + K.aJ[n][2] * K.aJ[d][2];
+                A0[n][d] = t;
+                A0[d][n] = t;
+            }
+        const T s1 = mu * rdJ, s2 = K.dJ * rdj * rdj;
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 3; i++) {
+            // row i of M' = m h'^T + lam tr(h') I
+            const T M0 = fma_t(m, hp[0][i], (i == 0) ? ltr : T(0));
+            const T M1 = fma_t(m, hp[1][i], (i == 1) ? ltr : T(0));
+            const T M2 = fma_t(m, hp[2][i], (i == 2) ? ltr : T(0));
 #pragma unroll
-            for (int J2 = 0; J2 < 3; J2++)
-                Y[i][J2] = Hv[i][0] * c.S[0][J2] + Hv[i][1] * c.S[1][J2] + Hv[i][2] * c.S[2][J2] +
-                           tp[i][0] * c.Fi[J2][0] + tp[i][1] * c.Fi[J2][1] + tp[i][2] * c.Fi[J2][2];
+            for (int d = 0; d < 3; d++) {
+                const T p1 = Dv[i][0] * A0[0][d] + Dv[i][1] * A0[1][d] + Dv[i][2] * A0[2][d];
+                const T p2 = M0 * aj[d][0] + M1 * aj[d][1] + M2 * aj[d][2];
+                Q[i][d] = fma_t(s1, p1, s2 * p2);
+            }
+        }
     }
     T f[3];
-    nodal_force(Y, K, l, f);
+    nodal_force_of_moment(Q, K, l, f);
     if (active) {
         uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
                         (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
@@ -302,15 +452,15 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
     T cu[3];
     gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, true);
-    Constitutive<T> c;
-    constitutive<T>(mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), K.H, c, false);
+    T Q[3][3];
+    const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q);
     T f[3];
-    nodal_force(c.P, K, l, f);
+    nodal_force_of_moment(Q, K, l, f);
     double d = R[3 * (int64_t)node] * to_double(f[0]) + R[3 * (int64_t)node + 1] * to_double(f[1]) +
                R[3 * (int64_t)node + 2] * to_double(f[2]);
     d = allreduce8(d);
     if (active && l == 0) {
-        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
                         (isfinite(d) ? 0u : JETSCI_FLAG_NONFINITE);
         raise_flag(A.flags, bits);
         g[e] = d;
@@ -365,6 +515,9 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
                                      cudaStream_t s) {
     const size_t smem = sizeof(TangentSmem<T>);
     JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // The FP64 block (112 KB) fits twice per SM only with the largest shared-memory carveout.
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared));
     // One launch per colour.  Splitting colours into L2-sized chunks (chunk-major order) was
     // measured slower at 128^3 for every precision: the 8x more, smaller launches lose more
     // in launch tails than the L2-resident read-modify-writes gain.

@@ -17,7 +17,8 @@
 
 namespace jetsci {
 
-struct df64 {
+// 8-byte aligned, so that a value moves through shared memory in one 64-bit access.
+struct __align__(8) df64 {
     float h, l;
     df64() = default;
     __host__ __device__ constexpr df64(float hi, float lo) : h(hi), l(lo) {}

@@ -77,11 +77,12 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
     gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
     const int ph = A.phase[e];
     const Material mt = A.mats[ph];
-    float F[3][3];
+    float H[3][3], F[3][3];
+    displacement_gradient(K, H);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) F[i][j] = (i == j ? 1.0f : 0.0f) + K.H[i][j];
+        for (int j = 0; j < 3; j++) F[i][j] = (i == j ? 1.0f : 0.0f) + H[i][j];
     float E6[6];
 #pragma unroll
     for (int a = 0; a < 6; a++) {

@@ -92,8 +92,10 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     float cu[3];
     gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
+    float H[3][3];
+    displacement_gradient(K, H);
     Constitutive<float> c;
-    constitutive<float>(mt.law, (float)mt.lam, (float)mt.mu, K.H, c, false);
+    constitutive<float>(mt.law, (float)mt.lam, (float)mt.mu, H, c);
     const bool lin = mt.law == JETSCI_LINEAR_ELASTIC;
     if (MODE == 0 && R) {
         float f[3];

@@ -131,6 +131,23 @@ __device__ __forceinline__ T allreduce8(T v) {
     return v;
 }
 
+// Reduce-scatter over the eight lanes of an element: lane l receives sum over lanes of v[l].
+// Each exchange stage keeps the half of the vector selected by one bit of l and adds the
+// partner's copy of it, so 7 additions and 7 exchanges replace 8 separate all-reduces.
+template <typename T>
+__device__ __forceinline__ T reduce_scatter8(const T v[8], int l) {
+    const bool h4 = l & 4, h2 = l & 2, h1 = l & 1;
+    T r4[4], r2[2];
+#pragma unroll
+    for (int j = 0; j < 4; j++) r4[j] = (h4 ? v[4 + j] : v[j]) + shfl_xor8(h4 ? v[j] : v[4 + j], 4);
+#pragma unroll
+    for (int j = 0; j < 2; j++) r2[j] = (h2 ? r4[2 + j] : r4[j]) + shfl_xor8(h2 ? r4[j] : r4[2 + j], 2);
+    return (h1 ? r2[1] : r2[0]) + shfl_xor8(h1 ? r2[0] : r2[1], 1);
+}
+
+// Reference-coordinate bit pattern (xi, eta, zeta) of hex8 local node a: {0,1,3,2,4,5,7,6}.
+__host__ __device__ constexpr int hex_bits_of_node(int a) { return a ^ ((a >> 1) & 1); }
+
 // 8 * reference derivatives at the lane's Gauss point from 8 * monomial coefficients held
 // by lanes 1..7 (component held by the calling lane in `c`):
 //   d/dxi   = c_xi   + c_xieta eta + c_xizeta zeta + c_xietazeta eta zeta
@@ -214,13 +231,12 @@ __device__ __forceinline__ ElemMaterial element_material(const Material *__restr
 }
 
 // Per-lane kinematics at the lane's Gauss point.
-//   Jp = 8 dX/dxi, aJ = adj(Jp), dJ = det(Jp)   (detJ = dJ / 512)
-//   H  = grad_X u = (8 du/dxi) Jp^-1
+//   Jp = 8 dX/dxi, aJ = adj(Jp), dJ = det(Jp)   (detJ = dJ / 512),  Du = 8 du/dxi
 template <typename T>
 struct GaussKinematics {
     T xi, eta, zeta;
     T Jp[3][3], aJ[3][3], dJ;
-    T H[3][3];
+    T Du[3][3];  // 8 du/dxi
 };
 
 // Gathers coordinates and one nodal field for element e, forms coefficients (FP64) and the
@@ -247,31 +263,43 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
     K.xi = (l & 1) ? g : -g;
     K.eta = (l & 2) ? g : -g;
     K.zeta = (l & 4) ? g : -g;
-    T Du[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         ref_gradient(cx[i], K.xi, K.eta, K.zeta, K.Jp[i]);
-        ref_gradient(cu[i], K.xi, K.eta, K.zeta, Du[i]);
+        ref_gradient(cu[i], K.xi, K.eta, K.zeta, K.Du[i]);
     }
     adj3(K.Jp, K.aJ);
     K.dJ = K.Jp[0][0] * K.aJ[0][0] + K.Jp[0][1] * K.aJ[1][0] + K.Jp[0][2] * K.aJ[2][0];
-    T rdJ = my_rcp(K.dJ);
+}
+
+// Displacement gradient H = grad_X u = (8 du/dxi) Jp^-1 at the lane's Gauss point.
+template <typename T>
+__device__ __forceinline__ void displacement_gradient(const GaussKinematics<T> &K, T H[3][3]) {
+    const T rdJ = my_rcp(K.dJ);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++)
-            K.H[i][j] = (Du[i][0] * K.aJ[0][j] + Du[i][1] * K.aJ[1][j] + Du[i][2] * K.aJ[2][j]) * rdJ;
+            H[i][j] = (K.Du[i][0] * K.aJ[0][j] + K.Du[i][1] * K.aJ[1][j] + K.Du[i][2] * K.aJ[2][j]) * rdJ;
+}
+
+// Reference gradient of a second nodal field v at the lane's Gauss point: Dv = 8 dv/dxi.
+template <typename T>
+__device__ __forceinline__ void field_ref_gradient(const double *__restrict__ v, int32_t node, int l,
+                                                   const GaussKinematics<T> &K, T Dv[3][3]) {
+    T cv[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) cv[i] = monomial_coeff<T>(v[3 * (int64_t)node + i], l);
+#pragma unroll
+    for (int i = 0; i < 3; i++) ref_gradient(cv[i], K.xi, K.eta, K.zeta, Dv[i]);
 }
 
 // Gradient of a second nodal field v with the same geometry: Hv = (8 dv/dxi) Jp^-1.
 template <typename T>
 __device__ __forceinline__ void field_gradient(const double *__restrict__ v, int32_t node, int l,
                                                const GaussKinematics<T> &K, T Hv[3][3]) {
-    T cv[3], Dv[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) cv[i] = monomial_coeff<T>(v[3 * (int64_t)node + i], l);
-#pragma unroll
-    for (int i = 0; i < 3; i++) ref_gradient(cv[i], K.xi, K.eta, K.zeta, Dv[i]);
+    T Dv[3][3];
+    field_ref_gradient<T>(v, node, l, K, Dv);
     T rdJ = my_rcp(K.dJ);
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -280,23 +308,21 @@ __device__ __forceinline__ void field_gradient(const double *__restrict__ v, int
             Hv[i][j] = (Dv[i][0] * K.aJ[0][j] + Dv[i][1] * K.aJ[1][j] + Dv[i][2] * K.aJ[2][j]) * rdJ;
 }
 
-// Constitutive state at one Gauss point.  P = first Piola-Kirchhoff stress.  For the
-// tangent: Fi = F^-1 (identity for the linear law), tau = Kirchhoff stress F S F^T,
-// lam and m = mu - lam lnJ so that the push-forward of CC is lam I(x)I + 2m Isym.
+// Constitutive state at one Gauss point: F, F^-1 (identity for the linear law), the second
+// and first Piola-Kirchhoff stresses S and P, lam and m = mu - lam lnJ (the push-forward of
+// the neo-Hookean CC is lam I(x)I + 2m Isym), ok = (J > 0).
 template <typename T>
 struct Constitutive {
     T P[3][3];
     T S[3][3];
     T Fi[3][3];
     T F[3][3];
-    T tau[3][3];
     T lam, m;
     bool ok;
 };
 
 template <typename T>
-__device__ __forceinline__ void constitutive(int law, T lam, T mu, const T H[3][3],
-                                             Constitutive<T> &c, bool want_tangent) {
+__device__ __forceinline__ void constitutive(int law, T lam, T mu, const T H[3][3], Constitutive<T> &c) {
     c.ok = true;
     if (law == JETSCI_LINEAR_ELASTIC) {
         T tr = H[0][0] + H[1][1] + H[2][2];
@@ -310,7 +336,6 @@ __device__ __forceinline__ void constitutive(int law, T lam, T mu, const T H[3][
                 c.S[i][j] = s;
                 c.F[i][j] = (i == j) ? T(1) : T(0);
                 c.Fi[i][j] = c.F[i][j];
-                c.tau[i][j] = T(0);
             }
         c.lam = lam;
         c.m = mu;
@@ -333,6 +358,8 @@ __device__ __forceinline__ void constitutive(int law, T lam, T mu, const T H[3][
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) c.Fi[i][j] = aF[i][j] * rJ;
+    c.lam = lam;
+    c.m = mu - lam * lnJ;
     T Ci[3][3];
 #pragma unroll
     for (int I = 0; I < 3; I++)
@@ -352,48 +379,129 @@ __device__ __forceinline__ void constitutive(int law, T lam, T mu, const T H[3][
 #pragma unroll
         for (int J2 = 0; J2 < 3; J2++)
             c.P[i][J2] = c.F[i][0] * c.S[0][J2] + c.F[i][1] * c.S[1][J2] + c.F[i][2] * c.S[2][J2];
-    c.lam = lam;
-    c.m = mu - lam * lnJ;
-    if (want_tangent) {
-        // tau = F S F^T = mu (F F^T - I) + lam lnJ I
-        T ll = lam * lnJ;
+}
+
+// Neo-Hookean state at the lane's Gauss point from the deformed Jacobian j = Jp + Du = 8 dx/dxi:
+// F = j Jp^-1, J = det j / det Jp (one reciprocal serves both determinants), m = mu - lam lnJ
+// and the Kirchhoff stress tau = F S F^T = mu (F F^T - I) + lam lnJ I with F F^T formed from
+// F det(Jp) = j adj(Jp).  ok = (J > 0); otherwise lnJ is taken as 0.
+template <typename T>
+struct NeoHookeanState {
+    T jm[3][3], aj[3][3];  // j and adj(j)
+    T rdj, rdJ;            // 1 / det j, 1 / det Jp
+    T lnJ, m;
+    T tau[3][3];
+    bool ok;
+};
+
+template <typename T>
+__device__ __forceinline__ void neo_hookean_state(const GaussKinematics<T> &K, T lam, T mu, NeoHookeanState<T> &s) {
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) s.jm[i][d] = K.Jp[i][d] + K.Du[i][d];
+    adj3(s.jm, s.aj);
+    const T dj = s.jm[0][0] * s.aj[0][0] + s.jm[0][1] * s.aj[1][0] + s.jm[0][2] * s.aj[2][0];
+    const T pj = K.dJ * dj;
+    s.ok = pj > T(0);
+    const T r = my_rcp(s.ok ? pj : T(1));
+    s.rdj = K.dJ * r;
+    s.rdJ = dj * r;
+    s.lnJ = my_log(s.ok ? dj * s.rdJ : T(1));
+    s.m = mu - lam * s.lnJ;
+    T Fd[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) Fd[i][k] = s.jm[i][0] * K.aJ[0][k] + s.jm[i][1] * K.aJ[1][k] + s.jm[i][2] * K.aJ[2][k];
+    const T mb = mu * s.rdJ * s.rdJ, diag = lam * s.lnJ - mu;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = i; k < 3; k++) {
+            const T b = Fd[i][0] * Fd[k][0] + Fd[i][1] * Fd[k][1] + Fd[i][2] * Fd[k][2];
+            const T t = (i == k) ? fma_t(mb, b, diag) : mb * b;
+            s.tau[i][k] = t;
+            s.tau[k][i] = t;
+        }
+}
+
+// Residual moment Q = P adj(Jp)^T (see nodal_force_of_moment) of the element's law at the
+// lane's Gauss point.  Linear law: P = sigma(H), H = Du Jp^-1.  Neo-Hookean: P = tau F^-T and
+// F^-T adj(Jp)^T = (det Jp / det j) adj(j)^T, so Q = (det Jp / det j) tau adj(j)^T.
+template <typename T>
+__device__ __forceinline__ bool residual_moment(const GaussKinematics<T> &K, int law, T lam, T mu, T Q[3][3]) {
+    if (law == JETSCI_LINEAR_ELASTIC) {
+        const T rdJ = my_rcp(K.dJ);
+        T H[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int k = i; k < 3; k++) {
-                T b = c.F[i][0] * c.F[k][0] + c.F[i][1] * c.F[k][1] + c.F[i][2] * c.F[k][2];
-                T t = mu * b + ((i == k) ? (ll - mu) : T(0));
-                c.tau[i][k] = t;
-                c.tau[k][i] = t;
-            }
+            for (int j = 0; j < 3; j++)
+                H[i][j] = (K.Du[i][0] * K.aJ[0][j] + K.Du[i][1] * K.aJ[1][j] + K.Du[i][2] * K.aJ[2][j]) * rdJ;
+        const T ltr = lam * (H[0][0] + H[1][1] + H[2][2]);
+        T Y[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) Y[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : T(0));
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) Q[i][d] = Y[i][0] * K.aJ[d][0] + Y[i][1] * K.aJ[d][1] + Y[i][2] * K.aJ[d][2];
+        return true;
     }
+    NeoHookeanState<T> s;
+    neo_hookean_state(K, lam, mu, s);
+    const T sc = K.dJ * s.rdj;
+    T ts[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) ts[i][k] = sc * s.tau[i][k];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) Q[i][d] = ts[i][0] * s.aj[d][0] + ts[i][1] * s.aj[d][1] + ts[i][2] * s.aj[d][2];
+    return s.ok;
 }
 
 // Nodal force of the lane's node from the lane's (Gauss point's) stress moment matrix
-// Q_id = (w/64) sum_j Y_ij adj(Jp)_dj, i.e. w detJ Y J^-T: returns
-// f_a,i = sum_q sum_d Q_q,id dN_a/dxi_d(q) for node a = lane (binary order).
+// Q_id = sum_j Y_ij adj(Jp)_dj, i.e. (64/w) w detJ Y J^-T: returns
+// f_a,i = (w/64) sum_q sum_d Q_q,id dN_a/dxi_d(q) for node a = lane (binary order).  The factor
+// w/64 is applied with the transpose's 1/8 at the end (an exact power-of-two scaling).
+template <typename T>
+__device__ __forceinline__ void nodal_force_of_moment(const T Q[3][3], const GaussKinematics<T> &K, int l,
+                                                      T f[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const T Q0 = Q[i][0], Q1 = Q[i][1], Q2 = Q[i][2];
+        // moment contributions of this Gauss point for monomials 0..7 (monomial 0 has none)
+        T mom[8];
+        mom[0] = T(0);
+        mom[1] = Q0;
+        mom[2] = Q1;
+        mom[4] = Q2;
+        mom[3] = Q0 * K.eta + Q1 * K.xi;
+        mom[5] = Q0 * K.zeta + Q2 * K.xi;
+        mom[6] = Q1 * K.zeta + Q2 * K.eta;
+        mom[7] = Q0 * (K.eta * K.zeta) + Q1 * (K.xi * K.zeta) + Q2 * (K.xi * K.eta);
+        // sum over the 8 Gauss points with moment m landing at lane m
+        const T mine = reduce_scatter8(mom, l);
+        f[i] = butterfly_transpose(mine, l) * T(1.0 / 512.0);
+    }
+}
+
+// The same from the stress Y (P for the residual, the linearised P for K v).
 template <typename T>
 __device__ __forceinline__ void nodal_force(const T Y[3][3], const GaussKinematics<T> &K, int l,
                                             T f[3]) {
-    const T w64 = T(1.0 / 64.0);
+    T Q[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) {
-        T Q0 = (Y[i][0] * K.aJ[0][0] + Y[i][1] * K.aJ[0][1] + Y[i][2] * K.aJ[0][2]) * w64;
-        T Q1 = (Y[i][0] * K.aJ[1][0] + Y[i][1] * K.aJ[1][1] + Y[i][2] * K.aJ[1][2]) * w64;
-        T Q2 = (Y[i][0] * K.aJ[2][0] + Y[i][1] * K.aJ[2][1] + Y[i][2] * K.aJ[2][2]) * w64;
-        // moment contributions of this Gauss point for monomials 1..7
-        T m1 = Q0, m2 = Q1, m4 = Q2;
-        T m3 = Q0 * K.eta + Q1 * K.xi;
-        T m5 = Q0 * K.zeta + Q2 * K.xi;
-        T m6 = Q1 * K.zeta + Q2 * K.eta;
-        T m7 = Q0 * (K.eta * K.zeta) + Q1 * (K.xi * K.zeta) + Q2 * (K.xi * K.eta);
-        // sum over the 8 Gauss points, then place moment m at lane m
-        m1 = allreduce8(m1); m2 = allreduce8(m2); m3 = allreduce8(m3); m4 = allreduce8(m4);
-        m5 = allreduce8(m5); m6 = allreduce8(m6); m7 = allreduce8(m7);
-        T mine = (l == 1) ? m1 : (l == 2) ? m2 : (l == 3) ? m3 : (l == 4) ? m4
-               : (l == 5) ? m5 : (l == 6) ? m6 : (l == 7) ? m7 : T(0);
-        f[i] = butterfly_transpose(mine, l) * T(0.125);
-    }
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) Q[i][d] = Y[i][0] * K.aJ[d][0] + Y[i][1] * K.aJ[d][1] + Y[i][2] * K.aJ[d][2];
+    nodal_force_of_moment(Q, K, l, f);
 }
 
 }  // namespace jetsci
