@@ -36,10 +36,20 @@ struct SurrogateConfig {
     float out_shift[2][6];
 };
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU a = z s and its derivative s (1 + z (1 - s)) with s = 1 / (1 + e^-z), from the fast
+// exponential and a fast reciprocal: their few-ulp FP32 errors are far below the BF16 rounding
+// (2^-9) every activation and tangent goes through, and an IEEE-rounded division here made
+// the epilogues several times slower.
+__device__ __forceinline__ float sigmoid_f(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 __device__ __forceinline__ float silu_prime_f(float z) {
-    float s = 1.0f / (1.0f + __expf(-z));
-    return s * (1.0f + z * (1.0f - s));
+    const float s = sigmoid_f(z);
+    return s * fmaf(z, 1.0f - s, 1.0f);
+}
+__device__ __forceinline__ void silu_and_prime(float z, float &a, float &ds) {
+    const float s = sigmoid_f(z);
+    a = z * s;
+    ds = s * fmaf(z, 1.0f - s, 1.0f);
 }
 
 // Shared-memory workspace of one 128-point tile for the forward + input-Jacobian pass.  The
@@ -132,9 +142,7 @@ __device__ inline bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, fl
                 tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    const float zz = z[j] + sm.b[layer][c0 + j];
-                    s[c0 + j] = silu_prime_f(zz);
-                    a[j] = silu_f(zz);
+                    silu_and_prime(z[j] + sm.b[layer][c0 + j], a[j], s[c0 + j]);
                 }
                 st_bf16x8(sm.act, t, c0 / 8, 64, a);
                 st_bf16x8(sm.act, t, c0 / 8 + 1, 64, a + 8);
