@@ -270,6 +270,9 @@ jetsci_status jetsci_mesh_surrogate_fallbacks(jetsci_mesh mesh, uint32_t *count_
  * ||R_free|| <= rtol * ||R_free(u_0)||; each CG stops at ||r|| <= cg_rtol ||r_0|| or max_cg.
  * Allocates its own workspace (about 7 n_dof doubles plus one CSR value array) and
  * synchronises.  Returns JETSCI_ERR_NOT_CONVERGED after max_newton steps, with *info filled.
+ * *info also splits the device time (CUDA events on `stream`) into residual evaluations,
+ * tangent assembly and CG solves: the assembly-versus-solve split of the paper's timings
+ * (Section V).
  */
 typedef struct {
     int32_t newton_iters;         /* Newton steps taken                                  */
@@ -278,12 +281,31 @@ typedef struct {
     int32_t reserved;
     double final_rel_residual;    /* ||R_free(u)|| / ||R_free(u_0)||                      */
     double residual_history[32];  /* relative residual before step k (k < 32)            */
+    double seconds_residual;      /* device time: FP64 residuals and norms               */
+    double seconds_tangent;       /* device time: tangent assembly and Jacobi diagonal   */
+    double seconds_solve;         /* device time: CG solves and updates                  */
 } jetsci_newton_info;
 
 jetsci_status jetsci_newton_solve(jetsci_mesh mesh, double *u_dev, int64_t n_bc, const int64_t *bc_dofs_dev,
                                   const double *bc_vals_dev, int32_t tangent_precision, double rtol,
                                   int32_t max_newton, double cg_rtol, int32_t max_cg, void *stream,
                                   jetsci_newton_info *info);
+
+/* ---------------------------------------------------------------------------
+ * Insertion of element blocks formed by the caller into the mesh's CSR pattern: the
+ * counterpart of handing element-batched dense Jacobian blocks (Section III-B) to a matrix
+ * preallocated with their COO pattern and setting its values with duplicates summed and
+ * INSERT semantics (Section III-C).  The COO order is element-major and implied by the
+ * connectivity: entry (e, 3a+i, 3b+k) goes to row 3 conn[e][a] + i, column 3 conn[e][b] + k.
+ *   Ke_dev   [n_elem][24][24] row-major, local DOF 3a + i (a = local node in connectivity
+ *            order, i = component); double for JETSCI_FP64, float for JETSCI_FP32.
+ *   vals_dev [nnz] of the same type, overwritten with sum_e P_e^T K_e P_e (rows of
+ *            jetsci_mesh_info's pattern).  Sums run colour by colour in a fixed order:
+ *            bitwise reproducible, no atomics.
+ * Other precisions -> JETSCI_ERR_ARG.  Asynchronous on `stream`.
+ */
+jetsci_status jetsci_assemble_element_blocks(jetsci_mesh mesh, const void *Ke_dev, void *vals_dev, int32_t precision,
+                                             void *stream);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free ||x||_2 (no counterpart in the paper; a service for callers that

@@ -467,6 +467,51 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
     }
 }
 
+// ---------------------------------------------------------------------------- block insertion
+// vals[(a,i),(b,k)] += Ke[e][3a+i][3b+k] for the elements of one colour: thread = (element, local
+// row 3a+i), the row's eight 3-wide blocks go to the slots of nodes b in node a's column list.
+constexpr int kInsElems = 8;  // elements per 192-thread block
+
+template <typename VT>
+__global__ void __launch_bounds__(24 * kInsElems) k_insert_blocks(const int32_t *__restrict__ elems, int64_t n,
+                                                                  const int32_t *__restrict__ conn,
+                                                                  const VT *__restrict__ Ke,
+                                                                  const int64_t *__restrict__ rowptr,
+                                                                  const uint8_t *__restrict__ slotmap,
+                                                                  VT *__restrict__ vals) {
+    const int64_t idx = (int64_t)blockIdx.x * kInsElems + threadIdx.x / 24;
+    if (idx >= n) return;
+    const int r = threadIdx.x % 24, a = r / 3, i = r - 3 * (r / 3);
+    const int64_t e = elems[idx];
+    const VT *row = Ke + (24 * e + r) * 24;
+    VT *dst = vals + rowptr[3 * (int64_t)conn[8 * e + a] + i];
+    const uint8_t *sl = slotmap + 64 * e + 8 * a;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        VT *d = dst + 3 * (int)sl[b];
+#pragma unroll
+        for (int k = 0; k < 3; k++) d[k] += row[3 * b + k];
+    }
+}
+
+jetsci_status launch_insert_blocks(jetsci_mesh m, const void *Ke, void *vals, bool fp32, cudaStream_t s) {
+    JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * (fp32 ? sizeof(float) : sizeof(double)), s));
+    for (int c = 0; c < m->n_colours; c++) {
+        const int32_t *elems = m->d_colour_elems + m->colour_ptr[c];
+        const int64_t n = m->colour_ptr[c + 1] - m->colour_ptr[c];
+        if (n == 0) continue;
+        const unsigned grid = (unsigned)((n + kInsElems - 1) / kInsElems);
+        if (fp32)
+            k_insert_blocks<float><<<grid, 24 * kInsElems, 0, s>>>(elems, n, m->d_conn, (const float *)Ke, m->d_rowptr,
+                                                                  m->d_slot, (float *)vals);
+        else
+            k_insert_blocks<double><<<grid, 24 * kInsElems, 0, s>>>(elems, n, m->d_conn, (const double *)Ke,
+                                                                   m->d_rowptr, m->d_slot, (double *)vals);
+    }
+    JETSCI_CUDA_TRY(cudaGetLastError());
+    return JETSCI_OK;
+}
+
 // ---------------------------------------------------------------------------- launchers
 static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
     ElemArgs A;

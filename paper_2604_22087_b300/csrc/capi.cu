@@ -72,3 +72,16 @@ extern "C" jetsci_status jetsci_norm2(jetsci_mesh m, const double *x, int64_t n,
     if (n < 0 || !out || (n > 0 && !x)) return fail(JETSCI_ERR_ARG, "invalid norm arguments");
     return launch_norm2(x, n, m->d_norm_partials, kNormMaxPartials, out, s);
 }
+
+extern "C" jetsci_status jetsci_assemble_element_blocks(jetsci_mesh m, const void *Ke, void *vals, int32_t precision,
+                                                        void *stream) {
+    cudaStream_t s;
+    jetsci_status st = enter(m, stream, &s);
+    if (st) return st;
+    if (precision != JETSCI_FP64 && precision != JETSCI_FP32)
+        return fail(JETSCI_ERR_ARG, "element blocks must be FP64 or FP32");
+    if (m->nnz > 0 && !vals) return fail(JETSCI_ERR_ARG, "vals is NULL");
+    if (m->n_elem > 0 && !Ke) return fail(JETSCI_ERR_ARG, "Ke is NULL");
+    if (m->nnz == 0) return JETSCI_OK;
+    return launch_insert_blocks(m, Ke, vals, precision == JETSCI_FP32, s);
+}

@@ -107,6 +107,7 @@ jetsci_status launch_norm2(const double *x, int64_t n, double *partials, int64_t
 jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float *vals, double *R, double *y,
                           const double *E_elem, cudaStream_t s);
 jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, double *R, cudaStream_t s);
+jetsci_status launch_insert_blocks(jetsci_mesh m, const void *Ke, void *vals, bool fp32, cudaStream_t s);
 jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
                                    const double *R, double *g, int precision, cudaStream_t s);
 

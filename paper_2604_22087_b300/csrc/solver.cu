@@ -129,11 +129,24 @@ struct Workspace {
     CgScalars *sc = nullptr;
     uint8_t *fixed = nullptr;
     void *vals = nullptr;
+    // events bracketing the residual, tangent and solve phases of a Newton step
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     ~Workspace() {
         cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(q); cudaFree(x); cudaFree(dinv); cudaFree(R);
         cudaFree(partials); cudaFree(scal_norm); cudaFree(sc); cudaFree(fixed); cudaFree(vals);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
     }
 };
+
+// Adds the device time between two recorded events (seconds) to *acc.
+static jetsci_status add_elapsed(cudaEvent_t a, cudaEvent_t b, double *acc) {
+    float ms = 0.0f;
+    JETSCI_CUDA_TRY(cudaEventSynchronize(b));
+    JETSCI_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+    *acc += 1e-3 * (double)ms;
+    return JETSCI_OK;
+}
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + 255) / 256); }
 
@@ -182,18 +195,22 @@ extern "C" jetsci_status jetsci_newton_solve(jetsci_mesh m, double *u, int64_t n
     JETSCI_CUDA_TRY(cudaMalloc(&w.sc, sizeof(CgScalars)));
     JETSCI_CUDA_TRY(cudaMalloc(&w.fixed, n));
     JETSCI_CUDA_TRY(cudaMalloc(&w.vals, m->nnz * (f32 ? 4 : 8) + 8));
+    for (cudaEvent_t &e : w.ev) JETSCI_CUDA_TRY(cudaEventCreate(&e));
     JETSCI_CUDA_TRY(cudaMemsetAsync(w.fixed, 0, n, s));
     if (n_bc) k_set_bc<<<blocks(n_bc), 256, 0, s>>>(bc_dofs, bc_vals, n_bc, n, u, w.fixed);
     double nrm0 = 0.0;
     int total_cg = 0;
     for (int it = 0; it <= max_newton; it++) {
         // FP64 residual on the free DOFs decides convergence
+        JETSCI_CUDA_TRY(cudaEventRecord(w.ev[0], s));
         if ((st = launch_residual(m, u, w.R, JETSCI_FP64, nullptr, s))) return st;
         k_zero_masked<<<blocks(n), 256, 0, s>>>(w.R, w.fixed, n);
         if ((st = launch_norm2(w.R, n, w.partials, kNormMaxPartials, w.scal_norm, s))) return st;
+        JETSCI_CUDA_TRY(cudaEventRecord(w.ev[1], s));
         double nrm = 0.0;
         JETSCI_CUDA_TRY(cudaMemcpyAsync(&nrm, w.scal_norm, 8, cudaMemcpyDeviceToHost, s));
         JETSCI_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((st = add_elapsed(w.ev[0], w.ev[1], &info->seconds_residual))) return st;
         if (!std::isfinite(nrm)) return fail(JETSCI_ERR_NONFINITE, "non-finite residual norm");
         if (it == 0) nrm0 = nrm;
         const double rel = nrm0 > 0 ? nrm / nrm0 : 0.0;
@@ -204,11 +221,14 @@ extern "C" jetsci_status jetsci_newton_solve(jetsci_mesh m, double *u, int64_t n
         if (rel <= rtol || nrm == 0.0) return JETSCI_OK;
         if (it == max_newton) break;
         // tangent and Jacobi preconditioner
+        JETSCI_CUDA_TRY(cudaEventRecord(w.ev[2], s));
         if ((st = launch_tangent(m, u, w.vals, nullptr, tangent_precision, nullptr, s))) return st;
         if (f32)
             k_jacobi<float><<<blocks(n), 256, 0, s>>>(m->d_rowptr, m->d_col, (const float *)w.vals, w.fixed, n, w.dinv);
         else
             k_jacobi<double><<<blocks(n), 256, 0, s>>>(m->d_rowptr, m->d_col, (const double *)w.vals, w.fixed, n, w.dinv);
+        JETSCI_CUDA_TRY(cudaEventRecord(w.ev[3], s));
+        if ((st = add_elapsed(w.ev[2], w.ev[3], &info->seconds_tangent))) return st;
         // CG on K x = -R (free block), x0 = 0
         JETSCI_CUDA_TRY(cudaMemsetAsync(w.x, 0, n * 8, s));
         JETSCI_CUDA_TRY(cudaMemcpyAsync(w.r, w.R, n * 8, cudaMemcpyDeviceToDevice, s));
@@ -241,6 +261,8 @@ extern "C" jetsci_status jetsci_newton_solve(jetsci_mesh m, double *u, int64_t n
         total_cg += k;
         if (k >= max_cg) info->cg_capped++;
         k_axpy<<<blocks(n), 256, 0, s>>>(1.0, w.x, u, n);
+        JETSCI_CUDA_TRY(cudaEventRecord(w.ev[0], s));
+        if ((st = add_elapsed(w.ev[3], w.ev[0], &info->seconds_solve))) return st;
         JETSCI_CUDA_TRY(cudaGetLastError());
     }
     info->cg_iters_total = total_cg;

@@ -29,7 +29,8 @@ EXPORTS = [
     "jetsci_mesh_create", "jetsci_mesh_destroy", "jetsci_mesh_info", "jetsci_mesh_check",
     "jetsci_mesh_copy_pattern",
     "jetsci_residual", "jetsci_tangent_csr", "jetsci_apply_tangent", "jetsci_material_grad",
-    "jetsci_norm2", "jetsci_norm2_static", "jetsci_last_error", "jetsci_version",
+    "jetsci_assemble_element_blocks", "jetsci_norm2", "jetsci_norm2_static", "jetsci_last_error",
+    "jetsci_version",
 ]
 
 
@@ -62,6 +63,7 @@ def _load():
         "jetsci_tangent_csr": [_vp, _vp, _vp, _vp, i32, _vp, _vp],
         "jetsci_apply_tangent": [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp],
         "jetsci_material_grad": [_vp, _vp, _vp, _vp, _vp, i32, _vp],
+        "jetsci_assemble_element_blocks": [_vp, _vp, _vp, i32, _vp],
         "jetsci_norm2": [_vp, _vp, i64, _vp, _vp],
         "jetsci_norm2_static": [_vp, i64, _vp, _vp],
     }
@@ -183,6 +185,19 @@ class Mesh:
         _dev_f64(E_elem, self.n_elem, "E_elem")
         _check(lib.jetsci_tangent_csr(self._h, _ptr(u), _ptr(vals), _ptr(R), precision, _ptr(E_elem),
                                       _stream(stream)))
+        return vals
+
+    def assemble_blocks(self, Ke, vals=None, stream=None):
+        """CSR values sum_e P_e^T K_e P_e from caller-formed element blocks Ke [n_elem][24][24]
+        (float64 -> FP64 values, float32 -> FP32 values)."""
+        if Ke.dtype not in (torch.float64, torch.float32) or not Ke.is_cuda or not Ke.is_contiguous() \
+                or tuple(Ke.shape) != (self.n_elem, 24, 24):
+            raise ValueError("Ke: contiguous CUDA float64/float32 tensor of shape [n_elem, 24, 24] expected")
+        precision = FP64 if Ke.dtype == torch.float64 else FP32
+        vals = self.new_values(precision) if vals is None else vals
+        if vals.dtype != Ke.dtype or vals.numel() != self.nnz or not vals.is_cuda:
+            raise ValueError("vals: wrong dtype/size/device")
+        _check(lib.jetsci_assemble_element_blocks(self._h, _ptr(Ke), _ptr(vals), precision, _stream(stream)))
         return vals
 
     def apply_tangent(self, u, v, y=None, mode=MATRIX_FREE, vals=None, precision=FP64, E_elem=None,
@@ -398,7 +413,8 @@ def attach_surrogate(mesh, surrogate):
 # ---------------------------------------------------------------------- Newton driver
 class NewtonInfo(C.Structure):
     _fields_ = [("newton_iters", C.c_int32), ("cg_iters_total", C.c_int32), ("cg_capped", C.c_int32),
-                ("reserved", C.c_int32), ("final_rel_residual", C.c_double), ("residual_history", C.c_double * 32)]
+                ("reserved", C.c_int32), ("final_rel_residual", C.c_double), ("residual_history", C.c_double * 32),
+                ("seconds_residual", C.c_double), ("seconds_tangent", C.c_double), ("seconds_solve", C.c_double)]
 
 
 lib.jetsci_newton_solve.argtypes = [_vp, _vp, C.c_int64, _vp, _vp, C.c_int32, C.c_double, C.c_int32, C.c_double,
