@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
 // FP64 elements, bound by B300's FP64 pipe, also store c lam g_a and c m g_a, so that an
 // off-diagonal pair costs 21 multiply-adds per Gauss point instead of 27; FP32 and two-float
 // elements keep the smaller record, which leaves room for more resident blocks.
-constexpr int kTanElems = 16;  // elements per 128-thread block
 
 // Shared memory: one array per per-node vector (g, tg and, for FP64, c lam g and c m g), each
 // [element][Gauss point][node][3], nodes 3 entries apart, so that the eight nodes of an element
@@ -85,10 +84,14 @@ constexpr int kTanElems = 16;  // elements per 128-thread block
 template <typename T>
 struct TangentLayout {
     static constexpr bool kPre = std::is_same<T, double>::value;
+    // Elements per block (one thread per element and Gauss point).  Measured at 128^3: 8 (two
+    // warps) is 4-5% faster than 16 for FP64 and FP32; the two-float kernel needs 16.
+    static constexpr int kElems = std::is_same<T, df64>::value ? 16 : 8;
+    static constexpr int kThreads = 8 * kElems;
     static constexpr int kNumVec = kPre ? 4 : 2;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
-    static constexpr int kArr = kTanElems * kElem;
+    static constexpr int kArr = kElems * kElem;
     // per (element, Gauss point): c lam, c m, c Tg (00,11,22,12,02,01); odd stride
     static constexpr int kCoef = 9;
     enum { kG = 0, kTG = 1, kLG = 2, kMG = 3 };
@@ -97,13 +100,13 @@ struct TangentLayout {
 template <typename T>
 struct TangentSmem {
     T v[TangentLayout<T>::kNumVec * TangentLayout<T>::kArr];
-    T coef[kTanElems * 8 * TangentLayout<T>::kCoef];
-    int32_t node[kTanElems][8];
-    int32_t elem[kTanElems];
+    T coef[TangentLayout<T>::kElems * 8 * TangentLayout<T>::kCoef];
+    int32_t node[TangentLayout<T>::kElems][8];
+    int32_t elem[TangentLayout<T>::kElems];
 };
 
 template <typename T, typename VT>
-__global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__restrict__ u,
+__global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs A, const double *__restrict__ u,
                                                  const int64_t *__restrict__ rowptr,
                                                  const uint8_t *__restrict__ slotmap,
                                                  VT *__restrict__ vals, double *__restrict__ R) {
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__res
     TangentSmem<T> &sm = *reinterpret_cast<TangentSmem<T> *>(smem_raw);
     const int l = threadIdx.x & 7;
     const int es = threadIdx.x >> 3;
-    const int64_t slot = (int64_t)blockIdx.x * kTanElems + es;
+    const int64_t slot = (int64_t)blockIdx.x * L::kElems + es;
     const bool active = slot < A.n;
     const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
     {
@@ -215,9 +218,9 @@ __global__ void __launch_bounds__(128) k_tangent(ElemArgs A, const double *__res
     // kind, so neither the residual (diagonal pairs only) nor the symmetric diagonal block leaves
     // lanes predicated off, and an element's diagonal blocks follow its other blocks closely.
     constexpr int kGroup = 8, kGroupItems = kGroup * 36, kGroupOff = kGroup * 28;
-    static_assert(kTanElems % kGroup == 0 && kGroupOff % 32 == 0 && kGroupItems % 32 == 0,
+    static_assert(L::kElems % kGroup == 0 && kGroupOff % 32 == 0 && kGroupItems % 32 == 0,
                   "items of one kind per warp");
-    for (int it = threadIdx.x; it < kTanElems * 36; it += blockDim.x) {
+    for (int it = threadIdx.x; it < L::kElems * 36; it += blockDim.x) {
         const int grp = it / kGroupItems, r = it - kGroupItems * grp;
         const bool off = r < kGroupOff;
         int ee, a, b;
@@ -560,7 +563,7 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
                                      cudaStream_t s) {
     const size_t smem = sizeof(TangentSmem<T>);
     JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // The FP64 block (112 KB) fits twice per SM only with the largest shared-memory carveout.
+    // The FP64 tangent needs 56 KB of shared memory per 8-element block: take the largest carveout.
     JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared));
     // One launch per colour.  Splitting colours into L2-sized chunks (chunk-major order) was
@@ -569,8 +572,8 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
     for_colour_chunks(m, 1, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
-        unsigned grid = (unsigned)((A.n + kTanElems - 1) / kTanElems);
-        k_tangent<T, VT><<<grid, 128, smem, s>>>(A, u, m->d_rowptr, m->d_slot, vals, R);
+        unsigned grid = (unsigned)((A.n + TangentLayout<T>::kElems - 1) / TangentLayout<T>::kElems);
+        k_tangent<T, VT><<<grid, TangentLayout<T>::kThreads, smem, s>>>(A, u, m->d_rowptr, m->d_slot, vals, R);
     });
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
