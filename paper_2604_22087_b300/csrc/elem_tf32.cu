@@ -8,6 +8,10 @@
 // Zt = blockdiag(c W D) Bt.  Four elements share one tcgen05.mma of M = 128 (96 rows used),
 // N = 96, K = 48 (6 instructions of K = 8); of its output only the four diagonal 24 x 24 blocks
 // are kept.  The geometric term delta_ik (G_a . c S G_b) is added in the epilogue.
+//
+// One CTA = one such group: warp 0 (4 elements x 8 Gauss points) forms the operands, the MMA
+// runs, and all four warps read one accumulator row each.  At about 53 KB of shared memory and
+// 128 TMEM columns four CTAs share an SM; 16 elements per CTA (one CTA per SM) was 1.65x slower.
 #include <cuda_runtime.h>
 
 #include "element.cuh"
@@ -16,8 +20,9 @@
 
 namespace jetsci {
 
-constexpr int kTfElems = 16;           // elements per CTA (8 Gauss points each = 128 threads)
-constexpr int kTfGroups = 4;           // MMA groups of 4 elements
+constexpr int kTfElems = 4;            // elements per CTA (warp 0 forms the operands)
+constexpr int kTfGroups = 1;           // MMA groups of 4 elements per CTA
+constexpr uint32_t kTfTmemCols = 128;  // 96 accumulator columns per group, allocated as a power of 2
 constexpr int kTfK = 48;               // 8 Gauss points x 6 Voigt components
 // Operand tiles use padded core-matrix strides: 144 B between core matrices along K (16 B of
 // padding) and 12 x 144 B between 8-row blocks.  With the fill pattern below (four elements x
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     const int t = threadIdx.x;
     const int l = t & 7, es = t >> 3;
     const int grp = es >> 2, el = es & 3;  // MMA group and element slot within it
-    if (t < 32) tc::tmem_alloc(&sm.tmem_base, 512);
+    if (t < 32) tc::tmem_alloc(&sm.tmem_base, kTfTmemCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
         tc::fence_mbar_init();
@@ -83,101 +88,104 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         const int g = i / (32 * kTfK), rem = i % (32 * kTfK);
         *reinterpret_cast<float *>(sm.A[g] + tf32_offset(96 + rem / kTfK, rem % kTfK)) = 0.0f;
     }
-    const int64_t slot = (int64_t)blockIdx.x * kTfElems + es;
-    const bool active = slot < A.n;
-    const int64_t e = A.elems[active ? slot : A.n - 1];
-    // ---------------- phase 1: thread = (element, Gauss point)
-    int32_t node;
-    GaussKinematics<float> K;
-    float cu[3];
-    gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
-    ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
-    float H[3][3];
-    displacement_gradient(K, H);
-    Constitutive<float> c;
-    constitutive<float>(mt.law, (float)mt.lam, (float)mt.mu, H, c);
-    const bool lin = mt.law == JETSCI_LINEAR_ELASTIC;
-    if (MODE == 0 && R) {
-        float f[3];
-        nodal_force(c.P, K, l, f);
-        if (active)
+    // ---------------- phase 1: thread = (element, Gauss point), warps holding elements only
+    if (es < kTfElems) {
+        const int64_t slot = (int64_t)blockIdx.x * kTfElems + es;
+        const bool active = slot < A.n;
+        const int64_t e = A.elems[active ? slot : A.n - 1];
+        int32_t node;
+        GaussKinematics<float> K;
+        float cu[3];
+        gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
+        ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
+        float H[3][3];
+        displacement_gradient(K, H);
+        Constitutive<float> c;
+        constitutive<float>(mt.law, (float)mt.lam, (float)mt.mu, H, c);
+        const bool lin = mt.law == JETSCI_LINEAR_ELASTIC;
+        if (MODE == 0 && R) {
+            float f[3];
+            nodal_force(c.P, K, l, f);
+            if (active)
 #pragma unroll
-            for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
-    }
-    if (active) {
-        uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
-        if (bits) atomicOr(A.flags, bits);
-    }
-    // Voigt tangent D (dS/dE w.r.t. tensor components) and the kinematic F of B
-    float D[6][6];
-    if (lin) {
-#pragma unroll
-        for (int a = 0; a < 6; a++)
-#pragma unroll
-            for (int b = 0; b < 6; b++)
-                D[a][b] = (a < 3 && b < 3 ? c.lam : 0.0f) + (a == b ? 2.0f * c.m : 0.0f);
-    } else {
-        float Ci[3][3];
-#pragma unroll
-        for (int I = 0; I < 3; I++)
-#pragma unroll
-            for (int Kk = 0; Kk < 3; Kk++)
-                Ci[I][Kk] = c.Fi[I][0] * c.Fi[Kk][0] + c.Fi[I][1] * c.Fi[Kk][1] + c.Fi[I][2] * c.Fi[Kk][2];
-#pragma unroll
-        for (int a = 0; a < 6; a++) {
-            const int I = voigt_i(a), Jj = voigt_j(a);
-#pragma unroll
-            for (int b = 0; b < 6; b++) {
-                const int Kk = voigt_i(b), L = voigt_j(b);
-                float w = c.lam * Ci[I][Jj] * Ci[Kk][L] + c.m * (Ci[I][Kk] * Ci[Jj][L] + Ci[I][L] * Ci[Jj][Kk]);
-                D[a][b] = (Kk == L) ? w : 2.0f * w;
-            }
+                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
         }
-    }
-    const float cw = K.dJ * (1.0f / 512.0f);
-    const float rdJ = 1.0f / K.dJ;
-#pragma unroll
-    for (int a = 0; a < 6; a++) sm.cS[es][l][a] = lin ? 0.0f : cw * c.S[voigt_i(a)][voigt_j(a)];
-    // B_b and Z_b = c W D B_b for every node b, written at k = 6q + alpha
-    unsigned char *At = sm.A[grp];
-    unsigned char *Bt = sm.B[grp];
-#pragma unroll
-    for (int b = 0; b < 8; b++) {
-        const int nb = hex_node_of_lane(b);
-        const float s0 = (nb & 1) ? 1.0f : -1.0f, s1 = (nb & 2) ? 1.0f : -1.0f, s2 = (nb & 4) ? 1.0f : -1.0f;
-        const float fx = 1.0f + s0 * K.xi, fy = 1.0f + s1 * K.eta, fz = 1.0f + s2 * K.zeta;
-        const float n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
-        float G[3];
-#pragma unroll
-        for (int j = 0; j < 3; j++) G[j] = (K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2) * rdJ;
-#pragma unroll
-        for (int j = 0; j < 3; j++) sm.G[es][l][b][j] = G[j];
-        float Bb[6][3];
-#pragma unroll
-        for (int a = 0; a < 6; a++) {
-            const int I = voigt_i(a), Jj = voigt_j(a);
-#pragma unroll
-            for (int i = 0; i < 3; i++) Bb[a][i] = 0.5f * (c.F[i][I] * G[Jj] + c.F[i][Jj] * G[I]);
+        if (active) {
+            uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
+            if (bits) atomicOr(A.flags, bits);
         }
+        // Voigt tangent D (dS/dE w.r.t. tensor components) and the kinematic F of B
+        float D[6][6];
+        if (lin) {
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            const int row = 24 * el + 3 * b + i;
+            for (int a = 0; a < 6; a++)
+#pragma unroll
+                for (int b = 0; b < 6; b++)
+                    D[a][b] = (a < 3 && b < 3 ? c.lam : 0.0f) + (a == b ? 2.0f * c.m : 0.0f);
+        } else {
+            float Ci[3][3];
+#pragma unroll
+            for (int I = 0; I < 3; I++)
+#pragma unroll
+                for (int Kk = 0; Kk < 3; Kk++)
+                    Ci[I][Kk] = c.Fi[I][0] * c.Fi[Kk][0] + c.Fi[I][1] * c.Fi[Kk][1] + c.Fi[I][2] * c.Fi[Kk][2];
 #pragma unroll
             for (int a = 0; a < 6; a++) {
-                float z = 0.0f;
+                const int I = voigt_i(a), Jj = voigt_j(a);
 #pragma unroll
-                for (int bb = 0; bb < 6; bb++) z += D[a][bb] * Bb[bb][i];
-                const float wgt = a < 3 ? cw : 2.0f * cw;
-                *reinterpret_cast<float *>(At + tf32_offset(row, 6 * l + a)) = to_tf32(Bb[a][i]);
-                *reinterpret_cast<float *>(Bt + tf32_offset(row, 6 * l + a)) = to_tf32(wgt * z);
+                for (int b = 0; b < 6; b++) {
+                    const int Kk = voigt_i(b), L = voigt_j(b);
+                    float w = c.lam * Ci[I][Jj] * Ci[Kk][L] + c.m * (Ci[I][Kk] * Ci[Jj][L] + Ci[I][L] * Ci[Jj][Kk]);
+                    D[a][b] = (Kk == L) ? w : 2.0f * w;
+                }
             }
         }
-    }
-    sm.node[es][hex_node_of_lane(l)] = node;
-    if (MODE == 1)
+        const float cw = K.dJ * (1.0f / 512.0f);
+        const float rdJ = 1.0f / K.dJ;
 #pragma unroll
-        for (int k = 0; k < 3; k++) sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
-    if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+        for (int a = 0; a < 6; a++) sm.cS[es][l][a] = lin ? 0.0f : cw * c.S[voigt_i(a)][voigt_j(a)];
+        // B_b and Z_b = c W D B_b for every node b, written at k = 6q + alpha
+        unsigned char *At = sm.A[grp];
+        unsigned char *Bt = sm.B[grp];
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const int nb = hex_node_of_lane(b);
+            const float s0 = (nb & 1) ? 1.0f : -1.0f, s1 = (nb & 2) ? 1.0f : -1.0f, s2 = (nb & 4) ? 1.0f : -1.0f;
+            const float fx = 1.0f + s0 * K.xi, fy = 1.0f + s1 * K.eta, fz = 1.0f + s2 * K.zeta;
+            const float n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
+            float G[3];
+#pragma unroll
+            for (int j = 0; j < 3; j++) G[j] = (K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2) * rdJ;
+#pragma unroll
+            for (int j = 0; j < 3; j++) sm.G[es][l][b][j] = G[j];
+            float Bb[6][3];
+#pragma unroll
+            for (int a = 0; a < 6; a++) {
+                const int I = voigt_i(a), Jj = voigt_j(a);
+#pragma unroll
+                for (int i = 0; i < 3; i++) Bb[a][i] = 0.5f * (c.F[i][I] * G[Jj] + c.F[i][Jj] * G[I]);
+            }
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const int row = 24 * el + 3 * b + i;
+#pragma unroll
+                for (int a = 0; a < 6; a++) {
+                    float z = 0.0f;
+#pragma unroll
+                    for (int bb = 0; bb < 6; bb++) z += D[a][bb] * Bb[bb][i];
+                    const float wgt = a < 3 ? cw : 2.0f * cw;
+                    *reinterpret_cast<float *>(At + tf32_offset(row, 6 * l + a)) = to_tf32(Bb[a][i]);
+                    *reinterpret_cast<float *>(Bt + tf32_offset(row, 6 * l + a)) = to_tf32(wgt * z);
+                }
+            }
+        }
+        sm.node[es][hex_node_of_lane(l)] = node;
+        if (MODE == 1)
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
+        if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+    }
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (t < 32) tc::tmem_dealloc(tm, 512);
+    if (t < 32) tc::tmem_dealloc(tm, kTfTmemCols);
 }
 
 jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float *vals, double *R, double *y,
