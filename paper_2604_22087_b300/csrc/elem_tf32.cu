@@ -9,8 +9,9 @@
 // N = 96, K = 48 (6 instructions of K = 8); of its output only the four diagonal 24 x 24 blocks
 // are kept.  The geometric term delta_ik (G_a . c S G_b) is added in the epilogue.
 //
-// One CTA = one such group: warp 0 (4 elements x 8 Gauss points) forms the operands, the MMA
-// runs, and all four warps read one accumulator row each.  At about 53 KB of shared memory and
+// One CTA = one such group: each warp evaluates the 4 elements x 8 Gauss points and forms the
+// operand rows of two of the eight nodes, the MMA runs, and all four warps read one accumulator
+// row each.  At about 53 KB of shared memory and
 // 128 TMEM columns four CTAs share an SM; 16 elements per CTA (one CTA per SM) was 1.65x slower.
 #include <cuda_runtime.h>
 
@@ -20,7 +21,7 @@
 
 namespace jetsci {
 
-constexpr int kTfElems = 4;            // elements per CTA (warp 0 forms the operands)
+constexpr int kTfElems = 4;            // elements per CTA
 constexpr int kTfGroups = 1;           // MMA groups of 4 elements per CTA
 constexpr uint32_t kTfTmemCols = 128;  // 96 accumulator columns per group, allocated as a power of 2
 constexpr int kTfK = 48;               // 8 Gauss points x 6 Voigt components
@@ -75,9 +76,12 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
                                               float *__restrict__ vals, double *__restrict__ R, double *__restrict__ y) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Tf32Smem &sm = *reinterpret_cast<Tf32Smem *>(smem_raw);
+    static_assert(kTfElems == 4 && kTfGroups == 1, "one MMA group of four elements per CTA");
     const int t = threadIdx.x;
-    const int l = t & 7, es = t >> 3;
-    const int grp = es >> 2, el = es & 3;  // MMA group and element slot within it
+    // Every warp covers all four elements (lane = element slot x Gauss point); warp w forms the
+    // operand rows of nodes 2w and 2w+1, warp 0 also the residual and the per-element records.
+    const int w = t >> 5, l = t & 7, es = (t >> 3) & 3;
+    const int grp = 0, el = es;
     if (t < 32) tc::tmem_alloc(&sm.tmem_base, kTfTmemCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
@@ -88,8 +92,8 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         const int g = i / (32 * kTfK), rem = i % (32 * kTfK);
         *reinterpret_cast<float *>(sm.A[g] + tf32_offset(96 + rem / kTfK, rem % kTfK)) = 0.0f;
     }
-    // ---------------- phase 1: thread = (element, Gauss point), warps holding elements only
-    if (es < kTfElems) {
+    // ---------------- phase 1: thread = (element, Gauss point) in every warp
+    {
         const int64_t slot = (int64_t)blockIdx.x * kTfElems + es;
         const bool active = slot < A.n;
         const int64_t e = A.elems[active ? slot : A.n - 1];
@@ -103,14 +107,14 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         Constitutive<float> c;
         constitutive<float>(mt.law, (float)mt.lam, (float)mt.mu, H, c);
         const bool lin = mt.law == JETSCI_LINEAR_ELASTIC;
-        if (MODE == 0 && R) {
+        if (MODE == 0 && R && w == 0) {
             float f[3];
             nodal_force(c.P, K, l, f);
             if (active)
 #pragma unroll
                 for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
         }
-        if (active) {
+        if (active && w == 0) {
             uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
             if (bits) atomicOr(A.flags, bits);
         }
@@ -142,13 +146,15 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         }
         const float cw = K.dJ * (1.0f / 512.0f);
         const float rdJ = 1.0f / K.dJ;
+        if (w == 0)
 #pragma unroll
-        for (int a = 0; a < 6; a++) sm.cS[es][l][a] = lin ? 0.0f : cw * c.S[voigt_i(a)][voigt_j(a)];
-        // B_b and Z_b = c W D B_b for every node b, written at k = 6q + alpha
+            for (int a = 0; a < 6; a++) sm.cS[es][l][a] = lin ? 0.0f : cw * c.S[voigt_i(a)][voigt_j(a)];
+        // B_b and Z_b = c W D B_b for this warp's nodes b, written at k = 6q + alpha
         unsigned char *At = sm.A[grp];
         unsigned char *Bt = sm.B[grp];
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
+        for (int bi = 0; bi < 2; bi++) {
+            const int b = 2 * w + bi;
             const int nb = hex_node_of_lane(b);
             const float s0 = (nb & 1) ? 1.0f : -1.0f, s1 = (nb & 2) ? 1.0f : -1.0f, s2 = (nb & 4) ? 1.0f : -1.0f;
             const float fx = 1.0f + s0 * K.xi, fy = 1.0f + s1 * K.eta, fz = 1.0f + s2 * K.zeta;
@@ -179,12 +185,14 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
                 }
             }
         }
-        sm.node[es][hex_node_of_lane(l)] = node;
-        if (MODE == 1)
+        if (w == 0) {
+            sm.node[es][hex_node_of_lane(l)] = node;
+            if (MODE == 1)
 #pragma unroll
-            for (int k = 0; k < 3; k++)
-                sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
-        if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+                for (int k = 0; k < 3; k++)
+                    sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
+            if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+        }
     }
     tc::fence_smem_to_async();
     tc::fence_before_sync();
