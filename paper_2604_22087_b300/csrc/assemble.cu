@@ -569,7 +569,7 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
     // One launch per colour.  Splitting colours into L2-sized chunks (chunk-major order) was
     // measured slower at 128^3 for every precision: the 8x more, smaller launches lose more
     // in launch tails than the L2-resident read-modify-writes gain.
-    for_colour_chunks(m, 1, [&](const int32_t *elems, int64_t n) {
+    for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + TangentLayout<T>::kElems - 1) / TangentLayout<T>::kElems);

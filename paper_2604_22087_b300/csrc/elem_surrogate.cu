@@ -312,7 +312,7 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
     if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     JETSCI_CUDA_TRY(cudaMemsetAsync(m->d_fallback, 0, sizeof(uint32_t), s));
     const SurrogateConfig cfg = surrogate_config(sg);
-    for_colour_chunks(m, 1, [&](const int32_t *elems, int64_t n) {
+    for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + 15) / 16);

@@ -300,7 +300,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
         JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     }
-    for_colour_chunks(m, 1, [&](const int32_t *elems, int64_t n) {
+    for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + kTfElems - 1) / kTfElems);

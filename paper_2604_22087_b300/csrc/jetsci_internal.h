@@ -68,29 +68,15 @@ jetsci_status cuda_fail(cudaError_t err, const char *what);
 // the stream; returns JETSCI_OK or an error.
 jetsci_status enter(jetsci_mesh m, void *stream, cudaStream_t *s);
 
-// Number of chunks each colour's element list is split into so that the CSR rows one chunk
-// (of every colour) touches fit in L2: about `value_bytes` per stored CSR value times 245
-// values per element (the unique non-zeros per hex8 element of a structured mesh), against
-// a budget of 64 MB.  1 for tiny meshes.
-inline int l2_chunks(jetsci_mesh m, int value_bytes) {
-    const double bytes = (double)m->n_elem * 245.0 * value_bytes;
-    int c = (int)(bytes / (64.0 * 1024 * 1024)) + 1;
-    return c < 1 ? 1 : (c > 64 ? 64 : c);
-}
-
-// Calls f(elems, n) for every launch range in chunk-major order: chunk 0 of every colour,
-// then chunk 1, ...  Within one range no two elements share a node (one colour); ranges are
-// launched in a fixed order on one stream, so the scatter stays race-free and deterministic.
-// On meshes numbered in spatial order, one chunk of all colours covers one slab of elements,
-// so its read-modify-writes of CSR rows hit L2 instead of streaming the whole matrix per colour.
+// Calls f(elems, n) for the element list of every colour in colour order.  Within one list no
+// two elements share a node; the lists are launched in a fixed order on one stream, so the
+// scatters stay race-free and deterministic.
 template <typename Fn>
-inline void for_colour_chunks(jetsci_mesh m, int n_chunks, Fn f) {
-    for (int ch = 0; ch < n_chunks; ch++)
-        for (int c = 0; c < m->n_colours; c++) {
-            const int64_t len = m->colour_ptr[c + 1] - m->colour_ptr[c];
-            const int64_t b = len * ch / n_chunks, e = len * (ch + 1) / n_chunks;
-            if (e > b) f(m->d_colour_elems + m->colour_ptr[c] + b, e - b);
-        }
+inline void for_each_colour(jetsci_mesh m, Fn f) {
+    for (int c = 0; c < m->n_colours; c++) {
+        const int64_t len = m->colour_ptr[c + 1] - m->colour_ptr[c];
+        if (len > 0) f(m->d_colour_elems + m->colour_ptr[c], len);
+    }
 }
 
 // Launch wrappers implemented in the .cu files.
