@@ -65,7 +65,7 @@ struct __align__(128) MlpTileSmem {
     unsigned char tan[3][128 * 64 * 2];  // tangent rows of the round's three directions
     float b[3][64];
     float b4[8];
-    float w1[64][8];                     // FP32 W1 (tangent seeds)
+    float w1t[8][64];                    // FP32 W1 transposed (tangent seeds), [input][unit]
     uint64_t mbar;
     uint32_t tmem_base;
 };
@@ -83,7 +83,17 @@ __device__ __forceinline__ void mlp_load_weights(MlpTileSmem &sm, const unsigned
         sm.b[2][i] = params[kOffB3 + i];
     }
     for (int i = t; i < 8; i += blockDim.x) sm.b4[i] = i < 6 ? params[kOffB4 + i] : 0.0f;
-    for (int i = t; i < 512; i += blockDim.x) sm.w1[i >> 3][i & 7] = params[kOffW1 + i];
+    for (int i = t; i < 512; i += blockDim.x) sm.w1t[i & 7][i >> 3] = params[kOffW1 + i];
+}
+
+// 16 consecutive FP32 values from 16-byte aligned shared memory (four vector loads; the
+// bias and seed rows are read by every thread of the tile, a broadcast).
+__device__ __forceinline__ void ld_f32x16(const float *p, float (&v)[16]) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float4 q = reinterpret_cast<const float4 *>(p)[k];
+        v[4 * k] = q.x, v[4 * k + 1] = q.y, v[4 * k + 2] = q.z, v[4 * k + 3] = q.w;
+    }
 }
 
 // Stores 8 consecutive values (columns 8*c8 .. 8*c8+7 of row r) as one 16-byte core-matrix
@@ -138,11 +148,12 @@ __device__ inline bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, fl
             float s[64];
 #pragma unroll
             for (int c0 = 0; c0 < 64; c0 += 16) {
-                float z[16], a[16];
+                float z[16], a[16], bias[16];
                 tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
+                ld_f32x16(&sm.b[layer][c0], bias);
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    silu_and_prime(z[j] + sm.b[layer][c0 + j], a[j], s[c0 + j]);
+                    silu_and_prime(z[j] + bias[j], a[j], s[c0 + j]);
                 }
                 st_bf16x8(sm.act, t, c0 / 8, 64, a);
                 st_bf16x8(sm.act, t, c0 / 8 + 1, 64, a + 8);
@@ -154,8 +165,9 @@ __device__ inline bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, fl
                 for (int c0 = 0; c0 < 64; c0 += 16) {
                     float u[16];
                     if (layer == 0) {
+                        ld_f32x16(&sm.w1t[d][c0], u);
 #pragma unroll
-                        for (int j = 0; j < 16; j++) u[j] = s[c0 + j] * sm.w1[c0 + j][d];
+                        for (int j = 0; j < 16; j++) u[j] *= s[c0 + j];
                     } else {
                         tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (dl + 1) + c0), u);
 #pragma unroll
