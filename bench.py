@@ -157,49 +157,68 @@ def config_dict(prob, n):
 
 
 # ------------------------------------------------------------------------------ CPU oracle
-def cpu_baseline(prob, target_seconds):
-    """The FP64 oracle (single-threaded C, as it stands) on a bounded sample of the same
-    workload: the first M elements in element order (a contiguous slab of the RVE); one step =
-    tangent CSR + residual + element-loop K.v + CSR K.v + norm; pattern setup not timed."""
-    import oracle
+class OracleSlab:
+    """The first m elements of the workload (a contiguous slab of the RVE) set up once for the
+    FP64 oracle (sub-mesh, CSR pattern, u and v restricted to its nodes)."""
 
-    def run(m):
+    def __init__(self, prob, m):
+        import oracle
+        self.m = m
         conn = prob.conn[:m]
         used = np.unique(conn)
         remap = -np.ones(prob.n_nodes, dtype=np.int64)
         remap[used] = np.arange(len(used))
         sub_conn = remap[conn].astype(np.int32)
         dofs = (3 * used[:, None] + np.arange(3)).ravel()
-        om = oracle.Mesh(prob.coords[used], sub_conn, prob.phase[:m], prob.materials)
-        rp, col = oracle.csr_pattern(sub_conn, len(used))
-        u, v = prob.u[dofs], prob.v[dofs]
+        self.om = oracle.Mesh(prob.coords[used], sub_conn, prob.phase[:m], prob.materials)
+        self.rp, self.col = oracle.csr_pattern(sub_conn, len(used))
+        self.u, self.v = prob.u[dofs], prob.v[dofs]
+
+    def step(self):
+        """One step of the oracle (single-threaded C, as it stands): tangent CSR + residual +
+        element-loop K.v + CSR K.v + norm.  Returns seconds."""
+        import oracle
         t0 = time.perf_counter()
-        vals, R = oracle.tangent_csr(om, u, rp, col)
-        oracle.apply_tangent(om, u, v)
-        oracle.spmv(rp, col, vals, v)
+        vals, R = oracle.tangent_csr(self.om, self.u, self.rp, self.col)
+        oracle.apply_tangent(self.om, self.u, self.v)
+        oracle.spmv(self.rp, self.col, vals, self.v)
         oracle.norm2(R)
         return time.perf_counter() - t0
 
-    m = 512
-    dt = run(m)
-    m = int(min(prob.n_elem, max(m, m * target_seconds / max(dt, 1e-6))))
-    dt = run(m)
-    return {"value": m / dt, "unit": "elem/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {m} elements (a contiguous slab) of the same workload, FP64, one step "
+
+def calibrated_slab(prob, target_seconds):
+    """A slab sized so that one oracle step takes about target_seconds, and a 512-element one."""
+    small = OracleSlab(prob, 512)
+    dt = min(small.step() for _ in range(2))
+    m = int(min(prob.n_elem, max(512, 512 * target_seconds / max(dt, 1e-6))))
+    return small, (OracleSlab(prob, m) if m > 512 else small)
+
+
+def baseline_line(slab, dt):
+    return {"value": slab.m / dt, "unit": "elem/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {slab.m} elements (a contiguous slab) of the same workload, FP64, one step "
                       f"(tangent CSR + residual + element K.v + CSR K.v + norm) in {dt:.1f} s"}
+
+
+def cpu_baseline(prob, target_seconds):
+    """The FP64 oracle on a bounded sample of the same workload; slab set-up is not timed."""
+    _, slab = calibrated_slab(prob, target_seconds)
+    return baseline_line(slab, slab.step())
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
     prob = make_problem(args.n)
+    # each timed step is one oracle step over a slab sized to keep the run within minutes
     per = max(1.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
+    small, slab = calibrated_slab(prob, per)
     for _ in range(args.warmup):
-        cpu_baseline(prob, min(per, 2.0))
-    vals = [cpu_baseline(prob, per) for _ in range(args.steps)]
-    v = statistics.median(x["value"] for x in vals)
-    cb = dict(vals[-1])
-    cb["value"] = v
+        small.step()
+    times = [slab.step() for _ in range(args.steps)]
+    dt = statistics.median(times)
+    v = slab.m / dt
+    cb = baseline_line(slab, dt)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elem/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * prob.n_elem / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
