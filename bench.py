@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % of HBM peak"
 
-# Work per element of the dominant kernel, k_tangent<double,double> (derivation in the design doc):
+# Work per element of the dominant kernel, k_tangent<double,double>:
 # executed FP64 operations of the formulation (ncu on the 64^3 fibre RVE: 7,704 DFMA x 2 +
 # 1,420 DADD + 1,536 DMUL per element) and the algorithmic bytes (write-once CSR values + mesh
 # data + u + R).
@@ -543,7 +543,7 @@ def main():
                          "traffic": TANGENT_DRAM_BYTES_PER_ELEM_FP64 * prob.n_elem,
                          "traffic_note": "bytes per tangent call (8 colour launches), ncu at 64^3 scaled by elements",
                          "kernel": "k_tangent<double,double>",
-                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 148 SMs x 2032 MHz (derived in DESIGN.md)",
+                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM (measured FP64 FMA rate) x 2 flop x 148 SMs x the maximum SM clock",
                          "ms_per_launch_group": ms_tangent, "hbm_achieved_gbs": hbm,
                          "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind},
             "e2e": {"value": world * prob.n_elem / (e2e_ms * 1e-3), "unit": "elem/s",
