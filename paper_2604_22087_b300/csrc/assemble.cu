@@ -84,10 +84,11 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
 template <typename T>
 struct TangentLayout {
     static constexpr bool kPre = std::is_same<T, double>::value;
-    // Elements per block (one thread per element and Gauss point).  Measured at 128^3: 8 (two
-    // warps) is 4-5% faster than 16 for FP64 and FP32; the two-float kernel needs 16.
+    // Elements per block (phase 1: one thread per element and Gauss point).  Measured at 128^3:
+    // 8 is 4-5% faster than 16 for FP64 and FP32; the two-float kernel needs 16.  The FP64 block
+    // adds two warps that only join the pair loop (phase 2): 5% faster again (FP32: slower).
     static constexpr int kElems = std::is_same<T, df64>::value ? 16 : 8;
-    static constexpr int kThreads = 8 * kElems;
+    static constexpr int kThreads = kPre ? 128 : 8 * kElems;
     static constexpr int kNumVec = kPre ? 4 : 2;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
     const int64_t slot = (int64_t)blockIdx.x * L::kElems + es;
     const bool active = slot < A.n;
     const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
-    {
+    if (es < L::kElems) {  // warps beyond the element slots join in phase 2 only
         int32_t node;
         GaussKinematics<T> K;
         T cu[3];
