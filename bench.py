@@ -43,7 +43,7 @@ TANGENT_BYTES_PER_ELEM_FP64 = 2_160.0
 # DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
 # coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
-TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 17_837.0
+TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 17_838.0
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
 # index (a node's three rows share one column list); v and y are per-row and stay in L2.
 SPMV_BYTES_PER_NNZ = {"fp64": 8.0 + 4.0 / 3.0, "fp32": 4.0 + 4.0 / 3.0}

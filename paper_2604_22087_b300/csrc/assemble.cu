@@ -86,9 +86,10 @@ struct TangentLayout {
     static constexpr bool kPre = std::is_same<T, double>::value;
     // Elements per block (phase 1: one thread per element and Gauss point).  Measured at 128^3:
     // 8 is 4-5% faster than 16 for FP64 and FP32; the two-float kernel needs 16.  The FP64 block
-    // adds two warps that only join the pair loop (phase 2): 5% faster again (FP32: slower).
+    // adds four warps that only join the pair loop (phase 2): 6% faster again (two warps: 5%,
+    // six: slower; FP32 and two-float: slower with any).
     static constexpr int kElems = std::is_same<T, df64>::value ? 16 : 8;
-    static constexpr int kThreads = kPre ? 128 : 8 * kElems;
+    static constexpr int kThreads = kPre ? 192 : 8 * kElems;
     static constexpr int kNumVec = kPre ? 4 : 2;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
