@@ -36,14 +36,14 @@ METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % o
 
 # Work per element of the dominant kernel, k_tangent<double,double>:
 # executed FP64 operations of the formulation (ncu on the 64^3 fibre RVE: 7,704 DFMA x 2 +
-# 1,396 DADD + 1,536 DMUL per element) and the algorithmic bytes (write-once CSR values + mesh
+# 820 DADD + 1,536 DMUL per element) and the algorithmic bytes (write-once CSR values + mesh
 # data + u + R).
-TANGENT_FP64_FLOP_PER_ELEM = 18_340.0
+TANGENT_FP64_FLOP_PER_ELEM = 17_764.0
 TANGENT_BYTES_PER_ELEM_FP64 = 2_160.0
 # DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
 # coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
-TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 17_838.0
+TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 12_414.0
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
 # index (a node's three rows share one column list); v and y are per-row and stay in L2.
 SPMV_BYTES_PER_NNZ = {"fp64": 8.0 + 4.0 / 3.0, "fp32": 4.0 + 4.0 / 3.0}

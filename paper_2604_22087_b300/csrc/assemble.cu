@@ -31,6 +31,15 @@ __device__ __forceinline__ void raise_flag(uint32_t *flags, uint32_t bits) {
     if (bits) atomicOr(flags, bits);
 }
 
+// CSR scatter of one value: the first writer of a block stores (no read), later writers add.
+template <typename VT>
+__device__ __forceinline__ void put_or_add(VT *dst, VT v, bool first) {
+    if (first)
+        *dst = v;
+    else
+        *dst += v;
+}
+
 // ---------------------------------------------------------------------------- residual
 // R_e(a,i) = sum_q w detJ P_iJ G_aJ, scattered into R (FP64 in every precision); the stress
 // moment comes from residual_moment (spatial form for the neo-Hookean law).
@@ -97,6 +106,11 @@ struct TangentLayout {
     // per (element, Gauss point): c lam, c m, c Tg (00,11,22,12,02,01); odd stride
     static constexpr int kCoef = 9;
     enum { kG = 0, kTG = 1, kLG = 2, kMG = 3 };
+    // FP64 values: each CSR block's first writer stores and no clearing pass is needed (saves
+    // the 4 GB memset at 128^3).  FP32 and two-float were measured slower that way (the
+    // partial-sector first stores and the divergent store/accumulate paths cost more than the
+    // clearing pass), so they clear the array and accumulate.
+    static constexpr bool kFirstWrites = std::is_same<T, double>::value;
 };
 
 template <typename T>
@@ -105,12 +119,14 @@ struct TangentSmem {
     T coef[TangentLayout<T>::kElems * 8 * TangentLayout<T>::kCoef];
     int32_t node[TangentLayout<T>::kElems][8];
     int32_t elem[TangentLayout<T>::kElems];
+    uint8_t first[TangentLayout<T>::kElems][8];  // first-writer bits of each node's blocks (FP64)
 };
 
 template <typename T, typename VT>
 __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs A, const double *__restrict__ u,
                                                  const int64_t *__restrict__ rowptr,
                                                  const uint8_t *__restrict__ slotmap,
+                                                 const uint8_t *__restrict__ first,
                                                  VT *__restrict__ vals, double *__restrict__ R) {
     using L = TangentLayout<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -212,6 +228,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         pc[6] = cw * Tg[0][2];
         pc[7] = cw * Tg[0][1];
         sm.node[es][hex_node_of_lane(l)] = node;
+        sm.first[es][hex_node_of_lane(l)] = first[8 * e + hex_node_of_lane(l)];
         if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
     }
     __syncthreads();
@@ -284,17 +301,20 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             const int32_t nb = sm.node[ee][b];
             const int sab = slotmap[sbase + 8 * a + b];
             const int sba = slotmap[sbase + 8 * b + a];
+            // the block's first writer (lowest colour) stores, later colours accumulate
+            const bool fab = L::kFirstWrites && ((sm.first[ee][a] >> b) & 1);
+            const bool fba = L::kFirstWrites && ((sm.first[ee][b] >> a) & 1);
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
 #pragma unroll
-                for (int k = 0; k < 3; k++) dst[k] += store_as<VT>(Kab[i][k]);
+                for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), fab);
             }
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
 #pragma unroll
-                for (int i = 0; i < 3; i++) dst[i] += store_as<VT>(Kab[i][k]);
+                for (int i = 0; i < 3; i++) put_or_add(dst + i, store_as<VT>(Kab[i][k]), fba);
             }
         } else {
             // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
@@ -334,11 +354,12 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             Kab[0][2] = Kab[2][0] = k02;
             Kab[0][1] = Kab[1][0] = k01;
             const int saa = slotmap[sbase + 9 * a];
+            const bool faa = L::kFirstWrites && ((sm.first[ee][a] >> a) & 1);
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * saa;
 #pragma unroll
-                for (int k = 0; k < 3; k++) dst[k] += store_as<VT>(Kab[i][k]);
+                for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), faa);
             }
             if (R) {
                 const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
@@ -575,7 +596,8 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + TangentLayout<T>::kElems - 1) / TangentLayout<T>::kElems);
-        k_tangent<T, VT><<<grid, TangentLayout<T>::kThreads, smem, s>>>(A, u, m->d_rowptr, m->d_slot, vals, R);
+        k_tangent<T, VT><<<grid, TangentLayout<T>::kThreads, smem, s>>>(A, u, m->d_rowptr, m->d_slot, m->d_first,
+                                                                       vals, R);
     });
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
@@ -584,8 +606,8 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
 jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double *R, int precision,
                              const double *E_elem, cudaStream_t s) {
     ElemArgs A = make_args(m, E_elem);
+    // FP64 needs no clearing of vals (first writers store, TangentLayout::kFirstWrites).
     if (precision == JETSCI_FP64) {
-        JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(double), s));
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
         return tangent_colours<double, double>(m, A, u, (double *)vals, R, s);
     }

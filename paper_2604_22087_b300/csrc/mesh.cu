@@ -88,6 +88,36 @@ __global__ void k_slot_map(int64_t n_elem, const int32_t *__restrict__ conn,
     *reinterpret_cast<uint2 *>(slot + 8 * t) = packed;
 }
 
+// Lowest colour among the elements that contain each node-pair block of the CSR pattern; block
+// ids follow the neighbour lists (block of node a and its neighbour of rank r = nbr_ptr[a] + r).
+__global__ void k_block_min_colour(int64_t n_elem, const int32_t *__restrict__ conn,
+                                   const int64_t *__restrict__ nbr_ptr, const uint8_t *__restrict__ slot,
+                                   const uint8_t *__restrict__ colour, uint32_t *__restrict__ block_min) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_elem * 8) return;
+    int64_t e = t >> 3;
+    const int64_t base = nbr_ptr[conn[t]];
+    const uint32_t c = colour[e];
+#pragma unroll
+    for (int b = 0; b < 8; b++) atomicMin(&block_min[base + slot[8 * t + b]], c);
+}
+
+// first[e*8 + a] bit b = element e is the block (a, b)'s lowest-colour element, i.e. the first
+// to write it in the colour-ordered launches.
+__global__ void k_first_writer(int64_t n_elem, const int32_t *__restrict__ conn,
+                               const int64_t *__restrict__ nbr_ptr, const uint8_t *__restrict__ slot,
+                               const uint8_t *__restrict__ colour, const uint32_t *__restrict__ block_min,
+                               uint8_t *__restrict__ first) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_elem * 8) return;
+    const int64_t base = nbr_ptr[conn[t]];
+    const uint32_t c = colour[t >> 3];
+    uint32_t bits = 0;
+#pragma unroll
+    for (int b = 0; b < 8; b++) bits |= (block_min[base + slot[8 * t + b]] == c ? 1u : 0u) << b;
+    first[t] = (uint8_t)bits;
+}
+
 static void free_mesh(jetsci_mesh m) {
     if (!m) return;
     cudaFree(m->d_conn);
@@ -96,6 +126,7 @@ static void free_mesh(jetsci_mesh m) {
     cudaFree(m->d_rowptr);
     cudaFree(m->d_col);
     cudaFree(m->d_slot);
+    cudaFree(m->d_first);
     cudaFree(m->d_colour_elems);
     cudaFree(m->d_mats);
     cudaFree(m->d_norm_partials);
@@ -233,6 +264,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     if ((st = dev_alloc(&m->d_rowptr, m->n_dof + 1))) return st;
     if ((st = dev_alloc(&m->d_col, m->nnz))) return st;
     if ((st = dev_alloc(&m->d_slot, 64 * n_elem))) return st;
+    if ((st = dev_alloc(&m->d_first, 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_colour_elems, n_elem))) return st;
     if ((st = dev_alloc(&m->d_mats, kMaxPhases))) return st;
     if ((st = dev_alloc(&m->d_norm_partials, kNormMaxPartials))) return st;
@@ -240,9 +272,14 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     if ((st = dev_alloc(&m->d_fallback, 1))) return st;
     int64_t *d_nbr_ptr = nullptr;
     int32_t *d_nbr = nullptr;
-    if ((st = dev_alloc(&d_nbr_ptr, n_nodes + 1))) return st;
-    if ((st = dev_alloc(&d_nbr, nbr.size()))) { cudaFree(d_nbr_ptr); return st; }
-    auto cleanup_tmp = [&]() { cudaFree(d_nbr_ptr); cudaFree(d_nbr); };
+    uint8_t *d_colour = nullptr;
+    uint32_t *d_block_min = nullptr;
+    auto cleanup_tmp = [&]() { cudaFree(d_nbr_ptr); cudaFree(d_nbr); cudaFree(d_colour); cudaFree(d_block_min); };
+    if ((st = dev_alloc(&d_nbr_ptr, n_nodes + 1)) || (st = dev_alloc(&d_nbr, nbr.size())) ||
+        (st = dev_alloc(&d_colour, n_elem)) || (st = dev_alloc(&d_block_min, nbr.size()))) {
+        cleanup_tmp();
+        return st;
+    }
 #define UP(dst, src, bytes)                                                               \
     do {                                                                                  \
         if ((bytes) > 0) {                                                                \
@@ -263,6 +300,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     UP(m->d_mats, m->mats, sizeof(m->mats));
     UP(d_nbr_ptr, nbr_ptr.data(), (n_nodes + 1) * sizeof(int64_t));
     UP(d_nbr, nbr.data(), nbr_ptr[n_nodes] * sizeof(int32_t));
+    UP(d_colour, colour.data(), n_elem * sizeof(uint8_t));
 #undef UP
     {
         cudaError_t e = cudaMemsetAsync(m->d_flags, 0, sizeof(uint32_t), s);
@@ -275,8 +313,13 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
                                                                       m->d_rowptr, m->d_col);
     }
     if (n_elem > 0) {
-        k_slot_map<<<(unsigned)((8 * n_elem + 255) / 256), 256, 0, s>>>(n_elem, m->d_conn, d_nbr_ptr,
-                                                                         d_nbr, m->d_slot);
+        const unsigned g8 = (unsigned)((8 * n_elem + 255) / 256);
+        k_slot_map<<<g8, 256, 0, s>>>(n_elem, m->d_conn, d_nbr_ptr, d_nbr, m->d_slot);
+        cudaError_t e = cudaMemsetAsync(d_block_min, 0xFF, nbr.size() * sizeof(uint32_t), s);
+        if (e != cudaSuccess) { cleanup_tmp(); return cuda_fail(e, "memset block colours"); }
+        k_block_min_colour<<<g8, 256, 0, s>>>(n_elem, m->d_conn, d_nbr_ptr, m->d_slot, d_colour, d_block_min);
+        k_first_writer<<<g8, 256, 0, s>>>(n_elem, m->d_conn, d_nbr_ptr, m->d_slot, d_colour, d_block_min,
+                                          m->d_first);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

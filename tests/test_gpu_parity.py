@@ -159,6 +159,24 @@ def test_material_gradient_fp64():
     assert abs(L.item() - 0.5 * oracle.norm2(R_ref) ** 2) <= 1e-13 * L.item()
 
 
+@pytest.mark.parametrize("name", ["FP64", "FP32", "DF64"])
+def test_tangent_overwrites_every_value(case, name):
+    """The tangent does not clear the value array: each CSR block's first writer (its
+    lowest-colour element) stores, later colours add.  Whatever vals held before must not leak
+    into the result, and every block must be written."""
+    prob, mesh, _, _ = case
+    J = jetsci()
+    p = getattr(J, name)
+    u = cuda(prob.u)
+    a = mesh.new_values(p)
+    a.zero_()
+    mesh.tangent_csr(u, vals=a, precision=p)
+    b = mesh.new_values(p)
+    b.fill_(float("nan"))
+    mesh.tangent_csr(u, vals=b, precision=p)
+    assert torch.equal(a, b)
+
+
 def test_empty_mesh():
     J = jetsci()
     coords = np.zeros((4, 3))
