@@ -94,8 +94,8 @@ typedef struct {
 #define JETSCI_FLAG_NONFINITE 0x4u   /* NaN/Inf met in an input or an intermediate  */
 
 /* ---------------------------------------------------------------------------
- * Mesh: geometry, connectivity, phases and materials ("element information" and
- * "problem structure" of the paper's Fig. 1) plus everything derived once from
+ * Mesh: geometry, connectivity, phases and materials (the element data and problem
+ * structure of the paper's Fig. 1) plus everything derived once from
  * them: the CSR pattern of K (rows = DOFs; per row the columns sorted ascending;
  * DOFs of one node are interleaved so each row's columns come in node-sorted
  * 3-wide blocks), an element colouring (no two elements of one colour share a
