@@ -177,6 +177,41 @@ def test_tangent_overwrites_every_value(case, name):
     assert torch.equal(a, b)
 
 
+def test_shuffled_numbering_general_colouring():
+    """Node ids and element order of a distorted 6x5x4 box shuffled: the greedy colouring is no
+    longer the 8 parity classes, and the pattern, slot map and first-writer masks come from a
+    general mesh.  FP64 residual, tangent (into NaN-filled values), matrix-free and CSR K.v
+    against the oracle."""
+    J = jetsci()
+    coords, conn = I.box_mesh(6, 5, 4, distort=0.25, seed=9)
+    g = np.random.default_rng(9)
+    perm_n = g.permutation(len(coords))  # new id of old node k is inv[k]
+    inv = np.empty_like(perm_n)
+    inv[perm_n] = np.arange(len(coords))
+    coords = coords[perm_n]
+    conn = inv[conn][g.permutation(len(conn))].astype(np.int32)
+    phase = (g.uniform(size=len(conn)) < 0.5).astype(np.int32)
+    prob = I.Problem("shuffled_6x5x4", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                     g.uniform(-3e-3, 3e-3, coords.size), g.uniform(-1, 1, coords.size))
+    mesh = J.Mesh.of(prob)
+    assert mesh.n_colours > 8
+    om = oracle.Mesh.of(prob)
+    rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
+    u, v = cuda(prob.u), cuda(prob.v)
+    R = mesh.new_vector()
+    vals = mesh.new_values(J.FP64)
+    vals.fill_(float("nan"))
+    mesh.tangent_csr(u, vals=vals, R=R)
+    assert relerr(R.cpu().numpy(), R_ref) <= FP64_TOL
+    assert relerr(vals.cpu().numpy(), vals_ref) <= FP64_TOL
+    y_ref = oracle.apply_tangent(om, prob.u, prob.v)
+    assert relerr(mesh.apply_tangent(u, v).cpu().numpy(), y_ref) <= FP64_TOL
+    assert relerr(mesh.apply_tangent(None, v, mode=J.CSR, vals=vals).cpu().numpy(), y_ref) <= FP64_TOL
+    assert mesh.check() == 0
+    mesh.close()
+
+
 def test_empty_mesh():
     J = jetsci()
     coords = np.zeros((4, 3))
@@ -333,6 +368,8 @@ def test_newton_cg_jacobi_converges_to_oracle_solution(tp):
                           rtol=1e-10, cg_rtol=1e-10)
     assert info.final_rel_residual <= 1e-10
     assert info.newton_iters <= (6 if tp == "fp64" else 12)
+    # the device-time split covers every phase that ran
+    assert info.seconds_residual > 0 and info.seconds_tangent > 0 and info.seconds_solve > 0
     u_ref = _oracle_newton(prob, dofs, vals)
     assert relerr(u.cpu().numpy(), u_ref) <= 1e-8
 
