@@ -40,6 +40,7 @@ struct __align__(128) Tf32Smem {
     float G[kTfElems][8][8][3];  // [elem][q][node][comp]
     float cS[kTfElems][8][6];
     float vnode[kTfElems][8][3];  // v at the element's nodes (matrix-free mode), FP32
+    float geo[kTfElems][8][8];    // sum_q G_a . c S G_b (symmetric in a, b)
     int32_t node[kTfElems][8];
     int32_t elem[kTfElems];
     uint64_t mbar;
@@ -211,8 +212,29 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     }
     uint32_t ph = 0;
     if (t == 0) tc::mma_commit(&sm.mbar);
+    // While the MMA runs: the geometric term of every element and node pair a <= b (row a of
+    // the upper triangle starts at 8a - a(a-1)/2), once per pair instead of once per row.
+    for (int it = t; it < kTfElems * 36; it += blockDim.x) {
+        const int ee = it / 36, p = it - 36 * (it / 36);
+        const int a = (p >= 8) + (p >= 15) + (p >= 21) + (p >= 26) + (p >= 30) + (p >= 33) + (p >= 35);
+        const int b = p - (8 * a - (a * (a - 1)) / 2) + a;
+        float g = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float *s6 = sm.cS[ee][q];
+            const float *ga = sm.G[ee][q][a];
+            const float *gb = sm.G[ee][q][b];
+            const float sg0 = s6[0] * ga[0] + s6[5] * ga[1] + s6[4] * ga[2];
+            const float sg1 = s6[5] * ga[0] + s6[1] * ga[1] + s6[3] * ga[2];
+            const float sg2 = s6[4] * ga[0] + s6[3] * ga[1] + s6[2] * ga[2];
+            g += sg0 * gb[0] + sg1 * gb[1] + sg2 * gb[2];
+        }
+        sm.geo[ee][a][b] = g;
+        sm.geo[ee][b][a] = g;
+    }
     const bool ok = tc::mbar_wait_bounded(&sm.mbar, ph & 1);
     tc::fence_after_sync();
+    __syncthreads();  // geometric terms of all threads visible to the epilogue
     if (!ok && t == 0) atomicOr(A.flags, JETSCI_FLAG_NONFINITE);
     // ---------------- epilogue: thread t owns row t of each group's accumulator
     // tcgen05.ld is warp-collective with one column address per warp, and a warp's 32 rows
@@ -241,22 +263,13 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         const int32_t eid = sm.elem[ee];
         if (eid < 0) continue;
         const int a = (t % 24) / 3, i = t % 3;
-        // geometric term on the diagonal of each 3x3 block: sum_q G_a . cS G_b
-#pragma unroll 1
-        for (int q = 0; q < 8; q++) {
-            const float *s6 = sm.cS[ee][q];
-            const float *ga = sm.G[ee][q][a];
-            const float sg0 = s6[0] * ga[0] + s6[5] * ga[1] + s6[4] * ga[2];
-            const float sg1 = s6[5] * ga[0] + s6[1] * ga[1] + s6[3] * ga[2];
-            const float sg2 = s6[4] * ga[0] + s6[3] * ga[1] + s6[2] * ga[2];
+        // geometric term on the diagonal of each 3x3 block
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const float *gb = sm.G[ee][q][b];
-                const float geo = sg0 * gb[0] + sg1 * gb[1] + sg2 * gb[2];
+        for (int b = 0; b < 8; b++) {
+            const float geo = sm.geo[ee][a][b];
 #pragma unroll
-                for (int k = 0; k < 3; k++)
-                    if (k == i) rowv[3 * b + k] += geo;  // compile-time index, predicated
-            }
+            for (int k = 0; k < 3; k++)
+                if (k == i) rowv[3 * b + k] += geo;  // compile-time index, predicated
         }
         const int32_t na = sm.node[ee][a];
         if (MODE == 0) {
