@@ -148,6 +148,13 @@ jetsci_status jetsci_residual(jetsci_mesh mesh, const double *u_dev, double *R_d
  * K_e(a,i)(b,k) = sum_q w_q detJ_q sum_{J,L} G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL.
  * vals_dev [nnz]: double for FP64/DF64, float for FP32/TF32/SURROGATE (overwritten).
  * R_dev [n_dof] FP64 or NULL: if given, the residual is produced by the same pass.
+ * Assembly: FP64 and DF64 scatter element by element, one colour at a time (no two elements
+ * of a colour share a node).  FP32 forms every element's blocks in one pass into a
+ * mesh-owned workspace, then writes each CSR row once, its sum taken over the elements of
+ * the row's node in ascending element order (no atomics in either; results are bitwise
+ * reproducible).  The first FP32 call on a mesh allocates that workspace (1,488 bytes per
+ * element, freed by jetsci_mesh_destroy) and synchronises `stream`; it fails with
+ * JETSCI_ERR_ARG if `stream` is being captured, so make one call before a capture.
  */
 jetsci_status jetsci_tangent_csr(jetsci_mesh mesh, const double *u_dev, void *vals_dev,
                                  double *R_dev, int32_t precision, const double *E_elem_dev,
@@ -298,10 +305,12 @@ jetsci_status jetsci_newton_solve(jetsci_mesh mesh, double *u_dev, int64_t n_bc,
  * INSERT semantics (Section III-C).  The COO order is element-major and implied by the
  * connectivity: entry (e, 3a+i, 3b+k) goes to row 3 conn[e][a] + i, column 3 conn[e][b] + k.
  *   Ke_dev   [n_elem][24][24] row-major, local DOF 3a + i (a = local node in connectivity
- *            order, i = component); double for JETSCI_FP64, float for JETSCI_FP32.
+ *            order, i = component); double for JETSCI_FP64, float for JETSCI_FP32; 16-byte
+ *            aligned (it is read in 16-byte pieces), else JETSCI_ERR_ARG.
  *   vals_dev [nnz] of the same type, overwritten with sum_e P_e^T K_e P_e (rows of
- *            jetsci_mesh_info's pattern).  Sums run colour by colour in a fixed order:
- *            bitwise reproducible, no atomics.
+ *            jetsci_mesh_info's pattern).  Each row is written once: its blocks are summed
+ *            over the elements of the row's node in ascending element order (bitwise
+ *            reproducible, no atomics, no clearing pass).
  * Other precisions -> JETSCI_ERR_ARG.  Asynchronous on `stream`.
  */
 jetsci_status jetsci_assemble_element_blocks(jetsci_mesh mesh, const void *Ke_dev, void *vals_dev, int32_t precision,

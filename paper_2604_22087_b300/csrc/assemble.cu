@@ -6,6 +6,7 @@
 
 #include <type_traits>
 
+#include "blocks.cuh"
 #include "element.cuh"
 #include "jetsci_internal.h"
 
@@ -122,15 +123,25 @@ struct TangentSmem {
     uint8_t first[TangentLayout<T>::kElems][8];  // first-writer bits of each node's blocks (FP64)
 };
 
-template <typename T, typename VT>
+// Offset of the per-warp staging area of the element-block mode in shared memory.
+template <typename T>
+constexpr size_t tangent_stage_offset() { return (sizeof(TangentSmem<T>) + 15) / 16 * 16; }
+
+// kBlocks = false: scatter into the CSR values (vals) and R, one launch per colour.
+// kBlocks = true: the element pass of the row-gather assembly, over all elements in order in
+// one launch; vals is the element-block workspace (blocks.cuh) and R its residual part.  Each
+// warp stages its 32 blocks in shared memory and writes them as one contiguous span.
+template <typename T, typename VT, bool kBlocks>
 __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs A, const double *__restrict__ u,
                                                  const int64_t *__restrict__ rowptr,
                                                  const uint8_t *__restrict__ slotmap,
                                                  const uint8_t *__restrict__ first,
                                                  VT *__restrict__ vals, double *__restrict__ R) {
     using L = TangentLayout<T>;
+    constexpr bool kFirst = L::kFirstWrites && !kBlocks;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TangentSmem<T> &sm = *reinterpret_cast<TangentSmem<T> *>(smem_raw);
+    VT *stage = reinterpret_cast<VT *>(smem_raw + tangent_stage_offset<T>()) + (threadIdx.x >> 5) * (32 * kBlkStride);
     const int l = threadIdx.x & 7;
     const int es = threadIdx.x >> 3;
     const int64_t slot = (int64_t)blockIdx.x * L::kElems + es;
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         pc[6] = cw * Tg[0][2];
         pc[7] = cw * Tg[0][1];
         sm.node[es][hex_node_of_lane(l)] = node;
-        sm.first[es][hex_node_of_lane(l)] = first[8 * e + hex_node_of_lane(l)];
+        sm.first[es][hex_node_of_lane(l)] = kFirst ? first[8 * e + hex_node_of_lane(l)] : 0;
         if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
     }
     __syncthreads();
@@ -256,7 +267,10 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             a = b = j & 7;
         }
         const int32_t eid = sm.elem[ee];
-        if (eid < 0) continue;
+        // (the element-block mode also runs the padding elements of the last block: its warps
+        // store together, and the workspace has room for them)
+        if (!kBlocks && eid < 0) continue;
+        const int64_t eidx = (int64_t)blockIdx.x * L::kElems + ee;  // storage index, element-block mode
         const T *pa = sm.v + ee * L::kElem + 3 * a;
         const T *pb = sm.v + ee * L::kElem + 3 * b;
         const T *pc = sm.coef + ee * 8 * L::kCoef;
@@ -298,23 +312,25 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             Kab[0][0] += gs;
             Kab[1][1] += gs;
             Kab[2][2] += gs;
-            const int32_t nb = sm.node[ee][b];
-            const int sab = slotmap[sbase + 8 * a + b];
-            const int sba = slotmap[sbase + 8 * b + a];
-            // the block's first writer (lowest colour) stores, later colours accumulate
-            const bool fab = L::kFirstWrites && ((sm.first[ee][a] >> b) & 1);
-            const bool fba = L::kFirstWrites && ((sm.first[ee][b] >> a) & 1);
+            if constexpr (!kBlocks) {
+                const int32_t nb = sm.node[ee][b];
+                const int sab = slotmap[sbase + 8 * a + b];
+                const int sba = slotmap[sbase + 8 * b + a];
+                // the block's first writer (lowest colour) stores, later colours accumulate
+                const bool fab = kFirst && ((sm.first[ee][a] >> b) & 1);
+                const bool fba = kFirst && ((sm.first[ee][b] >> a) & 1);
 #pragma unroll
-            for (int i = 0; i < 3; i++) {
-                VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
+                for (int i = 0; i < 3; i++) {
+                    VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
 #pragma unroll
-                for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), fab);
-            }
+                    for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), fab);
+                }
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
+                for (int k = 0; k < 3; k++) {
+                    VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
 #pragma unroll
-                for (int i = 0; i < 3; i++) put_or_add(dst + i, store_as<VT>(Kab[i][k]), fba);
+                    for (int i = 0; i < 3; i++) put_or_add(dst + i, store_as<VT>(Kab[i][k]), fba);
+                }
             }
         } else {
             // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
@@ -353,21 +369,56 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             Kab[1][2] = Kab[2][1] = k12;
             Kab[0][2] = Kab[2][0] = k02;
             Kab[0][1] = Kab[1][0] = k01;
-            const int saa = slotmap[sbase + 9 * a];
-            const bool faa = L::kFirstWrites && ((sm.first[ee][a] >> a) & 1);
+            if constexpr (!kBlocks) {
+                const int saa = slotmap[sbase + 9 * a];
+                const bool faa = kFirst && ((sm.first[ee][a] >> a) & 1);
 #pragma unroll
-            for (int i = 0; i < 3; i++) {
-                VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * saa;
+                for (int i = 0; i < 3; i++) {
+                    VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * saa;
 #pragma unroll
-                for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), faa);
+                    for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), faa);
+                }
             }
             if (R) {
                 const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
-                if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
-                R[3 * (int64_t)na] += to_double(Ra0);
-                R[3 * (int64_t)na + 1] += to_double(Ra1);
-                R[3 * (int64_t)na + 2] += to_double(Ra2);
+                if (!fin && eid >= 0) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
+                if constexpr (kBlocks) {
+                    double *dst = R + 3 * (8 * eidx + a);
+                    dst[0] = to_double(Ra0);
+                    dst[1] = to_double(Ra1);
+                    dst[2] = to_double(Ra2);
+                } else {
+                    R[3 * (int64_t)na] += to_double(Ra0);
+                    R[3 * (int64_t)na + 1] += to_double(Ra1);
+                    R[3 * (int64_t)na + 2] += to_double(Ra2);
+                }
             }
+        }
+        if constexpr (kBlocks) {
+            // the warp's 32 items are 32 consecutive blocks of one group of 8 elements
+            const int lane = threadIdx.x & 31;
+            VT blk[kBlkStride];
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) blk[3 * i + k] = store_as<VT>(Kab[i][k]);
+#pragma unroll
+            for (int c = kBlkVals; c < kBlkStride; c++) blk[c] = VT(0);
+            constexpr int kVecBlk = kBlkStride * (int)sizeof(VT) / 16;
+#pragma unroll
+            for (int c = 0; c < kVecBlk; c++)
+                reinterpret_cast<uint4 *>(stage + kBlkStride * lane)[c] = reinterpret_cast<const uint4 *>(blk)[c];
+            __syncwarp();
+            const int it0 = it - lane;
+            const int g0 = it0 / kGroupItems;
+            const int64_t gblk = ((int64_t)blockIdx.x * (L::kElems / kGroup) + g0) * kBlkPerGroup +
+                                 (it0 - kGroupItems * g0);
+            uint4 *dst = reinterpret_cast<uint4 *>(vals + kBlkStride * gblk);
+            const uint4 *src = reinterpret_cast<const uint4 *>(stage);
+            constexpr int kVec = 32 * kVecBlk;
+#pragma unroll
+            for (int c = lane; c < kVec; c += 32) dst[c] = src[c];
+            __syncwarp();
         }
     }
 }
@@ -494,48 +545,12 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
 }
 
 // ---------------------------------------------------------------------------- block insertion
-// vals[(a,i),(b,k)] += Ke[e][3a+i][3b+k] for the elements of one colour: thread = (element, local
-// row 3a+i), the row's eight 3-wide blocks go to the slots of nodes b in node a's column list.
-constexpr int kInsElems = 8;  // elements per 192-thread block
-
-template <typename VT>
-__global__ void __launch_bounds__(24 * kInsElems) k_insert_blocks(const int32_t *__restrict__ elems, int64_t n,
-                                                                  const int32_t *__restrict__ conn,
-                                                                  const VT *__restrict__ Ke,
-                                                                  const int64_t *__restrict__ rowptr,
-                                                                  const uint8_t *__restrict__ slotmap,
-                                                                  VT *__restrict__ vals) {
-    const int64_t idx = (int64_t)blockIdx.x * kInsElems + threadIdx.x / 24;
-    if (idx >= n) return;
-    const int r = threadIdx.x % 24, a = r / 3, i = r - 3 * (r / 3);
-    const int64_t e = elems[idx];
-    const VT *row = Ke + (24 * e + r) * 24;
-    VT *dst = vals + rowptr[3 * (int64_t)conn[8 * e + a] + i];
-    const uint8_t *sl = slotmap + 64 * e + 8 * a;
-#pragma unroll
-    for (int b = 0; b < 8; b++) {
-        VT *d = dst + 3 * (int)sl[b];
-#pragma unroll
-        for (int k = 0; k < 3; k++) d[k] += row[3 * b + k];
-    }
-}
-
+// Caller blocks Ke[e][24][24] go through the row pass of the row-gather assembly: each CSR row
+// is the element-ordered sum of its blocks, written once (no clearing, no colouring).
 jetsci_status launch_insert_blocks(jetsci_mesh m, const void *Ke, void *vals, bool fp32, cudaStream_t s) {
-    JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * (fp32 ? sizeof(float) : sizeof(double)), s));
-    for (int c = 0; c < m->n_colours; c++) {
-        const int32_t *elems = m->d_colour_elems + m->colour_ptr[c];
-        const int64_t n = m->colour_ptr[c + 1] - m->colour_ptr[c];
-        if (n == 0) continue;
-        const unsigned grid = (unsigned)((n + kInsElems - 1) / kInsElems);
-        if (fp32)
-            k_insert_blocks<float><<<grid, 24 * kInsElems, 0, s>>>(elems, n, m->d_conn, (const float *)Ke, m->d_rowptr,
-                                                                  m->d_slot, (float *)vals);
-        else
-            k_insert_blocks<double><<<grid, 24 * kInsElems, 0, s>>>(elems, n, m->d_conn, (const double *)Ke,
-                                                                   m->d_rowptr, m->d_slot, (double *)vals);
-    }
-    JETSCI_CUDA_TRY(cudaGetLastError());
-    return JETSCI_OK;
+    if (reinterpret_cast<uintptr_t>(Ke) % 16 != 0) return fail(JETSCI_ERR_ARG, "Ke_dev must be 16-byte aligned");
+    if (fp32) return launch_gather_rows<float>(m, (const float *)Ke, true, nullptr, (float *)vals, nullptr, s);
+    return launch_gather_rows<double>(m, (const double *)Ke, true, nullptr, (double *)vals, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------- launchers
@@ -581,14 +596,21 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
     return JETSCI_OK;
 }
 
+template <typename T, typename VT, bool kBlocks>
+static jetsci_status tangent_setup(size_t smem) {
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    // The FP64 tangent needs 56 KB of shared memory per 8-element block: take the largest carveout.
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kBlocks>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared));
+    return JETSCI_OK;
+}
+
 template <typename T, typename VT>
 static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u, VT *vals, double *R,
                                      cudaStream_t s) {
     const size_t smem = sizeof(TangentSmem<T>);
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // The FP64 tangent needs 56 KB of shared memory per 8-element block: take the largest carveout.
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared));
+    if (jetsci_status st = tangent_setup<T, VT, false>(smem)) return st;
     // One launch per colour.  Splitting colours into L2-sized chunks (chunk-major order) was
     // measured slower at 128^3 for every precision: the 8x more, smaller launches lose more
     // in launch tails than the L2-resident read-modify-writes gain.
@@ -596,11 +618,34 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + TangentLayout<T>::kElems - 1) / TangentLayout<T>::kElems);
-        k_tangent<T, VT><<<grid, TangentLayout<T>::kThreads, smem, s>>>(A, u, m->d_rowptr, m->d_slot, m->d_first,
-                                                                       vals, R);
+        k_tangent<T, VT, false><<<grid, TangentLayout<T>::kThreads, smem, s>>>(A, u, m->d_rowptr, m->d_slot,
+                                                                              m->d_first, vals, R);
     });
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
+}
+
+// Row-gather assembly: the element pass writes every element's blocks and residual vectors to
+// the mesh's workspace in one launch, the row pass forms each CSR row and R entry once.
+template <typename T, typename VT>
+static jetsci_status tangent_rows(jetsci_mesh m, ElemArgs A, const double *u, VT *vals, double *R,
+                                  cudaStream_t s) {
+    void *ws = nullptr;
+    double *Re = nullptr;
+    if (jetsci_status st = ensure_block_workspace(m, blk_values_bytes(m->n_elem, sizeof(VT)), s, &ws, &Re)) return st;
+    VT *blocks = reinterpret_cast<VT *>(ws);
+    if (!R) Re = nullptr;
+    if (m->n_elem > 0) {
+        using L = TangentLayout<T>;
+        const size_t smem = tangent_stage_offset<T>() + (size_t)(L::kThreads / 32) * 32 * kBlkStride * sizeof(VT);
+        if (jetsci_status st = tangent_setup<T, VT, true>(smem)) return st;
+        A.elems = nullptr;
+        A.n = m->n_elem;
+        const unsigned grid = (unsigned)((A.n + L::kElems - 1) / L::kElems);
+        k_tangent<T, VT, true><<<grid, L::kThreads, smem, s>>>(A, u, nullptr, nullptr, nullptr, blocks, Re);
+        JETSCI_CUDA_TRY(cudaGetLastError());
+    }
+    return launch_gather_rows<VT>(m, blocks, false, Re, vals, R, s);
 }
 
 jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double *R, int precision,
@@ -611,11 +656,7 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
         return tangent_colours<double, double>(m, A, u, (double *)vals, R, s);
     }
-    if (precision == JETSCI_FP32) {
-        JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(float), s));
-        if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
-        return tangent_colours<float, float>(m, A, u, (float *)vals, R, s);
-    }
+    if (precision == JETSCI_FP32) return tangent_rows<float, float>(m, A, u, (float *)vals, R, s);
     if (precision == JETSCI_DF64) {
         JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(double), s));
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));

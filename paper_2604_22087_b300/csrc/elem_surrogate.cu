@@ -14,6 +14,7 @@
 // with the Voigt tangent; it is not symmetric for the surrogate, so all 64 node pairs are formed.
 #include <cuda_runtime.h>
 
+#include "blocks.cuh"
 #include "element.cuh"
 #include "jetsci_internal.h"
 #include "surrogate.cuh"
@@ -52,8 +53,6 @@ template <bool TANGENT>
 __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const double *__restrict__ u,
                                                            const unsigned char *__restrict__ img,
                                                            const float *__restrict__ params, SurrogateConfig cfg,
-                                                           const int64_t *__restrict__ rowptr,
-                                                           const uint8_t *__restrict__ slotmap,
                                                            float *__restrict__ vals, double *__restrict__ R) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpTileSmem &sm = *reinterpret_cast<MlpTileSmem *>(smem_raw);
@@ -69,7 +68,7 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
     mlp_load_weights(sm, img, params);
     const int64_t slot = (int64_t)blockIdx.x * 16 + es;
     const bool active = slot < A.n;
-    const int64_t e = A.elems[active ? slot : A.n - 1];
+    const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
     // ---------------- phase 1
     int32_t node;
     GaussKinematics<float> K;
@@ -170,9 +169,14 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
                                   (isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]) ? 0u : JETSCI_FLAG_NONFINITE) |
                                   (ok ? 0u : JETSCI_FLAG_NONFINITE);
             if (bits) atomicOr(A.flags, bits);
-            if (R)
+            if (R) {
+                if (TANGENT)  // the workspace's residual part [element][local node][3]
 #pragma unroll
-                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
+                    for (int i = 0; i < 3; i++) R[3 * (8 * e + hex_node_of_lane(l)) + i] = to_double(f[i]);
+                else
+#pragma unroll
+                    for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
+            }
         }
     }
     if (!TANGENT) {
@@ -275,17 +279,17 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
                     Kab[b][i][k] += M[i][k][0] * g0 + M[i][k][1] * g1 + M[i][k][2] * g2 + (i == k ? geo : 0.0f);
         }
     }
-    const int32_t na = s_node[es][a];
-    const uint8_t *sl = slotmap + 64 * (int64_t)eid + 8 * a;
+    // rows 3a .. 3a+2 of K_e: 72 contiguous values of the workspace [element][24][24]
+    float4 *dst = reinterpret_cast<float4 *>(vals + 576 * (int64_t)eid + 72 * a);
 #pragma unroll
-    for (int i = 0; i < 3; i++) {
-        float *row = vals + rowptr[3 * (int64_t)na + i];
+    for (int c = 0; c < 18; c++) {
+        float x[4];
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
-            float *dst = row + 3 * (int)sl[b];
-#pragma unroll
-            for (int k = 0; k < 3; k++) dst[k] += Kab[b][i][k];
+        for (int h = 0; h < 4; h++) {
+            const int v = 4 * c + h, i = v / 24, b = (v % 24) / 3, k = v % 3;
+            x[h] = Kab[b][i][k];
         }
+        dst[c] = make_float4(x[0], x[1], x[2], x[3]);
     }
 }
 
@@ -303,25 +307,35 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
     A.flags = m->d_flags;
     A.fallback_count = m->d_fallback;
     const size_t smem = sizeof(MlpTileSmem);
-    if (vals) {
-        JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_elem_surrogate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(float), s));
-    } else {
-        JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_elem_surrogate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
-    if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     JETSCI_CUDA_TRY(cudaMemsetAsync(m->d_fallback, 0, sizeof(uint32_t), s));
     const SurrogateConfig cfg = surrogate_config(sg);
+    if (vals) {
+        // row-gather assembly: element rows (one launch, elements in order), then the row pass
+        void *ws = nullptr;
+        double *Re = nullptr;
+        if (jetsci_status st = ensure_block_workspace(m, blk_full_bytes(m->n_elem, sizeof(float)), s, &ws, &Re))
+            return st;
+        if (!R) Re = nullptr;
+        if (m->n_elem > 0) {
+            JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_elem_surrogate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+            A.elems = nullptr;
+            A.n = m->n_elem;
+            const unsigned grid = (unsigned)((A.n + 15) / 16);
+            k_elem_surrogate<true><<<grid, 128, smem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
+                                                           (float *)ws, Re);
+            JETSCI_CUDA_TRY(cudaGetLastError());
+        }
+        return launch_gather_rows<float>(m, (const float *)ws, true, Re, vals, R, s);
+    }
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_elem_surrogate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + 15) / 16);
-        if (vals)
-            k_elem_surrogate<true><<<grid, 128, smem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
-                                                           m->d_rowptr, m->d_slot, vals, R);
-        else
-            k_elem_surrogate<false><<<grid, 128, smem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
-                                                            m->d_rowptr, m->d_slot, nullptr, R);
+        k_elem_surrogate<false><<<grid, 128, smem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
+                                                        nullptr, R);
     });
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;

@@ -15,6 +15,7 @@
 // 128 TMEM columns four CTAs share an SM; 16 elements per CTA (one CTA per SM) was 1.65x slower.
 #include <cuda_runtime.h>
 
+#include "blocks.cuh"
 #include "element.cuh"
 #include "jetsci_internal.h"
 #include "tc.cuh"
@@ -70,10 +71,12 @@ struct Tf32Args {
     uint32_t *flags;
 };
 
-// MODE 0: CSR values (+ optional R); MODE 1: y += K_e v_e (matrix-free).
+// MODE 0: element pass of the row-gather assembly -- the element's 24 x 24 stiffness rows go to
+// vals = the workspace [element][24][24] (elements in order, one launch) and, if R is given, its
+// nodal forces to R = the workspace's residual part [element][local node][3];
+// MODE 1: y += K_e v_e (matrix-free, one launch per colour).
 template <int MODE>
 __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restrict__ u, const double *__restrict__ v,
-                                              const int64_t *__restrict__ rowptr, const uint8_t *__restrict__ slotmap,
                                               float *__restrict__ vals, double *__restrict__ R, double *__restrict__ y) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Tf32Smem &sm = *reinterpret_cast<Tf32Smem *>(smem_raw);
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     {
         const int64_t slot = (int64_t)blockIdx.x * kTfElems + es;
         const bool active = slot < A.n;
-        const int64_t e = A.elems[active ? slot : A.n - 1];
+        const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
         int32_t node;
         GaussKinematics<float> K;
         float cu[3];
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
             nodal_force(c.P, K, l, f);
             if (active)
 #pragma unroll
-                for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
+                for (int i = 0; i < 3; i++) R[3 * (8 * e + hex_node_of_lane(l)) + i] = to_double(f[i]);
         }
         if (active && w == 0) {
             uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
@@ -273,14 +276,11 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         }
         const int32_t na = sm.node[ee][a];
         if (MODE == 0) {
-            float *rowp = vals + rowptr[3 * (int64_t)na + i];
-            const uint8_t *sl = slotmap + 64 * (int64_t)eid + 8 * a;
+            // row 3a + i of K_e: 96 contiguous bytes; a warp writes 32 consecutive rows
+            float4 *dst = reinterpret_cast<float4 *>(vals + 576 * (int64_t)eid + 24 * (3 * a + i));
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                float *dst = rowp + 3 * (int)sl[b];
-#pragma unroll
-                for (int k = 0; k < 3; k++) dst[k] += rowv[3 * b + k];
-            }
+            for (int c = 0; c < 6; c++)
+                dst[c] = make_float4(rowv[4 * c], rowv[4 * c + 1], rowv[4 * c + 2], rowv[4 * c + 3]);
         } else {
             float s = 0.0f;
 #pragma unroll
@@ -306,21 +306,29 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
     A.flags = m->d_flags;
     const size_t smem = sizeof(Tf32Smem);
     if (vals) {
-        JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(float), s));
-        if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
-    } else {
-        JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
+        // row-gather assembly: element rows (one launch, elements in order), then the row pass
+        void *ws = nullptr;
+        double *Re = nullptr;
+        if (jetsci_status st = ensure_block_workspace(m, blk_full_bytes(m->n_elem, sizeof(float)), s, &ws, &Re))
+            return st;
+        if (!R) Re = nullptr;
+        if (m->n_elem > 0) {
+            JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            A.elems = nullptr;
+            A.n = m->n_elem;
+            const unsigned grid = (unsigned)((A.n + kTfElems - 1) / kTfElems);
+            k_tf32<0><<<grid, 128, smem, s>>>(A, u, nullptr, (float *)ws, Re, nullptr);
+            JETSCI_CUDA_TRY(cudaGetLastError());
+        }
+        return launch_gather_rows<float>(m, (const float *)ws, true, Re, vals, R, s);
     }
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + kTfElems - 1) / kTfElems);
-        if (vals)
-            k_tf32<0><<<grid, 128, smem, s>>>(A, u, nullptr, m->d_rowptr, m->d_slot, vals, R, nullptr);
-        else
-            k_tf32<1><<<grid, 128, smem, s>>>(A, u, v, m->d_rowptr, m->d_slot, nullptr, nullptr, y);
+        k_tf32<1><<<grid, 128, smem, s>>>(A, u, v, nullptr, nullptr, y);
     });
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;

@@ -45,6 +45,11 @@ struct jetsci_mesh_s {
     uint8_t *d_first = nullptr;         // [n_elem*8]: bit b of byte a set = the element writes CSR block
                                         // (node a, node b) first (lowest colour among its elements)
     int32_t *d_colour_elems = nullptr;  // [n_elem], grouped by colour, ascending within a colour
+    int64_t *d_ne_ptr = nullptr;        // [n_nodes+1]: offsets into d_ne
+    uint32_t *d_ne = nullptr;           // [n_elem*8]: per node, 8e + a for each element e holding it
+                                        // as local node a, ascending
+    void *d_blocks = nullptr;           // element-block workspace of the row-gather assembly
+    size_t blocks_bytes = 0;            // (allocated on first use, kept until the mesh is destroyed)
     jetsci::Material *d_mats = nullptr; // [kMaxPhases]
     double *d_norm_partials = nullptr;  // [kNormMaxPartials]
     uint32_t *d_flags = nullptr;        // [1]
@@ -96,6 +101,15 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
                           const double *E_elem, cudaStream_t s);
 jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, double *R, cudaStream_t s);
 jetsci_status launch_insert_blocks(jetsci_mesh m, const void *Ke, void *vals, bool fp32, cudaStream_t s);
+// The mesh's element-block workspace (blocks.cuh): values_bytes of blocks, then the residual
+// part.  Allocated on first use (synchronising the stream) or grown; fails if the stream is
+// being captured and the workspace is too small.  Sets *blocks and *Re.
+jetsci_status ensure_block_workspace(jetsci_mesh m, size_t values_bytes, cudaStream_t s, void **blocks, double **Re);
+// Row pass of the row-gather assembly: vals (all nnz entries) and, if R != NULL, R (all n_dof
+// entries) are overwritten from element blocks, compact (blocks.cuh) or [n_elem][24][24] (full).
+template <typename VT>
+jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, bool full, const double *Re, VT *vals,
+                                 double *R, cudaStream_t s);
 jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
                                    const double *R, double *g, int precision, cudaStream_t s);
 

@@ -128,6 +128,9 @@ static void free_mesh(jetsci_mesh m) {
     cudaFree(m->d_slot);
     cudaFree(m->d_first);
     cudaFree(m->d_colour_elems);
+    cudaFree(m->d_ne_ptr);
+    cudaFree(m->d_ne);
+    cudaFree(m->d_blocks);
     cudaFree(m->d_mats);
     cudaFree(m->d_norm_partials);
     cudaFree(m->d_flags);
@@ -187,14 +190,16 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     m->n_dof = 3 * n_nodes;
     m->n_mats = n_mats;
 
-    // ---------------- node -> element adjacency (counting sort)
+    // ---------------- node -> element adjacency (counting sort): entries 8e + a (element e,
+    // local node a), ascending per node; kept on the device for the row-gather assembly
+    if (8 * n_elem >= (int64_t)UINT32_MAX) return fail(JETSCI_ERR_ARG, "too many elements");
     std::vector<int64_t> ne_ptr(n_nodes + 1, 0);
     for (int64_t t = 0; t < 8 * n_elem; t++) ne_ptr[conn[t] + 1]++;
     for (int64_t n = 0; n < n_nodes; n++) ne_ptr[n + 1] += ne_ptr[n];
-    std::vector<int64_t> ne_idx(8 * n_elem);
+    std::vector<uint32_t> ne_idx(std::max<int64_t>(8 * n_elem, 1));
     {
         std::vector<int64_t> fill(ne_ptr.begin(), ne_ptr.end() - 1);
-        for (int64_t t = 0; t < 8 * n_elem; t++) ne_idx[fill[conn[t]]++] = t / 8;
+        for (int64_t t = 0; t < 8 * n_elem; t++) ne_idx[fill[conn[t]]++] = (uint32_t)t;
     }
 
     // ---------------- node neighbour lists (sorted, unique, including the node itself)
@@ -205,7 +210,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
         std::vector<int32_t> cand;
         cand.reserve(8 * (ne_ptr[n + 1] - ne_ptr[n]));
         for (int64_t t = ne_ptr[n]; t < ne_ptr[n + 1]; t++)
-            for (int b = 0; b < 8; b++) cand.push_back(conn[8 * ne_idx[t] + b]);
+            for (int b = 0; b < 8; b++) cand.push_back(conn[8 * (int64_t)(ne_idx[t] >> 3) + b]);
         std::sort(cand.begin(), cand.end());
         int64_t cnt = std::unique(cand.begin(), cand.end()) - cand.begin();
         if (cnt > 255) too_many = true;
@@ -220,7 +225,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
         std::vector<int32_t> cand;
         cand.reserve(8 * (ne_ptr[n + 1] - ne_ptr[n]));
         for (int64_t t = ne_ptr[n]; t < ne_ptr[n + 1]; t++)
-            for (int b = 0; b < 8; b++) cand.push_back(conn[8 * ne_idx[t] + b]);
+            for (int b = 0; b < 8; b++) cand.push_back(conn[8 * (int64_t)(ne_idx[t] >> 3) + b]);
         std::sort(cand.begin(), cand.end());
         auto end = std::unique(cand.begin(), cand.end());
         std::copy(cand.begin(), end, nbr.begin() + nbr_ptr[n]);
@@ -266,6 +271,8 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     if ((st = dev_alloc(&m->d_slot, 64 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_first, 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_colour_elems, n_elem))) return st;
+    if ((st = dev_alloc(&m->d_ne_ptr, n_nodes + 1))) return st;
+    if ((st = dev_alloc(&m->d_ne, 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_mats, kMaxPhases))) return st;
     if ((st = dev_alloc(&m->d_norm_partials, kNormMaxPartials))) return st;
     if ((st = dev_alloc(&m->d_flags, 1))) return st;
@@ -297,6 +304,8 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     }
     UP(m->d_rowptr, rowptr.data(), (m->n_dof + 1) * sizeof(int64_t));
     UP(m->d_colour_elems, colour_elems.data(), n_elem * sizeof(int32_t));
+    UP(m->d_ne_ptr, ne_ptr.data(), (n_nodes + 1) * sizeof(int64_t));
+    UP(m->d_ne, ne_idx.data(), 8 * n_elem * sizeof(uint32_t));
     UP(m->d_mats, m->mats, sizeof(m->mats));
     UP(d_nbr_ptr, nbr_ptr.data(), (n_nodes + 1) * sizeof(int64_t));
     UP(d_nbr, nbr.data(), nbr_ptr[n_nodes] * sizeof(int32_t));

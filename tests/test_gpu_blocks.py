@@ -134,6 +134,12 @@ def test_argument_errors():
     assert ei.value.status == 1
     with pytest.raises(ValueError):
         mesh.assemble_blocks(torch.zeros(mesh.n_elem, 24, 23, dtype=torch.float64, device="cuda"))
+    # blocks are read in 16-byte pieces: a pointer off that boundary is refused before any launch
+    flat = torch.zeros(mesh.n_elem * 576 + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(J.JetsciError) as ei:
+        J._check(J.lib.jetsci_assemble_element_blocks(mesh.handle, J._ptr(flat[1:]), J._ptr(vals), J.FP64,
+                                                      J._stream()))
+    assert ei.value.status == 1
     empty = J.Mesh(np.zeros((4, 3)), np.zeros((0, 8), np.int32), None, [(1e9, 0.3, 0)])
     out = empty.assemble_blocks(torch.zeros(0, 24, 24, dtype=torch.float64, device="cuda"))
     assert out.numel() == 0

@@ -161,9 +161,10 @@ def test_material_gradient_fp64():
 
 @pytest.mark.parametrize("name", ["FP64", "FP32", "DF64"])
 def test_tangent_overwrites_every_value(case, name):
-    """The tangent does not clear the value array: each CSR block's first writer (its
-    lowest-colour element) stores, later colours add.  Whatever vals held before must not leak
-    into the result, and every block must be written."""
+    """The tangent does not clear the value array: in the coloured scatter (FP64) each CSR
+    block's first writer (its lowest-colour element) stores and later colours add; in the
+    row-gather assembly (FP32) each row is written once.  Whatever vals held before must not
+    leak into the result, and every block must be written."""
     prob, mesh, _, _ = case
     J = jetsci()
     p = getattr(J, name)
@@ -208,6 +209,65 @@ def test_shuffled_numbering_general_colouring():
     y_ref = oracle.apply_tangent(om, prob.u, prob.v)
     assert relerr(mesh.apply_tangent(u, v).cpu().numpy(), y_ref) <= FP64_TOL
     assert relerr(mesh.apply_tangent(None, v, mode=J.CSR, vals=vals).cpu().numpy(), y_ref) <= FP64_TOL
+    # FP32 row-gather assembly on the same general numbering (NaN-filled outputs)
+    R32 = torch.full_like(R, float("nan"))
+    vals32 = mesh.new_values(J.FP32)
+    vals32.fill_(float("nan"))
+    mesh.tangent_csr(u, vals=vals32, R=R32, precision=J.FP32)
+    assert relerr(vals32.cpu().numpy(), vals_ref) <= 5e-5
+    assert relerr(R32.cpu().numpy(), R_ref) <= 2e-4
+    assert mesh.check() == 0
+    mesh.close()
+
+
+def high_valence_problem():
+    """Twelve hexahedra sharing node 0 (as local node k mod 8 of element k), each with seven
+    nodes of its own, plus one node in no element: node 0 has 12 elements and 85 neighbours
+    (more than the 8 elements and 32 neighbours one step of the row pass takes), the isolated
+    node has empty rows and a zero residual."""
+    g = np.random.default_rng(21)
+    corner = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], float)
+    coords = [np.zeros(3)]
+    conn = []
+    for k in range(12):
+        la, h = k % 8, 0.3 + 0.05 * k
+        ids = []
+        for b in range(8):
+            if b == la:
+                ids.append(0)
+            else:
+                coords.append(h * (corner[b] - corner[la]) + g.uniform(-0.03, 0.03, 3))
+                ids.append(len(coords) - 1)
+        conn.append(ids)
+    coords.append(np.array([2.0, 2.0, 2.0]))
+    coords = np.array(coords)
+    conn = np.array(conn, dtype=np.int32)
+    phase = (np.arange(12) % 2).astype(np.int32)
+    return I.Problem("high_valence", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                     g.uniform(-3e-3, 3e-3, coords.size), g.uniform(-1, 1, coords.size))
+
+
+@pytest.mark.parametrize("name", ["FP64", "FP32"])
+def test_high_valence_node_and_isolated_node(name):
+    J = jetsci()
+    prob = high_valence_problem()
+    mesh = J.Mesh.of(prob)
+    rp, col = mesh.pattern()
+    rp = rp.cpu().numpy()
+    assert (rp[1] - rp[0]) // 3 == 85 and rp[-1] == rp[-4]  # node 0: 85 neighbours; last node: none
+    om = oracle.Mesh.of(prob)
+    orp, ocol = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    vals_ref, R_ref = oracle.tangent_csr(om, prob.u, orp, ocol)
+    p = getattr(J, name)
+    u = cuda(prob.u)
+    R = torch.full((mesh.n_dof,), float("nan"), dtype=torch.float64, device="cuda")
+    vals = mesh.new_values(p)
+    vals.fill_(float("nan"))
+    mesh.tangent_csr(u, vals=vals, R=R, precision=p)
+    tol_v, tol_r = (FP64_TOL, FP64_TOL) if name == "FP64" else (5e-5, 2e-4)
+    assert relerr(vals.cpu().numpy(), vals_ref) <= tol_v
+    assert relerr(R.cpu().numpy(), R_ref) <= tol_r
+    assert torch.count_nonzero(R[-3:]).item() == 0
     assert mesh.check() == 0
     mesh.close()
 
@@ -223,6 +283,10 @@ def test_empty_mesh():
     assert torch.count_nonzero(R).item() == 0
     y = mesh.apply_tangent(u, u.clone())
     assert torch.count_nonzero(y).item() == 0
+    for p in (J.FP64, J.FP32):
+        R.fill_(7.0)
+        vals = mesh.tangent_csr(u, R=R, precision=p)
+        assert vals.numel() == 0 and torch.count_nonzero(R).item() == 0
     assert mesh.norm2(u).item() == pytest.approx(np.sqrt(12.0), rel=1e-15)
 
 
