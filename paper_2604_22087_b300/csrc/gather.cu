@@ -15,158 +15,161 @@ namespace jetsci {
 
 namespace {
 
-constexpr int kChunk = 8;  // elements staged per step
+constexpr int kGroupLanes = 8;  // lanes per node (lane = column node lb of the element)
+constexpr int kNodesPerWarp = 32 / kGroupLanes;
+constexpr int kRowWarps = 4;    // warps per block
+constexpr int kSlots = 32;      // neighbour slots per accumulation pass (more take further passes)
+constexpr int kAccStride = 12;  // accumulator values per slot (3 x 3 block, 16-byte aligned)
 
-// nodes (warps) per block of the row pass: shared memory stays under 48 KB
+// elements whose blocks a lane loads at once (in flight together); measured at 128^3: 2 is
+// faster than 4 and 8, whose registers cost more occupancy than the deeper prefetch gains
 template <typename VT>
-constexpr int row_warps() { return sizeof(VT) == 4 ? 8 : 4; }
+constexpr int row_chunk() { return 2; }
 
-template <typename VT>
-struct RowSmem {
-    // per warp: the staged blocks of a chunk -- compact layout: [element j][lb][kBlkStride],
-    // block (min(la,lb), max(la,lb)) as stored; caller layout: [element j][72], node la's three
-    // rows as stored -- reused to stage the output rows (3 x 96 values)
-    VT blk[row_warps<VT>()][kChunk * 8 * kBlkStride];
-    uint2 slots[row_warps<VT>()][kChunk];  // slot bytes of node a's row in each element
-    double re[row_warps<VT>()][kChunk][3]; // residual vectors R_e(a)
-};
-
-// Asynchronous global -> shared copy of N (8 or 16) bytes; completed by cp.async.wait_group.
-template <int N>
-__device__ __forceinline__ void cp_async(void *dst_smem, const void *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-    if constexpr (N == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(N) : "memory");
+// Block K_e(la, lb) (rows at node la) into y[3 i + k]: compact symmetric layout (blocks.cuh),
+// the pair (lb, la) of lb < la read transposed; or caller blocks [e][24][24].
+template <typename VT, bool kFull>
+__device__ __forceinline__ void load_block(const VT *__restrict__ blocks, int64_t e, int la, int lb, VT y[9]) {
+    if constexpr (kFull) {
+        const VT *p = blocks + 576 * e + 72 * la + 3 * lb;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) y[3 * i + k] = __ldg(p + 24 * i + k);
+    } else {
+        const bool tr = la > lb;
+        const VT *p = blocks + kBlkStride * blk_index(e, tr ? lb : la, tr ? la : lb);
+        VT x[kBlkStride];
+#pragma unroll
+        for (int c = 0; c < kBlkStride * (int)sizeof(VT) / 16; c++)
+            reinterpret_cast<uint4 *>(x)[c] = __ldg(reinterpret_cast<const uint4 *>(p) + c);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) y[3 * i + k] = tr ? x[3 * k + i] : x[3 * i + k];
+    }
 }
 
-// One warp per node a.  For each element around the node (eight at a time, ascending), the
-// warp copies the eight blocks K_e(a, b) of node a's rows into shared memory with 16-byte
-// asynchronous copies (compact layout: lane = (element, lb), whole blocks; caller layout: the 72
-// contiguous values of node a's rows); lane s then sums, over the staged elements in order, the
-// block whose column node has rank s in node a's neighbour list (the slot map), for s = lane,
-// lane + 32, ...  Blocks stored as (lb, la) with lb < la are read transposed.
+// Brings element e's blocks into L2 in whole lines (the blocks of the node rows that follow
+// then hit L2 instead of fetching 48-byte pieces from DRAM one node at a time).
 template <typename VT, bool kFull>
-__global__ void __launch_bounds__(32 * row_warps<VT>()) k_gather_rows(int64_t n_nodes, const int64_t *__restrict__ ne_ptr,
-                                                                      const uint32_t *__restrict__ ne,
-                                                                      const uint8_t *__restrict__ slot,
-                                                                      const int64_t *__restrict__ rowptr,
-                                                                      const VT *__restrict__ blocks,
-                                                                      const double *__restrict__ Re,
-                                                                      VT *__restrict__ vals, double *__restrict__ R) {
-    constexpr int kV16 = 16 / (int)sizeof(VT);  // values per 16-byte copy
-    __shared__ __align__(16) RowSmem<VT> sm;
+__device__ __forceinline__ void prefetch_element(const VT *__restrict__ blocks, int64_t e) {
+    if constexpr (kFull) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blocks + 576 * e), "r"(576u * (unsigned)sizeof(VT))
+                     : "memory");
+    } else {
+        const VT *off = blocks + kBlkStride * blk_index(e, 0, 1);  // its 28 pairs a < b, contiguous
+        const VT *dia = blocks + kBlkStride * blk_index(e, 0, 0);  // its 8 pairs a == a, contiguous
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(off), "r"(28u * kBlkStride * (unsigned)sizeof(VT))
+                     : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(dia), "r"(8u * kBlkStride * (unsigned)sizeof(VT))
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Eight lanes per node a, four nodes per warp.  The node's rows are accumulated in shared
+// memory, one 3 x 3 block per neighbour slot; at each element step (elements in ascending
+// order) lane lb adds the element's block K_e(a, b) of its column node b at b's slot (the slot
+// map).  The eight blocks of one element go to eight distinct slots, so the lanes never
+// collide, and every contribution to an entry arrives in element order.  A lane loads the
+// blocks of several elements before adding any (they are in flight together).  Nodes with more
+// than 32 neighbours take one pass per 32 slots.
+template <typename VT, bool kFull>
+__global__ void __launch_bounds__(32 * kRowWarps) k_gather_rows(int64_t n_nodes, const int64_t *__restrict__ ne_ptr,
+                                                                const uint32_t *__restrict__ ne,
+                                                                const uint8_t *__restrict__ slot,
+                                                                const int64_t *__restrict__ rowptr,
+                                                                const VT *__restrict__ blocks,
+                                                                const double *__restrict__ Re,
+                                                                VT *__restrict__ vals, double *__restrict__ R) {
+    constexpr int kChunk = row_chunk<VT>();
+    constexpr int kV16 = 16 / (int)sizeof(VT);
+    __shared__ __align__(16) VT acc_s[kRowWarps * kNodesPerWarp][kSlots * kAccStride];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t a = (int64_t)blockIdx.x * row_warps<VT>() + w;
-    if (a >= n_nodes) return;  // warp-uniform
-    const int64_t j0 = ne_ptr[a], cnt = ne_ptr[a + 1] - j0;
-    const int64_t base = rowptr[3 * a];
-    const int nnb = (int)((rowptr[3 * a + 1] - base) / 3);
-    const int n_sc = (nnb + 31) / 32;
-    VT *const blk = sm.blk[w];
+    const int grp = lane / kGroupLanes, lb = lane % kGroupLanes, gl0 = kGroupLanes * grp;
+    const int64_t a = ((int64_t)blockIdx.x * kRowWarps + w) * kNodesPerWarp + grp;
+    const bool valid = a < n_nodes;
+    int64_t j0 = 0, base = 0;
+    int cnt = 0, nnb = 0;
+    if (valid) {
+        j0 = ne_ptr[a];
+        cnt = (int)(ne_ptr[a + 1] - j0);
+        base = rowptr[3 * a];
+        nnb = (int)((rowptr[3 * a + 1] - base) / 3);
+    }
+    const int n_sc = (nnb + kSlots - 1) / kSlots;
+    const int n_sc_max = warp_max(n_sc), cnt_max = warp_max(cnt);
+    VT *acc = acc_s[w * kNodesPerWarp + grp];
     double racc = 0.0;
-    for (int sc = 0; sc < (n_sc > 0 ? n_sc : 1); sc++) {
-        const int s = 32 * sc + lane;
-        VT acc[9];
-#pragma unroll
-        for (int c = 0; c < 9; c++) acc[c] = VT(0);
-        for (int64_t ec = 0; ec < cnt; ec += kChunk) {
-            const int nc = (int)(cnt - ec < kChunk ? cnt - ec : kChunk);
-            const uint32_t tl = lane < nc ? ne[j0 + ec + lane] : 0u;
-            uint32_t la_pack = 0;  // 3 bits per element of the chunk
-#pragma unroll
-            for (int j = 0; j < kChunk; j++) la_pack |= (__shfl_sync(0xffffffffu, tl, j) & 7u) << (3 * j);
-            if (n_sc > 0) {
-                if constexpr (kFull) {
-                    constexpr int kPer = 72 / kV16;  // 16-byte pieces of one element's rows
-                    for (int q0 = 0; q0 < nc * kPer; q0 += 32) {  // warp-uniform trip count
-                        const int q = q0 + lane;
-                        const int j = q / kPer < kChunk ? q / kPer : kChunk - 1, part = q - kPer * j;
-                        const uint32_t t = __shfl_sync(0xffffffffu, tl, j);
-                        if (q < nc * kPer)
-                            cp_async<16>(blk + 72 * j + kV16 * part,
-                                         blocks + 576 * (int64_t)(t >> 3) + 72 * (t & 7) + kV16 * part);
-                    }
-                } else {
-                    const int lb = lane & 7;
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const int j = (lane >> 3) + 4 * h;
-                        const uint32_t t = __shfl_sync(0xffffffffu, tl, j);
-                        if (j < nc) {
-                            const int64_t e = t >> 3;
-                            const int la = (int)(t & 7);
-                            const VT *src = blocks + kBlkStride * blk_index(e, la < lb ? la : lb, la < lb ? lb : la);
-                            VT *dst = blk + kBlkStride * (8 * j + lb);
-#pragma unroll
-                            for (int c = 0; c < kBlkStride / kV16; c++) cp_async<16>(dst + kV16 * c, src + kV16 * c);
-                        }
-                    }
-                }
-                if (lane < nc) cp_async<8>(&sm.slots[w][lane], slot + 64 * (int64_t)(tl >> 3) + 8 * (tl & 7));
-            }
-            if (R && sc == 0) {  // lane 3 j + c copies R_e(a)_c of element j
-                const uint32_t t = __shfl_sync(0xffffffffu, tl, lane / 3 < kChunk ? lane / 3 : kChunk - 1);
-                if (lane < 3 * nc) cp_async<8>(&sm.re[w][0][0] + lane, Re + 3 * (int64_t)t + lane % 3);
-            }
-            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-            __syncwarp();
-            if (s < nnb) {
-                const uint32_t rep = 0x01010101u * (uint32_t)s;
-                for (int j = 0; j < nc; j++) {
-                    const uint2 sw = sm.slots[w][j];
-                    const uint32_t mlo = __vcmpeq4(sw.x, rep), mhi = __vcmpeq4(sw.y, rep);
-                    if (mlo | mhi) {
-                        const int lb = mlo ? (__ffs(mlo) - 1) >> 3 : 4 + ((__ffs(mhi) - 1) >> 3);
-                        if constexpr (kFull) {
-                            const VT *x = blk + 72 * j + 3 * lb;
-#pragma unroll
-                            for (int i = 0; i < 3; i++)
-#pragma unroll
-                                for (int k = 0; k < 3; k++) acc[3 * i + k] += x[24 * i + k];
-                        } else {
-                            VT y[kBlkStride];
-#pragma unroll
-                            for (int c = 0; c < kBlkStride / kV16; c++)
-                                reinterpret_cast<uint4 *>(y)[c] =
-                                    reinterpret_cast<const uint4 *>(blk + kBlkStride * (8 * j + lb))[c];
-                            const bool tr = (int)((la_pack >> (3 * j)) & 7u) > lb;
-#pragma unroll
-                            for (int i = 0; i < 3; i++)
-#pragma unroll
-                                for (int k = 0; k < 3; k++) acc[3 * i + k] += tr ? y[3 * k + i] : y[3 * i + k];
-                        }
-                    }
-                }
-            }
-            if (R && sc == 0) {
-                // lane 3 j + c holds R_e(a)_c of element j; a fixed tree over j (8 -> 4 -> 2 -> 1)
-                double r = lane < 3 * nc ? (&sm.re[w][0][0])[lane] : 0.0;
-                r += __shfl_down_sync(0xffffffffu, r, 12);
-                r += __shfl_down_sync(0xffffffffu, r, 6);
-                r += __shfl_down_sync(0xffffffffu, r, 3);
-                racc += r;
-            }
-            __syncwarp();
-        }
-        if (n_sc == 0) break;
-        // rows 3a, 3a+1, 3a+2 are contiguous (3 nnb values each): stage, then write coalesced
-        const int ns = nnb - 32 * sc < 32 ? nnb - 32 * sc : 32;
-        if (lane < ns)
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int k = 0; k < 3; k++) blk[96 * i + 3 * lane + k] = acc[3 * i + k];
+    for (int sc = 0; sc < (n_sc_max > 0 ? n_sc_max : 1); sc++) {
+        if (sc < n_sc)
+            for (int c = lb; c < kSlots * kAccStride / kV16; c += kGroupLanes)
+                reinterpret_cast<uint4 *>(acc)[c] = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
+        for (int ec = 0; ec < cnt_max; ec += kChunk) {
+            const int nc = cnt - ec < 0 ? 0 : (cnt - ec < kChunk ? cnt - ec : kChunk);
+            // lane lb (< kChunk) holds element ec + lb of its node: entry 8e + la and the slot
+            // bytes of la's row
+            uint32_t tm = 0;
+            uint2 sw = make_uint2(0u, 0u);
+            if (lb < nc) {
+                tm = ne[j0 + ec + lb];
+                sw = __ldg(reinterpret_cast<const uint2 *>(slot + 64 * (int64_t)(tm >> 3) + 8 * (tm & 7)));
+                // the element's first node (local node 0, the lowest id on ordered meshes) pulls
+                // the whole element into L2 (measured 4-5% faster at 128^3)
+                if ((tm & 7) == 0 && sc == 0) prefetch_element<VT, kFull>(blocks, tm >> 3);
+            }
+            VT y[kChunk][9];
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            VT *row = vals + base + (int64_t)i * 3 * nnb + 96 * sc;
-            for (int c = lane; c < 3 * ns; c += 32) row[c] = blk[96 * i + c];
+            for (int j = 0; j < kChunk; j++) {
+                const uint32_t t = __shfl_sync(0xffffffffu, tm, gl0 + j);
+                if (j < nc && sc < n_sc) load_block<VT, kFull>(blocks, t >> 3, (int)(t & 7), lb, y[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < kChunk; j++) {
+                const uint32_t t = __shfl_sync(0xffffffffu, tm, gl0 + j);
+                const uint32_t wx = __shfl_sync(0xffffffffu, sw.x, gl0 + j), wy = __shfl_sync(0xffffffffu, sw.y, gl0 + j);
+                if (j < nc) {
+                    const int sl = (int)(((lb < 4 ? wx : wy) >> (8 * (lb & 3))) & 0xffu);
+                    if (sc < n_sc && sl / kSlots == sc) {
+                        VT *d = acc + kAccStride * (sl % kSlots);
+                        VT z[kAccStride];
+#pragma unroll
+                        for (int c = 0; c < kAccStride / kV16; c++)
+                            reinterpret_cast<uint4 *>(z)[c] = reinterpret_cast<const uint4 *>(d)[c];
+#pragma unroll
+                        for (int c = 0; c < 9; c++) z[c] += y[j][c];
+#pragma unroll
+                        for (int c = 0; c < kAccStride / kV16; c++)
+                            reinterpret_cast<uint4 *>(d)[c] = reinterpret_cast<const uint4 *>(z)[c];
+                    }
+                    if (R && sc == 0 && lb < 3) racc += Re[3 * (int64_t)t + lb];
+                }
+                __syncwarp();
+            }
+        }
+        if (sc < n_sc) {
+            // rows 3a, 3a+1, 3a+2 (3 nnb values each, contiguous); value 3 s + k of row i is
+            // entry (i, k) of slot s's block
+            const int ns = nnb - kSlots * sc < kSlots ? nnb - kSlots * sc : kSlots;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                VT *row = vals + base + (int64_t)i * 3 * nnb + 3 * kSlots * sc;
+                for (int c = lb; c < 3 * ns; c += kGroupLanes) {
+                    const int s3 = c / 3;
+                    row[c] = acc[kAccStride * s3 + 3 * i + (c - 3 * s3)];
+                }
+            }
         }
         __syncwarp();
     }
-    if (R && lane < 3) R[3 * a + lane] = racc;
+    if (R && valid && lb < 3) R[3 * a + lb] = racc;
 }
 
 }  // namespace
@@ -196,17 +199,17 @@ template <typename VT>
 jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, bool full, const double *Re, VT *vals,
                                  double *R, cudaStream_t s) {
     if (m->n_nodes == 0) return JETSCI_OK;
-    constexpr int kW = row_warps<VT>();
-    const unsigned grid = (unsigned)((m->n_nodes + kW - 1) / kW);
+    constexpr int kNodes = kRowWarps * kNodesPerWarp;
+    const unsigned grid = (unsigned)((m->n_nodes + kNodes - 1) / kNodes);
     // several blocks per SM need more shared memory than the default carveout gives
     JETSCI_CUDA_TRY(cudaFuncSetAttribute(full ? k_gather_rows<VT, true> : k_gather_rows<VT, false>,
                                          cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared));
     if (full)
-        k_gather_rows<VT, true><<<grid, 32 * kW, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot,
+        k_gather_rows<VT, true><<<grid, 32 * kRowWarps, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot,
                                                                 m->d_rowptr, blocks, Re, vals, R);
     else
-        k_gather_rows<VT, false><<<grid, 32 * kW, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot,
+        k_gather_rows<VT, false><<<grid, 32 * kRowWarps, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot,
                                                                  m->d_rowptr, blocks, Re, vals, R);
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
