@@ -1,18 +1,23 @@
-// Element stiffness on the tensor cores in TF32 (FP32 accumulate in TMEM): CSR assembly and
-// the matrix-free product K.v.
+// Element stiffness on the tensor cores in TF32 (FP32 accumulate in TMEM): the element rows of
+// the row-gather tangent assembly, and the matrix-free product K.v.
 //
-// For one element, K_e = sum_q B_q^T (c_q W D_q) B_q + geometric term, where B_q (6 x 24) maps
-// nodal displacements to the Voigt tensor components of the Green-Lagrange strain increment,
-// D_q = dS/dE (6 x 6) and W = diag(1,1,1,2,2,2).  Stacking the 8 Gauss points gives one
-// contraction over K = 48 = (q, Voigt component): K_mat = Bt^T Zt with Bt, Zt of 48 x 24 and
-// Zt = blockdiag(c W D) Bt.  Four elements share one tcgen05.mma of M = 128 (96 rows used),
-// N = 96, K = 48 (6 instructions of K = 8); of its output only the four diagonal 24 x 24 blocks
-// are kept.  The geometric term delta_ik (G_a . c S G_b) is added in the epilogue.
+// The tangent in pair form, as the CUDA-core kernels use it:
+//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi ] + delta_ik sum_q tg_a . g_b
+// with g_a = F^-T G_a the spatial shape-function gradients at Gauss point q, c = w detJ,
+// m = mu - lam lnJ (mu for Hooke) and tg_a = c (tau + m I) g_a (tau the Kirchhoff stress).  Its
+// two rank-8 parts are contractions over the Gauss points: with P[(a,i), q] = g_ai,
+//   T1 = P diag(c lam) P^T,   T2 = P diag(c m) P^T,   K_ab,ik = T1[(a,i),(b,k)] + T2[(a,k),(b,i)] + ...
+// Four elements share one tcgen05.mma (kind::tf32, M = 128, N = 48, K = 32, as four MMAs of
+// K = 8): A holds P of the four elements block-diagonally (row (e,a,i), column (e,q), zero
+// outside the element's eight columns) and B the columns c lam g_b | c m g_b (row (term,b,k),
+// column (e,q)).  Accumulator row (e,a,i) so receives T1 and T2 of its own element only, in 48
+// TMEM columns.  The geometric term (36 dot products per element and point) is reduced over the
+// Gauss-point lanes on the CUDA cores.
 //
-// One CTA = one such group: each warp evaluates the 4 elements x 8 Gauss points and forms the
-// operand rows of two of the eight nodes, the MMA runs, and all four warps read one accumulator
-// row each.  At about 53 KB of shared memory and
-// 128 TMEM columns four CTAs share an SM; 16 elements per CTA (one CTA per SM) was 1.65x slower.
+// One CTA = four groups of four elements: warp w evaluates group w (lane = element x Gauss
+// point) and writes its operand columns; one thread issues the 16 MMAs; then every warp reads
+// its TMEM lane quarter of each group's accumulator.  T2 is transposed within node blocks
+// through shared memory.
 #include <cuda_runtime.h>
 
 #include "blocks.cuh"
@@ -22,35 +27,37 @@
 
 namespace jetsci {
 
-constexpr int kTfElems = 4;            // elements per CTA
-constexpr int kTfGroups = 1;           // MMA groups of 4 elements per CTA
-constexpr uint32_t kTfTmemCols = 128;  // 96 accumulator columns per group, allocated as a power of 2
-constexpr int kTfK = 48;               // 8 Gauss points x 6 Voigt components
-// Operand tiles use padded core-matrix strides: 144 B between core matrices along K (16 B of
-// padding) and 12 x 144 B between 8-row blocks.  With the fill pattern below (four elements x
-// eight Gauss points per warp, one 4-byte store per lane) this leaves at most 2-way shared-
-// memory bank conflicts instead of 16-way with the dense 128 B / 1536 B strides.
-constexpr uint32_t kTfLBO = 144;
-constexpr uint32_t kTfSBO = (kTfK / 4) * kTfLBO;
-constexpr int kTfATile = 16 * kTfSBO;  // 128 rows (rows 96..127 zero)
-constexpr int kTfBTile = 12 * kTfSBO;  // 96 rows
+constexpr int kTgGroups = 4;                   // MMA groups per CTA (one per warp)
+constexpr int kTgElems = 4 * kTgGroups;        // elements per CTA
+constexpr int kTgK = 32;                       // 4 elements x 8 Gauss points
+constexpr int kTgN = 48;                       // 2 terms x 8 nodes x 3 components
+constexpr uint32_t kTgCols = 64;               // TMEM columns per group (48 used)
+constexpr uint32_t kTgTmemCols = kTgGroups * kTgCols;
+// K-major core matrices (8 rows x 16 bytes) with 144 B between core matrices along K (16 B of
+// padding): a warp's 32 lanes (8 element columns x 4 per core matrix) write one row of a tile
+// on 32 distinct banks.
+constexpr uint32_t kTgLBO = 144;
+constexpr uint32_t kTgSBO = (kTgK / 4) * kTgLBO;  // 8-row blocks
+constexpr int kTgATile = 12 * kTgSBO;             // rows 0..95 (M = 128: see below)
+constexpr int kTgBTile = 6 * kTgSBO;              // 48 rows
+constexpr int kTgT2Stride = 25;                   // floats per row of the T2 transposition buffer
 
-struct __align__(128) Tf32Smem {
-    unsigned char A[kTfGroups][kTfATile];
-    unsigned char B[kTfGroups][kTfBTile];
-    float G[kTfElems][8][8][3];  // [elem][q][node][comp]
-    float cS[kTfElems][8][6];
-    float vnode[kTfElems][8][3];  // v at the element's nodes (matrix-free mode), FP32
-    float geo[kTfElems][8][8];    // sum_q G_a . c S G_b (symmetric in a, b)
-    int32_t node[kTfElems][8];
-    int32_t elem[kTfElems];
+// The MMA reads 128 rows of A; rows 96..127 (row blocks 12..15) fall on the next tile or on the
+// B tiles and produce accumulator rows that are never read, so they need neither zeros nor room.
+struct __align__(128) TgSmem {
+    unsigned char A[kTgGroups][kTgATile];  // after the MMAs: T2 rows, [group][96][kTgT2Stride] floats
+    unsigned char B[kTgGroups][kTgBTile];
+    float geo[kTgElems][36];      // sum_q tg_a . g_b, pairs a <= b row by row
+    float vnode[kTgElems][8][3];  // v at the element's nodes (matrix-free mode), FP32
+    int32_t node[kTgElems][8];
+    int32_t elem[kTgElems];
     uint64_t mbar;
     uint32_t tmem_base;
 };
+static_assert(kTgGroups * 96 * kTgT2Stride * 4 <= (int)sizeof(TgSmem::A), "T2 buffer fits in the A tiles");
 
-__device__ __forceinline__ uint32_t tf32_offset(int r, int k) {
-    // K-major core matrices of 8 rows x 16 bytes (4 x 32-bit); 12 core matrices along K = 48
-    return (uint32_t)((r >> 3) * kTfSBO + (k >> 2) * kTfLBO + (r & 7) * 16 + (k & 3) * 4);
+__device__ __forceinline__ uint32_t tg_offset(int r, int k) {
+    return (uint32_t)((r >> 3) * kTgSBO + (k >> 2) * kTgLBO + (r & 7) * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -59,6 +66,8 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
+// pair (a, b), a <= b, of the 36 pairs of an element ordered row by row
+__device__ __forceinline__ int tg_pair(int a, int b) { return 8 * a - (a * (a - 1)) / 2 + (b - a); }
 
 struct Tf32Args {
     const int32_t *__restrict__ conn;
@@ -66,39 +75,31 @@ struct Tf32Args {
     const int32_t *__restrict__ phase;
     const Material *__restrict__ mats;
     const double *__restrict__ E_elem;
-    const int32_t *__restrict__ elems;
+    const int32_t *__restrict__ elems;  // element list (one colour) or NULL = all elements in order
     int64_t n;
     uint32_t *flags;
 };
 
 // MODE 0: element pass of the row-gather assembly -- the element's 24 x 24 stiffness rows go to
-// vals = the workspace [element][24][24] (elements in order, one launch) and, if R is given, its
-// nodal forces to R = the workspace's residual part [element][local node][3];
+// vals = the workspace [element][24][24] and, if R is given, its nodal forces to R = the
+// workspace's residual part [element][local node][3];
 // MODE 1: y += K_e v_e (matrix-free, one launch per colour).
 template <int MODE>
 __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restrict__ u, const double *__restrict__ v,
                                               float *__restrict__ vals, double *__restrict__ R, double *__restrict__ y) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Tf32Smem &sm = *reinterpret_cast<Tf32Smem *>(smem_raw);
-    static_assert(kTfElems == 4 && kTfGroups == 1, "one MMA group of four elements per CTA");
-    const int t = threadIdx.x;
-    // Every warp covers all four elements (lane = element slot x Gauss point); warp w forms the
-    // operand rows of nodes 2w and 2w+1, warp 0 also the residual and the per-element records.
-    const int w = t >> 5, l = t & 7, es = (t >> 3) & 3;
-    const int grp = 0, el = es;
-    if (t < 32) tc::tmem_alloc(&sm.tmem_base, kTfTmemCols);
+    TgSmem &sm = *reinterpret_cast<TgSmem *>(smem_raw);
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int el = lane >> 3, l = lane & 7;  // element in the group, Gauss point
+    const int es = t >> 3;                   // element slot in the CTA (= 4 w + el)
+    if (w == 0) tc::tmem_alloc(&sm.tmem_base, kTgTmemCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
         tc::fence_mbar_init();
     }
-    // zero the padding rows 96..127 of every A tile (4 row blocks)
-    for (int i = t; i < kTfGroups * 32 * kTfK; i += 128) {
-        const int g = i / (32 * kTfK), rem = i % (32 * kTfK);
-        *reinterpret_cast<float *>(sm.A[g] + tf32_offset(96 + rem / kTfK, rem % kTfK)) = 0.0f;
-    }
-    // ---------------- phase 1: thread = (element, Gauss point) in every warp
+    // ---------------- phase 1: thread = (element, Gauss point)
     {
-        const int64_t slot = (int64_t)blockIdx.x * kTfElems + es;
+        const int64_t slot = (int64_t)blockIdx.x * kTgElems + es;
         const bool active = slot < A.n;
         const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
         int32_t node;
@@ -106,97 +107,132 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         float cu[3];
         gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
-        float H[3][3];
-        displacement_gradient(K, H);
-        Constitutive<float> c;
-        constitutive<float>(mt.law, (float)mt.lam, (float)mt.mu, H, c);
-        const bool lin = mt.law == JETSCI_LINEAR_ELASTIC;
-        if (MODE == 0 && R && w == 0) {
-            float f[3];
-            nodal_force(c.P, K, l, f);
-            if (active)
+        const float lam = (float)mt.lam, mu = (float)mt.mu;
+        // W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau, m, and the residual moment Q
+        float W[3][3], tau[3][3], Q[3][3], m;
+        bool ok = true;
+        if (mt.law == JETSCI_LINEAR_ELASTIC) {
+            const float rdJ = 1.0f / K.dJ;
 #pragma unroll
-                for (int i = 0; i < 3; i++) R[3 * (8 * e + hex_node_of_lane(l)) + i] = to_double(f[i]);
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) W[d][j] = K.aJ[d][j] * rdJ;
+            float H[3][3], sg[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) H[i][j] = K.Du[i][0] * W[0][j] + K.Du[i][1] * W[1][j] + K.Du[i][2] * W[2][j];
+            const float ltr = lam * (H[0][0] + H[1][1] + H[2][2]);
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    sg[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : 0.0f);
+                    tau[i][j] = 0.0f;
+                }
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int d = 0; d < 3; d++) Q[i][d] = sg[i][0] * K.aJ[d][0] + sg[i][1] * K.aJ[d][1] + sg[i][2] * K.aJ[d][2];
+            m = mu;
+        } else {
+            NeoHookeanState<float> st;
+            neo_hookean_state(K, lam, mu, st);
+            ok = st.ok;
+            m = st.m;
+            const float sc = K.dJ * st.rdj;
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    W[d][j] = st.aj[d][j] * st.rdj;
+                    tau[d][j] = st.tau[d][j];
+                }
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int d = 0; d < 3; d++)
+                    Q[i][d] = sc * (st.tau[i][0] * st.aj[d][0] + st.tau[i][1] * st.aj[d][1] + st.tau[i][2] * st.aj[d][2]);
         }
-        if (active && w == 0) {
-            uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (c.ok ? 0u : JETSCI_FLAG_BAD_STATE);
+        if (active) {
+            const uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE);
             if (bits) atomicOr(A.flags, bits);
         }
-        // Voigt tangent D (dS/dE w.r.t. tensor components) and the kinematic F of B
-        float D[6][6];
-        if (lin) {
-#pragma unroll
-            for (int a = 0; a < 6; a++)
-#pragma unroll
-                for (int b = 0; b < 6; b++)
-                    D[a][b] = (a < 3 && b < 3 ? c.lam : 0.0f) + (a == b ? 2.0f * c.m : 0.0f);
-        } else {
-            float Ci[3][3];
-#pragma unroll
-            for (int I = 0; I < 3; I++)
-#pragma unroll
-                for (int Kk = 0; Kk < 3; Kk++)
-                    Ci[I][Kk] = c.Fi[I][0] * c.Fi[Kk][0] + c.Fi[I][1] * c.Fi[Kk][1] + c.Fi[I][2] * c.Fi[Kk][2];
-#pragma unroll
-            for (int a = 0; a < 6; a++) {
-                const int I = voigt_i(a), Jj = voigt_j(a);
-#pragma unroll
-                for (int b = 0; b < 6; b++) {
-                    const int Kk = voigt_i(b), L = voigt_j(b);
-                    float w = c.lam * Ci[I][Jj] * Ci[Kk][L] + c.m * (Ci[I][Kk] * Ci[Jj][L] + Ci[I][L] * Ci[Jj][Kk]);
-                    D[a][b] = (Kk == L) ? w : 2.0f * w;
-                }
-            }
-        }
         const float cw = K.dJ * (1.0f / 512.0f);
-        const float rdJ = 1.0f / K.dJ;
-        if (w == 0)
+        const float cl = cw * lam, cm = cw * m;
+        const float t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
+        const float t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
+        const float xp = 1.0f + K.xi, xm = 1.0f - K.xi, yp = 1.0f + K.eta, ym = 1.0f - K.eta;
+        const float zp = 1.0f + K.zeta, zm = 1.0f - K.zeta;
+        unsigned char *At = sm.A[w];
+        unsigned char *Bt = sm.B[w];
+        const int kc = 8 * el + l;  // this lane's column of A and B
+        float g[8][3], tg[8][3];
 #pragma unroll
-            for (int a = 0; a < 6; a++) sm.cS[es][l][a] = lin ? 0.0f : cw * c.S[voigt_i(a)][voigt_j(a)];
-        // B_b and Z_b = c W D B_b for this warp's nodes b, written at k = 6q + alpha
-        unsigned char *At = sm.A[grp];
-        unsigned char *Bt = sm.B[grp];
+        for (int a = 0; a < 8; a++) {
+            const int bits = hex_bits_of_node(a);
+            const float fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
+            const float yz = fy * fz, xz = fx * fz, xy = fx * fy;
+            const float n0 = (bits & 1) ? yz : -yz, n1 = (bits & 2) ? xz : -xz, n2 = (bits & 4) ? xy : -xy;
 #pragma unroll
-        for (int bi = 0; bi < 2; bi++) {
-            const int b = 2 * w + bi;
-            const int nb = hex_node_of_lane(b);
-            const float s0 = (nb & 1) ? 1.0f : -1.0f, s1 = (nb & 2) ? 1.0f : -1.0f, s2 = (nb & 4) ? 1.0f : -1.0f;
-            const float fx = 1.0f + s0 * K.xi, fy = 1.0f + s1 * K.eta, fz = 1.0f + s2 * K.zeta;
-            const float n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
-            float G[3];
-#pragma unroll
-            for (int j = 0; j < 3; j++) G[j] = (K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2) * rdJ;
-#pragma unroll
-            for (int j = 0; j < 3; j++) sm.G[es][l][b][j] = G[j];
-            float Bb[6][3];
-#pragma unroll
-            for (int a = 0; a < 6; a++) {
-                const int I = voigt_i(a), Jj = voigt_j(a);
-#pragma unroll
-                for (int i = 0; i < 3; i++) Bb[a][i] = 0.5f * (c.F[i][I] * G[Jj] + c.F[i][Jj] * G[I]);
-            }
+            for (int j = 0; j < 3; j++) g[a][j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
+            tg[a][0] = t00 * g[a][0] + t01 * g[a][1] + t02 * g[a][2];
+            tg[a][1] = t01 * g[a][0] + t11 * g[a][1] + t12 * g[a][2];
+            tg[a][2] = t02 * g[a][0] + t12 * g[a][1] + t22 * g[a][2];
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                const int row = 24 * el + 3 * b + i;
+                // A: the element's own row block gets g, the other three elements' rows a zero in
+                // this column
 #pragma unroll
-                for (int a = 0; a < 6; a++) {
-                    float z = 0.0f;
-#pragma unroll
-                    for (int bb = 0; bb < 6; bb++) z += D[a][bb] * Bb[bb][i];
-                    const float wgt = a < 3 ? cw : 2.0f * cw;
-                    *reinterpret_cast<float *>(At + tf32_offset(row, 6 * l + a)) = to_tf32(Bb[a][i]);
-                    *reinterpret_cast<float *>(Bt + tf32_offset(row, 6 * l + a)) = to_tf32(wgt * z);
-                }
+                for (int eo = 0; eo < 4; eo++)
+                    *reinterpret_cast<float *>(At + tg_offset(24 * eo + 3 * a + i, kc)) =
+                        eo == el ? to_tf32(g[a][i]) : 0.0f;
+                *reinterpret_cast<float *>(Bt + tg_offset(3 * a + i, kc)) = to_tf32(cl * g[a][i]);
+                *reinterpret_cast<float *>(Bt + tg_offset(24 + 3 * a + i, kc)) = to_tf32(cm * g[a][i]);
             }
         }
-        if (w == 0) {
-            sm.node[es][hex_node_of_lane(l)] = node;
-            if (MODE == 1)
+        // geometric term: d_p = tg_a . g_b for the 36 pairs, summed over the 8 Gauss-point lanes
+        // by a reduce-scatter (halves exchanged across lanes 4, 2, 1 apart); lane l ends with
+        // the sums of pairs 18 (l>>2 & 1) + 9 (l>>1 & 1) + 5 (l & 1) + j, j < 5 (< 4 for odd l)
+        float d[36];
 #pragma unroll
-                for (int k = 0; k < 3; k++)
-                    sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
-            if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+        for (int a = 0; a < 8; a++)
+#pragma unroll
+            for (int b = a; b < 8; b++)
+                d[tg_pair(a, b)] = tg[a][0] * g[b][0] + tg[a][1] * g[b][1] + tg[a][2] * g[b][2];
+        const bool h4 = (l >> 2) & 1, h2 = (l >> 1) & 1, h1 = l & 1;
+        float d18[18], d9[9], d5[5];
+#pragma unroll
+        for (int j = 0; j < 18; j++) {
+            const float keep = h4 ? d[18 + j] : d[j], give = h4 ? d[j] : d[18 + j];
+            d18[j] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
         }
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            const float keep = h2 ? d18[9 + j] : d18[j], give = h2 ? d18[j] : d18[9 + j];
+            d9[j] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+        }
+#pragma unroll
+        for (int j = 0; j < 5; j++) {
+            const float lo = d9[j], hi = j + 5 < 9 ? d9[j + 5] : 0.0f;
+            const float keep = h1 ? hi : lo, give = h1 ? lo : hi;
+            d5[j] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
+        }
+        const int p0 = 18 * h4 + 9 * h2 + 5 * h1;
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            if (5 * h1 + j < 9) sm.geo[es][p0 + j] = d5[j];
+        // residual: nodal forces of the lane's node
+        float f[3];
+        nodal_force_of_moment(Q, K, l, f);
+        if (MODE == 0 && R && active)
+#pragma unroll
+            for (int i = 0; i < 3; i++) R[3 * (8 * e + hex_node_of_lane(l)) + i] = to_double(f[i]);
+        sm.node[es][hex_node_of_lane(l)] = node;
+        if (MODE == 1)
+#pragma unroll
+            for (int k = 0; k < 3; k++) sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
+        if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
     }
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -204,95 +240,80 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
     tc::fence_after_sync();
     const uint32_t tm = sm.tmem_base;
     if (t == 0) {
-        const uint32_t id = tc::idesc_tf32(128, 96);
-        for (int g = 0; g < kTfGroups; g++) {
+        const uint32_t id = tc::idesc_tf32(128, kTgN);
+        for (int g = 0; g < kTgGroups; g++) {
             const uint32_t a0 = tc::smem_addr(sm.A[g]), b0 = tc::smem_addr(sm.B[g]);
             // one MMA of K = 8 covers two core matrices along K
-            for (int kk = 0; kk < kTfK / 8; kk++)
-                tc::mma_tf32(tm + 96 * g, tc::smem_desc(a0 + kk * 2 * kTfLBO, kTfLBO, kTfSBO),
-                             tc::smem_desc(b0 + kk * 2 * kTfLBO, kTfLBO, kTfSBO), id, kk > 0 ? 1u : 0u);
+            for (int kk = 0; kk < kTgK / 8; kk++)
+                tc::mma_tf32(tm + kTgCols * g, tc::smem_desc(a0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO),
+                             tc::smem_desc(b0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO), id, kk > 0 ? 1u : 0u);
         }
+        tc::mma_commit(&sm.mbar);
     }
-    uint32_t ph = 0;
-    if (t == 0) tc::mma_commit(&sm.mbar);
-    // While the MMA runs: the geometric term of every element and node pair a <= b (row a of
-    // the upper triangle starts at 8a - a(a-1)/2), once per pair instead of once per row.
-    for (int it = t; it < kTfElems * 36; it += blockDim.x) {
-        const int ee = it / 36, p = it - 36 * (it / 36);
-        const int a = (p >= 8) + (p >= 15) + (p >= 21) + (p >= 26) + (p >= 30) + (p >= 33) + (p >= 35);
-        const int b = p - (8 * a - (a * (a - 1)) / 2) + a;
-        float g = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const float *s6 = sm.cS[ee][q];
-            const float *ga = sm.G[ee][q][a];
-            const float *gb = sm.G[ee][q][b];
-            const float sg0 = s6[0] * ga[0] + s6[5] * ga[1] + s6[4] * ga[2];
-            const float sg1 = s6[5] * ga[0] + s6[1] * ga[1] + s6[3] * ga[2];
-            const float sg2 = s6[4] * ga[0] + s6[3] * ga[1] + s6[2] * ga[2];
-            g += sg0 * gb[0] + sg1 * gb[1] + sg2 * gb[2];
-        }
-        sm.geo[ee][a][b] = g;
-        sm.geo[ee][b][a] = g;
-    }
-    const bool ok = tc::mbar_wait_bounded(&sm.mbar, ph & 1);
+    const bool ok = tc::mbar_wait_bounded(&sm.mbar, 0);
     tc::fence_after_sync();
-    __syncthreads();  // geometric terms of all threads visible to the epilogue
     if (!ok && t == 0) atomicOr(A.flags, JETSCI_FLAG_NONFINITE);
-    // ---------------- epilogue: thread t owns row t of each group's accumulator
-    // tcgen05.ld is warp-collective with one column address per warp, and a warp's 32 rows
-    // straddle at most two element slots: load each slot's 24 columns uniformly, keep own.
-    const int warp = t >> 5;
-    const int elr_lo = min((32 * warp) / 24, 3), elr_hi = min((32 * warp + 31) / 24, 3);
-    for (int g = 0; g < kTfGroups; g++) {
-        float rowv[24];
-        const int elr = min(t / 24, 3);  // element slot of this row (rows >= 96 are padding)
-#pragma unroll
-        for (int pass = 0; pass < 2; pass++) {
-            const int slot_e = pass == 0 ? elr_lo : elr_hi;
-            if (pass == 1 && elr_hi == elr_lo) break;  // warp-uniform condition
+    // ---------------- epilogue: thread t owns accumulator row r = t of each group (TMEM lane t);
+    // rows 96..127 (warp 3) carry nothing.  First T2 of every group into the (now free) A tiles,
+    float *t2 = reinterpret_cast<float *>(sm.A[0]);
+    const int r = t, rel = r / 24, ra = (r % 24) / 3, ri = r % 3;
+    if (w < 3) {
+        for (int g = 0; g < kTgGroups; g++) {
             float v16[16], v8[8];
-            tc::tmem_ld16(tc::tmem_lane_addr(tm, 96 * g + 24 * slot_e), v16);
-            tc::tmem_ld8(tc::tmem_lane_addr(tm, 96 * g + 24 * slot_e + 16), v8);
-            if (elr == slot_e) {
+            tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * g + 24), v16);
+            tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * g + 40), v8);
+            float *dst = t2 + (96 * g + r) * kTgT2Stride;
 #pragma unroll
-                for (int j = 0; j < 16; j++) rowv[j] = v16[j];
+            for (int c = 0; c < 16; c++) dst[c] = v16[c];
 #pragma unroll
-                for (int j = 0; j < 8; j++) rowv[16 + j] = v8[j];
+            for (int c = 0; c < 8; c++) dst[16 + c] = v8[c];
+        }
+    }
+    __syncthreads();
+    // then each row: K[(a,i),(b,k)] = T1[(a,i),(b,k)] + T2[(b,i),(a,k)] + delta_ik geo(a,b)
+    // (T2 is symmetric: its entry ((a,k),(b,i)) is row (b,i), column (a,k))
+    if (w < 3) {
+        for (int g = 0; g < kTgGroups; g++) {
+            float rowv[24];
+            {
+                float v16[16], v8[8];
+                tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * g), v16);
+                tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * g + 16), v8);
+#pragma unroll
+                for (int c = 0; c < 16; c++) rowv[c] = v16[c];
+#pragma unroll
+                for (int c = 0; c < 8; c++) rowv[16 + c] = v8[c];
             }
-        }
-        if (t >= 96) continue;
-        const int ee = 4 * g + elr;
-        const int32_t eid = sm.elem[ee];
-        if (eid < 0) continue;
-        const int a = (t % 24) / 3, i = t % 3;
-        // geometric term on the diagonal of each 3x3 block
+            const int ee = 4 * g + rel;
+            const int32_t eid = sm.elem[ee];
+            if (eid < 0) continue;
+            const float *t2e = t2 + (96 * g + 24 * rel) * kTgT2Stride;
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
-            const float geo = sm.geo[ee][a][b];
+            for (int b = 0; b < 8; b++) {
+                const float geo = sm.geo[ee][ra <= b ? tg_pair(ra, b) : tg_pair(b, ra)];
 #pragma unroll
-            for (int k = 0; k < 3; k++)
-                if (k == i) rowv[3 * b + k] += geo;  // compile-time index, predicated
-        }
-        const int32_t na = sm.node[ee][a];
-        if (MODE == 0) {
-            // row 3a + i of K_e: 96 contiguous bytes; a warp writes 32 consecutive rows
-            float4 *dst = reinterpret_cast<float4 *>(vals + 576 * (int64_t)eid + 24 * (3 * a + i));
+                for (int k = 0; k < 3; k++)
+                    rowv[3 * b + k] += t2e[(3 * b + ri) * kTgT2Stride + 3 * ra + k] + (k == ri ? geo : 0.0f);
+            }
+            if (MODE == 0) {
+                // row 3a + i of K_e: 96 contiguous bytes
+                float4 *dst = reinterpret_cast<float4 *>(vals + 576 * (int64_t)eid + 24 * (3 * ra + ri));
 #pragma unroll
-            for (int c = 0; c < 6; c++)
-                dst[c] = make_float4(rowv[4 * c], rowv[4 * c + 1], rowv[4 * c + 2], rowv[4 * c + 3]);
-        } else {
-            float s = 0.0f;
+                for (int c = 0; c < 6; c++)
+                    dst[c] = make_float4(rowv[4 * c], rowv[4 * c + 1], rowv[4 * c + 2], rowv[4 * c + 3]);
+            } else {
+                float s = 0.0f;
 #pragma unroll
-            for (int b = 0; b < 8; b++)
+                for (int b = 0; b < 8; b++)
 #pragma unroll
-                for (int k = 0; k < 3; k++) s += rowv[3 * b + k] * sm.vnode[ee][b][k];
-            y[3 * (int64_t)na + i] += to_double(s);
+                    for (int k = 0; k < 3; k++) s += rowv[3 * b + k] * sm.vnode[ee][b][k];
+                y[3 * (int64_t)sm.node[ee][ra] + ri] += to_double(s);
+            }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (t < 32) tc::tmem_dealloc(tm, kTfTmemCols);
+    if (w == 0) tc::tmem_dealloc(tm, kTgTmemCols);
 }
 
 jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float *vals, double *R, double *y,
@@ -304,7 +325,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
     A.mats = m->d_mats;
     A.E_elem = E_elem;
     A.flags = m->d_flags;
-    const size_t smem = sizeof(Tf32Smem);
+    const size_t smem = sizeof(TgSmem);
     if (vals) {
         // row-gather assembly: element rows (one launch, elements in order), then the row pass
         void *ws = nullptr;
@@ -316,7 +337,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
             JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             A.elems = nullptr;
             A.n = m->n_elem;
-            const unsigned grid = (unsigned)((A.n + kTfElems - 1) / kTfElems);
+            const unsigned grid = (unsigned)((A.n + kTgElems - 1) / kTgElems);
             k_tf32<0><<<grid, 128, smem, s>>>(A, u, nullptr, (float *)ws, Re, nullptr);
             JETSCI_CUDA_TRY(cudaGetLastError());
         }
@@ -327,7 +348,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
     for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
-        unsigned grid = (unsigned)((A.n + kTfElems - 1) / kTfElems);
+        unsigned grid = (unsigned)((A.n + kTgElems - 1) / kTgElems);
         k_tf32<1><<<grid, 128, smem, s>>>(A, u, v, nullptr, nullptr, y);
     });
     JETSCI_CUDA_TRY(cudaGetLastError());
