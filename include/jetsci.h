@@ -152,10 +152,9 @@ jetsci_status jetsci_residual(jetsci_mesh mesh, const double *u_dev, double *R_d
  * of a colour share a node).  FP32, TF32 and SURROGATE form every element's blocks in one
  * pass into a mesh-owned workspace, then write each CSR row once, its sum taken over the
  * elements of the row's node in ascending element order (no atomics in either; results are
- * bitwise reproducible).  The first such call on a mesh allocates that workspace (1,920
- * bytes per element for FP32, 2,496 for TF32/SURROGATE; kept at the largest size used and
- * freed by jetsci_mesh_destroy) and synchronises `stream`; it fails with JETSCI_ERR_ARG if
- * `stream` is being captured, so make one call before a capture.
+ * bitwise reproducible).  The first such call on a mesh allocates that workspace (2,496
+ * bytes per element, kept until jetsci_mesh_destroy) and synchronises `stream`; it fails
+ * with JETSCI_ERR_ARG if `stream` is being captured, so make one call before a capture.
  */
 jetsci_status jetsci_tangent_csr(jetsci_mesh mesh, const double *u_dev, void *vals_dev,
                                  double *R_dev, int32_t precision, const double *E_elem_dev,

@@ -123,25 +123,138 @@ struct TangentSmem {
     uint8_t first[TangentLayout<T>::kElems][8];  // first-writer bits of each node's blocks (FP64)
 };
 
-// Offset of the per-warp staging area of the element-block mode in shared memory.
-template <typename T>
-constexpr size_t tangent_stage_offset() { return (sizeof(TangentSmem<T>) + 15) / 16 * 16; }
+// Work items, per group of 8 elements: first the 28 off-diagonal node pairs (a < b) of each
+// element (7 warps), then their 8 diagonal pairs (2 warps).  Each warp holds items of one kind,
+// so neither the residual (diagonal pairs only) nor the symmetric diagonal block leaves lanes
+// predicated off, and an element's diagonal blocks follow its other blocks closely.
+constexpr int kGroup = 8, kGroupItems = kGroup * 36, kGroupOff = kGroup * 28;
 
-// kBlocks = false: scatter into the CSR values (vals) and R, one launch per colour.
-// kBlocks = true: the element pass of the row-gather assembly, over all elements in order in
-// one launch; vals is the element-block workspace (blocks.cuh) and R its residual part.  Each
-// warp stages its 32 blocks in shared memory and writes them as one contiguous span.
-template <typename T, typename VT, bool kBlocks>
+// Block K_ab of work item `it` (element slot ee, nodes a <= b) from the phase-1 records; for a
+// diagonal item with want_r also the residual R_a = sum_q c Tg g_a.
+template <typename T>
+__device__ __forceinline__ void tangent_item(const TangentSmem<T> &sm, int it, bool want_r, T Kab[3][3], T Ra[3],
+                                             int &ee, int &a, int &b, bool &off) {
+    using L = TangentLayout<T>;
+    const int grp = it / kGroupItems, r = it - kGroupItems * grp;
+    off = r < kGroupOff;
+    if (off) {
+        const int eg = r / 28;
+        const int p = r - 28 * eg;
+        ee = kGroup * grp + eg;
+        // p -> (a, b), a < b, in row order: row a starts at 7a - a(a-1)/2
+        a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
+        b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
+    } else {
+        const int j = r - kGroupOff;
+        ee = kGroup * grp + (j >> 3);
+        a = b = j & 7;
+    }
+    const T *pa = sm.v + ee * L::kElem + 3 * a;
+    const T *pb = sm.v + ee * L::kElem + 3 * b;
+    const T *pc = sm.coef + ee * 8 * L::kCoef;
+    if (off) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
+        T gs = T(0);
+#pragma unroll 2
+        for (int q = 0; q < 8; q++) {
+            const T *qa = pa + q * L::kPoint;
+            const T *qb = pb + q * L::kPoint;
+            const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
+            const T *ta = qa + L::kTG * L::kArr;
+            T l0, l1, l2, m0, m1, m2;
+            if constexpr (L::kPre) {
+                const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
+                l0 = la[0], l1 = la[1], l2 = la[2], m0 = ma[0], m1 = ma[1], m2 = ma[2];
+            } else {
+                const T *cf = pc + q * L::kCoef;
+                const T lam = cf[0], m = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
+                l0 = lam * a0, l1 = lam * a1, l2 = lam * a2, m0 = m * a0, m1 = m * a1, m2 = m * a2;
+            }
+            gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
+            Kab[0][0] = fma_t(l0, b0, fma_t(m0, b0, Kab[0][0]));
+            Kab[0][1] = fma_t(l0, b1, fma_t(m1, b0, Kab[0][1]));
+            Kab[0][2] = fma_t(l0, b2, fma_t(m2, b0, Kab[0][2]));
+            Kab[1][0] = fma_t(l1, b0, fma_t(m0, b1, Kab[1][0]));
+            Kab[1][1] = fma_t(l1, b1, fma_t(m1, b1, Kab[1][1]));
+            Kab[1][2] = fma_t(l1, b2, fma_t(m2, b1, Kab[1][2]));
+            Kab[2][0] = fma_t(l2, b0, fma_t(m0, b2, Kab[2][0]));
+            Kab[2][1] = fma_t(l2, b1, fma_t(m1, b2, Kab[2][1]));
+            Kab[2][2] = fma_t(l2, b2, fma_t(m2, b2, Kab[2][2]));
+        }
+        Kab[0][0] += gs;
+        Kab[1][1] += gs;
+        Kab[2][2] += gs;
+    } else {
+        // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
+        T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
+        T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
+#pragma unroll 2
+        for (int q = 0; q < 8; q++) {
+            const T *qa = pa + q * L::kPoint;
+            const T *cf = pc + q * L::kCoef;
+            const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
+            const T *ta = qa + L::kTG * L::kArr;
+            T s0, s1, s2;
+            if constexpr (L::kPre) {
+                const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
+                s0 = la[0] + ma[0], s1 = la[1] + ma[1], s2 = la[2] + ma[2];
+            } else {
+                const T lm = cf[0] + cf[1];
+                s0 = lm * b0, s1 = lm * b1, s2 = lm * b2;
+            }
+            gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
+            k00 = fma_t(s0, b0, k00);
+            k11 = fma_t(s1, b1, k11);
+            k22 = fma_t(s2, b2, k22);
+            k12 = fma_t(s1, b2, k12);
+            k02 = fma_t(s0, b2, k02);
+            k01 = fma_t(s0, b1, k01);
+            if (want_r) {
+                Ra0 = fma_t(cf[2], b0, fma_t(cf[7], b1, fma_t(cf[6], b2, Ra0)));
+                Ra1 = fma_t(cf[7], b0, fma_t(cf[3], b1, fma_t(cf[5], b2, Ra1)));
+                Ra2 = fma_t(cf[6], b0, fma_t(cf[5], b1, fma_t(cf[4], b2, Ra2)));
+            }
+        }
+        Kab[0][0] = k00 + gs;
+        Kab[1][1] = k11 + gs;
+        Kab[2][2] = k22 + gs;
+        Kab[1][2] = Kab[2][1] = k12;
+        Kab[0][2] = Kab[2][0] = k02;
+        Kab[0][1] = Kab[1][0] = k01;
+        Ra[0] = Ra0;
+        Ra[1] = Ra1;
+        Ra[2] = Ra2;
+    }
+}
+
+// Shared memory of the rows mode: the block's element matrices [element][24 rows][kRowStride],
+// laid over the phase-1 records once every item has read them.
+constexpr int kRowStride = 28;  // floats per staged row: 16-byte aligned, rows 4 banks apart
+template <typename T>
+constexpr size_t tangent_smem_bytes(bool rows) {
+    const size_t mat = (size_t)TangentLayout<T>::kElems * 24 * kRowStride * sizeof(T);
+    return rows && mat > sizeof(TangentSmem<T>) ? mat : sizeof(TangentSmem<T>);
+}
+
+// kRows = false: scatter into the CSR values (vals) and R, one launch per colour.
+// kRows = true: the element pass of the row-gather assembly, over all elements in order in one
+// launch: vals is the workspace [element][24][24] (blocks.cuh) and R its residual part.  Each
+// thread keeps its items' blocks in registers until every item has read the phase-1 records;
+// then the block's element matrices are assembled over those records in shared memory and
+// written out as one contiguous span.
+template <typename T, typename VT, bool kRows>
 __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs A, const double *__restrict__ u,
                                                  const int64_t *__restrict__ rowptr,
                                                  const uint8_t *__restrict__ slotmap,
                                                  const uint8_t *__restrict__ first,
                                                  VT *__restrict__ vals, double *__restrict__ R) {
     using L = TangentLayout<T>;
-    constexpr bool kFirst = L::kFirstWrites && !kBlocks;
+    constexpr bool kFirst = L::kFirstWrites && !kRows;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TangentSmem<T> &sm = *reinterpret_cast<TangentSmem<T> *>(smem_raw);
-    VT *stage = reinterpret_cast<VT *>(smem_raw + tangent_stage_offset<T>()) + (threadIdx.x >> 5) * (32 * kBlkStride);
     const int l = threadIdx.x & 7;
     const int es = threadIdx.x >> 3;
     const int64_t slot = (int64_t)blockIdx.x * L::kElems + es;
@@ -243,182 +356,205 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
     }
     __syncthreads();
-    // Work items, per group of 8 elements: first the 28 off-diagonal node pairs (a < b) of each
-    // element (7 warps), then their 8 diagonal pairs (2 warps).  Each warp holds items of one
-    // kind, so neither the residual (diagonal pairs only) nor the symmetric diagonal block leaves
-    // lanes predicated off, and an element's diagonal blocks follow its other blocks closely.
-    constexpr int kGroup = 8, kGroupItems = kGroup * 36, kGroupOff = kGroup * 28;
     static_assert(L::kElems % kGroup == 0 && kGroupOff % 32 == 0 && kGroupItems % 32 == 0,
                   "items of one kind per warp");
-    for (int it = threadIdx.x; it < L::kElems * 36; it += blockDim.x) {
-        const int grp = it / kGroupItems, r = it - kGroupItems * grp;
-        const bool off = r < kGroupOff;
-        int ee, a, b;
-        if (off) {
-            const int eg = r / 28;
-            const int p = r - 28 * eg;
-            ee = kGroup * grp + eg;
-            // p -> (a, b), a < b, in row order: row a starts at 7a - a(a-1)/2
-            a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
-            b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
-        } else {
-            const int j = r - kGroupOff;
-            ee = kGroup * grp + (j >> 3);
-            a = b = j & 7;
-        }
-        const int32_t eid = sm.elem[ee];
-        // (the element-block mode also runs the padding elements of the last block: its warps
-        // store together, and the workspace has room for them)
-        if (!kBlocks && eid < 0) continue;
-        const int64_t eidx = (int64_t)blockIdx.x * L::kElems + ee;  // storage index, element-block mode
-        const T *pa = sm.v + ee * L::kElem + 3 * a;
-        const T *pb = sm.v + ee * L::kElem + 3 * b;
-        const T *pc = sm.coef + ee * 8 * L::kCoef;
-        const int32_t na = sm.node[ee][a];
-        const int64_t sbase = 64 * (int64_t)eid;
-        T Kab[3][3];
-        if (off) {
+    if constexpr (!kRows) {
+        for (int it = threadIdx.x; it < L::kElems * 36; it += blockDim.x) {
+            const int grp = it / kGroupItems, r = it - kGroupItems * grp;
+            const bool off = r < kGroupOff;
+            int ee, a, b;
+            if (off) {
+                const int eg = r / 28;
+                const int p = r - 28 * eg;
+                ee = kGroup * grp + eg;
+                // p -> (a, b), a < b, in row order: row a starts at 7a - a(a-1)/2
+                a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
+                b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
+            } else {
+                const int j = r - kGroupOff;
+                ee = kGroup * grp + (j >> 3);
+                a = b = j & 7;
+            }
+            const int32_t eid = sm.elem[ee];
+            if (eid < 0) continue;
+            const T *pa = sm.v + ee * L::kElem + 3 * a;
+            const T *pb = sm.v + ee * L::kElem + 3 * b;
+            const T *pc = sm.coef + ee * 8 * L::kCoef;
+            const int32_t na = sm.node[ee][a];
+            const int64_t sbase = 64 * (int64_t)eid;
+            T Kab[3][3];
+            if (off) {
 #pragma unroll
-            for (int i = 0; i < 3; i++)
+                for (int i = 0; i < 3; i++)
 #pragma unroll
-                for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
-            T gs = T(0);
+                    for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
+                T gs = T(0);
 #pragma unroll 2
-            for (int q = 0; q < 8; q++) {
-                const T *qa = pa + q * L::kPoint;
-                const T *qb = pb + q * L::kPoint;
-                const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
-                const T *ta = qa + L::kTG * L::kArr;
-                T l0, l1, l2, m0, m1, m2;
-                if constexpr (L::kPre) {
-                    const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
-                    l0 = la[0], l1 = la[1], l2 = la[2], m0 = ma[0], m1 = ma[1], m2 = ma[2];
-                } else {
+                for (int q = 0; q < 8; q++) {
+                    const T *qa = pa + q * L::kPoint;
+                    const T *qb = pb + q * L::kPoint;
+                    const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
+                    const T *ta = qa + L::kTG * L::kArr;
+                    T l0, l1, l2, m0, m1, m2;
+                    if constexpr (L::kPre) {
+                        const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
+                        l0 = la[0], l1 = la[1], l2 = la[2], m0 = ma[0], m1 = ma[1], m2 = ma[2];
+                    } else {
+                        const T *cf = pc + q * L::kCoef;
+                        const T lam = cf[0], m = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
+                        l0 = lam * a0, l1 = lam * a1, l2 = lam * a2, m0 = m * a0, m1 = m * a1, m2 = m * a2;
+                    }
+                    gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
+                    Kab[0][0] = fma_t(l0, b0, fma_t(m0, b0, Kab[0][0]));
+                    Kab[0][1] = fma_t(l0, b1, fma_t(m1, b0, Kab[0][1]));
+                    Kab[0][2] = fma_t(l0, b2, fma_t(m2, b0, Kab[0][2]));
+                    Kab[1][0] = fma_t(l1, b0, fma_t(m0, b1, Kab[1][0]));
+                    Kab[1][1] = fma_t(l1, b1, fma_t(m1, b1, Kab[1][1]));
+                    Kab[1][2] = fma_t(l1, b2, fma_t(m2, b1, Kab[1][2]));
+                    Kab[2][0] = fma_t(l2, b0, fma_t(m0, b2, Kab[2][0]));
+                    Kab[2][1] = fma_t(l2, b1, fma_t(m1, b2, Kab[2][1]));
+                    Kab[2][2] = fma_t(l2, b2, fma_t(m2, b2, Kab[2][2]));
+                }
+                Kab[0][0] += gs;
+                Kab[1][1] += gs;
+                Kab[2][2] += gs;
+                {
+                    const int32_t nb = sm.node[ee][b];
+                    const int sab = slotmap[sbase + 8 * a + b];
+                    const int sba = slotmap[sbase + 8 * b + a];
+                    // the block's first writer (lowest colour) stores, later colours accumulate
+                    const bool fab = kFirst && ((sm.first[ee][a] >> b) & 1);
+                    const bool fba = kFirst && ((sm.first[ee][b] >> a) & 1);
+#pragma unroll
+                    for (int i = 0; i < 3; i++) {
+                        VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
+#pragma unroll
+                        for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), fab);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
+#pragma unroll
+                        for (int i = 0; i < 3; i++) put_or_add(dst + i, store_as<VT>(Kab[i][k]), fba);
+                    }
+                }
+            } else {
+                // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
+                T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
+                T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
+#pragma unroll 2
+                for (int q = 0; q < 8; q++) {
+                    const T *qa = pa + q * L::kPoint;
                     const T *cf = pc + q * L::kCoef;
-                    const T lam = cf[0], m = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
-                    l0 = lam * a0, l1 = lam * a1, l2 = lam * a2, m0 = m * a0, m1 = m * a1, m2 = m * a2;
+                    const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
+                    const T *ta = qa + L::kTG * L::kArr;
+                    T s0, s1, s2;
+                    if constexpr (L::kPre) {
+                        const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
+                        s0 = la[0] + ma[0], s1 = la[1] + ma[1], s2 = la[2] + ma[2];
+                    } else {
+                        const T lm = cf[0] + cf[1];
+                        s0 = lm * b0, s1 = lm * b1, s2 = lm * b2;
+                    }
+                    gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
+                    k00 = fma_t(s0, b0, k00);
+                    k11 = fma_t(s1, b1, k11);
+                    k22 = fma_t(s2, b2, k22);
+                    k12 = fma_t(s1, b2, k12);
+                    k02 = fma_t(s0, b2, k02);
+                    k01 = fma_t(s0, b1, k01);
+                    if (R) {
+                        Ra0 = fma_t(cf[2], b0, fma_t(cf[7], b1, fma_t(cf[6], b2, Ra0)));
+                        Ra1 = fma_t(cf[7], b0, fma_t(cf[3], b1, fma_t(cf[5], b2, Ra1)));
+                        Ra2 = fma_t(cf[6], b0, fma_t(cf[5], b1, fma_t(cf[4], b2, Ra2)));
+                    }
                 }
-                gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
-                Kab[0][0] = fma_t(l0, b0, fma_t(m0, b0, Kab[0][0]));
-                Kab[0][1] = fma_t(l0, b1, fma_t(m1, b0, Kab[0][1]));
-                Kab[0][2] = fma_t(l0, b2, fma_t(m2, b0, Kab[0][2]));
-                Kab[1][0] = fma_t(l1, b0, fma_t(m0, b1, Kab[1][0]));
-                Kab[1][1] = fma_t(l1, b1, fma_t(m1, b1, Kab[1][1]));
-                Kab[1][2] = fma_t(l1, b2, fma_t(m2, b1, Kab[1][2]));
-                Kab[2][0] = fma_t(l2, b0, fma_t(m0, b2, Kab[2][0]));
-                Kab[2][1] = fma_t(l2, b1, fma_t(m1, b2, Kab[2][1]));
-                Kab[2][2] = fma_t(l2, b2, fma_t(m2, b2, Kab[2][2]));
-            }
-            Kab[0][0] += gs;
-            Kab[1][1] += gs;
-            Kab[2][2] += gs;
-            if constexpr (!kBlocks) {
-                const int32_t nb = sm.node[ee][b];
-                const int sab = slotmap[sbase + 8 * a + b];
-                const int sba = slotmap[sbase + 8 * b + a];
-                // the block's first writer (lowest colour) stores, later colours accumulate
-                const bool fab = kFirst && ((sm.first[ee][a] >> b) & 1);
-                const bool fba = kFirst && ((sm.first[ee][b] >> a) & 1);
+                Kab[0][0] = k00 + gs;
+                Kab[1][1] = k11 + gs;
+                Kab[2][2] = k22 + gs;
+                Kab[1][2] = Kab[2][1] = k12;
+                Kab[0][2] = Kab[2][0] = k02;
+                Kab[0][1] = Kab[1][0] = k01;
+                {
+                    const int saa = slotmap[sbase + 9 * a];
+                    const bool faa = kFirst && ((sm.first[ee][a] >> a) & 1);
 #pragma unroll
-                for (int i = 0; i < 3; i++) {
-                    VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
+                    for (int i = 0; i < 3; i++) {
+                        VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * saa;
 #pragma unroll
-                    for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), fab);
+                        for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), faa);
+                    }
                 }
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
-#pragma unroll
-                    for (int i = 0; i < 3; i++) put_or_add(dst + i, store_as<VT>(Kab[i][k]), fba);
-                }
-            }
-        } else {
-            // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
-            T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
-            T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
-#pragma unroll 2
-            for (int q = 0; q < 8; q++) {
-                const T *qa = pa + q * L::kPoint;
-                const T *cf = pc + q * L::kCoef;
-                const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
-                const T *ta = qa + L::kTG * L::kArr;
-                T s0, s1, s2;
-                if constexpr (L::kPre) {
-                    const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
-                    s0 = la[0] + ma[0], s1 = la[1] + ma[1], s2 = la[2] + ma[2];
-                } else {
-                    const T lm = cf[0] + cf[1];
-                    s0 = lm * b0, s1 = lm * b1, s2 = lm * b2;
-                }
-                gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
-                k00 = fma_t(s0, b0, k00);
-                k11 = fma_t(s1, b1, k11);
-                k22 = fma_t(s2, b2, k22);
-                k12 = fma_t(s1, b2, k12);
-                k02 = fma_t(s0, b2, k02);
-                k01 = fma_t(s0, b1, k01);
                 if (R) {
-                    Ra0 = fma_t(cf[2], b0, fma_t(cf[7], b1, fma_t(cf[6], b2, Ra0)));
-                    Ra1 = fma_t(cf[7], b0, fma_t(cf[3], b1, fma_t(cf[5], b2, Ra1)));
-                    Ra2 = fma_t(cf[6], b0, fma_t(cf[5], b1, fma_t(cf[4], b2, Ra2)));
-                }
-            }
-            Kab[0][0] = k00 + gs;
-            Kab[1][1] = k11 + gs;
-            Kab[2][2] = k22 + gs;
-            Kab[1][2] = Kab[2][1] = k12;
-            Kab[0][2] = Kab[2][0] = k02;
-            Kab[0][1] = Kab[1][0] = k01;
-            if constexpr (!kBlocks) {
-                const int saa = slotmap[sbase + 9 * a];
-                const bool faa = kFirst && ((sm.first[ee][a] >> a) & 1);
-#pragma unroll
-                for (int i = 0; i < 3; i++) {
-                    VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * saa;
-#pragma unroll
-                    for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), faa);
-                }
-            }
-            if (R) {
-                const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
-                if (!fin && eid >= 0) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
-                if constexpr (kBlocks) {
-                    double *dst = R + 3 * (8 * eidx + a);
-                    dst[0] = to_double(Ra0);
-                    dst[1] = to_double(Ra1);
-                    dst[2] = to_double(Ra2);
-                } else {
+                    const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
+                    if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
                     R[3 * (int64_t)na] += to_double(Ra0);
                     R[3 * (int64_t)na + 1] += to_double(Ra1);
                     R[3 * (int64_t)na + 2] += to_double(Ra2);
                 }
             }
         }
-        if constexpr (kBlocks) {
-            // the warp's 32 items are 32 consecutive blocks of one group of 8 elements
-            const int lane = threadIdx.x & 31;
-            VT blk[kBlkStride];
+    } else {
+        constexpr int kItems = L::kElems * 36;
+        constexpr int kIters = (kItems + L::kThreads - 1) / L::kThreads;
+        VT res[kIters][9];
 #pragma unroll
-            for (int i = 0; i < 3; i++)
+        for (int j = 0; j < kIters; j++) {
+            const int it = threadIdx.x + j * L::kThreads;
+            if (it < kItems) {  // warp-uniform (kItems is a multiple of 32)
+                T Kab[3][3], Ra[3];
+                int ee, a, b;
+                bool off;
+                tangent_item<T>(sm, it, R != nullptr, Kab, Ra, ee, a, b, off);
 #pragma unroll
-                for (int k = 0; k < 3; k++) blk[3 * i + k] = store_as<VT>(Kab[i][k]);
+                for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int c = kBlkVals; c < kBlkStride; c++) blk[c] = VT(0);
-            constexpr int kVecBlk = kBlkStride * (int)sizeof(VT) / 16;
+                    for (int k = 0; k < 3; k++) res[j][3 * i + k] = store_as<VT>(Kab[i][k]);
+                const int32_t eid = sm.elem[ee];
+                if (!off && R && eid >= 0) {
+                    const bool fin = isfinite(Ra[0]) && isfinite(Ra[1]) && isfinite(Ra[2]);
+                    if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
 #pragma unroll
-            for (int c = 0; c < kVecBlk; c++)
-                reinterpret_cast<uint4 *>(stage + kBlkStride * lane)[c] = reinterpret_cast<const uint4 *>(blk)[c];
-            __syncwarp();
-            const int it0 = it - lane;
-            const int g0 = it0 / kGroupItems;
-            const int64_t gblk = ((int64_t)blockIdx.x * (L::kElems / kGroup) + g0) * kBlkPerGroup +
-                                 (it0 - kGroupItems * g0);
-            uint4 *dst = reinterpret_cast<uint4 *>(vals + kBlkStride * gblk);
-            const uint4 *src = reinterpret_cast<const uint4 *>(stage);
-            constexpr int kVec = 32 * kVecBlk;
+                    for (int i = 0; i < 3; i++) R[3 * (8 * (int64_t)eid + a) + i] = to_double(Ra[i]);
+                }
+            }
+        }
+        __syncthreads();  // every item has read the phase-1 records: lay the matrices over them
+        VT *mat = reinterpret_cast<VT *>(smem_raw);
 #pragma unroll
-            for (int c = lane; c < kVec; c += 32) dst[c] = src[c];
-            __syncwarp();
+        for (int j = 0; j < kIters; j++) {
+            const int it = threadIdx.x + j * L::kThreads;
+            if (it < kItems) {
+                const int grp = it / kGroupItems, r = it - kGroupItems * grp;
+                int ee, a, b;
+                if (r < kGroupOff) {
+                    const int eg = r / 28, p = r - 28 * eg;
+                    ee = kGroup * grp + eg;
+                    a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
+                    b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
+                } else {
+                    ee = kGroup * grp + ((r - kGroupOff) >> 3);
+                    a = b = (r - kGroupOff) & 7;
+                }
+                VT *me = mat + (size_t)ee * 24 * kRowStride;
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        me[(3 * a + i) * kRowStride + 3 * b + k] = res[j][3 * i + k];
+                        me[(3 * b + k) * kRowStride + 3 * a + i] = res[j][3 * i + k];  // K_ba = K_ab^T
+                    }
+            }
+        }
+        __syncthreads();
+        // rows of the block's elements, in order: contiguous in the workspace
+        constexpr int kVecRow = 24 * (int)sizeof(VT) / 16;
+        const int64_t e0 = (int64_t)blockIdx.x * L::kElems;
+        const int n_rows = (int)((A.n - e0 < L::kElems ? A.n - e0 : L::kElems) * 24);
+        uint4 *dst = reinterpret_cast<uint4 *>(vals + 576 * e0);
+        for (int c = threadIdx.x; c < n_rows * kVecRow; c += blockDim.x) {
+            const int row = c / kVecRow, part = c - kVecRow * row;
+            dst[c] = reinterpret_cast<const uint4 *>(mat + (size_t)row * kRowStride)[part];
         }
     }
 }
@@ -549,8 +685,8 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
 // is the element-ordered sum of its blocks, written once (no clearing, no colouring).
 jetsci_status launch_insert_blocks(jetsci_mesh m, const void *Ke, void *vals, bool fp32, cudaStream_t s) {
     if (reinterpret_cast<uintptr_t>(Ke) % 16 != 0) return fail(JETSCI_ERR_ARG, "Ke_dev must be 16-byte aligned");
-    if (fp32) return launch_gather_rows<float>(m, (const float *)Ke, true, nullptr, (float *)vals, nullptr, s);
-    return launch_gather_rows<double>(m, (const double *)Ke, true, nullptr, (double *)vals, nullptr, s);
+    if (fp32) return launch_gather_rows<float>(m, (const float *)Ke, nullptr, (float *)vals, nullptr, s);
+    return launch_gather_rows<double>(m, (const double *)Ke, nullptr, (double *)vals, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------- launchers
@@ -596,12 +732,12 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
     return JETSCI_OK;
 }
 
-template <typename T, typename VT, bool kBlocks>
+template <typename T, typename VT, bool kRows>
 static jetsci_status tangent_setup(size_t smem) {
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
     // The FP64 tangent needs 56 KB of shared memory per 8-element block: take the largest carveout.
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kBlocks>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kRows>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared));
     return JETSCI_OK;
 }
@@ -609,7 +745,7 @@ static jetsci_status tangent_setup(size_t smem) {
 template <typename T, typename VT>
 static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u, VT *vals, double *R,
                                      cudaStream_t s) {
-    const size_t smem = sizeof(TangentSmem<T>);
+    const size_t smem = tangent_smem_bytes<T>(false);
     if (jetsci_status st = tangent_setup<T, VT, false>(smem)) return st;
     // One launch per colour.  Splitting colours into L2-sized chunks (chunk-major order) was
     // measured slower at 128^3 for every precision: the 8x more, smaller launches lose more
@@ -625,27 +761,26 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
     return JETSCI_OK;
 }
 
-// Row-gather assembly: the element pass writes every element's blocks and residual vectors to
-// the mesh's workspace in one launch, the row pass forms each CSR row and R entry once.
+// Row-gather assembly: the element pass writes every element's 24 x 24 rows and residual
+// vectors to the mesh's workspace in one launch, the row pass forms each CSR row and R entry once.
 template <typename T, typename VT>
 static jetsci_status tangent_rows(jetsci_mesh m, ElemArgs A, const double *u, VT *vals, double *R,
                                   cudaStream_t s) {
     void *ws = nullptr;
     double *Re = nullptr;
-    if (jetsci_status st = ensure_block_workspace(m, blk_values_bytes(m->n_elem, sizeof(VT)), s, &ws, &Re)) return st;
-    VT *blocks = reinterpret_cast<VT *>(ws);
+    if (jetsci_status st = ensure_block_workspace(m, blk_full_bytes(m->n_elem, sizeof(VT)), s, &ws, &Re)) return st;
     if (!R) Re = nullptr;
     if (m->n_elem > 0) {
         using L = TangentLayout<T>;
-        const size_t smem = tangent_stage_offset<T>() + (size_t)(L::kThreads / 32) * 32 * kBlkStride * sizeof(VT);
+        const size_t smem = tangent_smem_bytes<T>(true);
         if (jetsci_status st = tangent_setup<T, VT, true>(smem)) return st;
         A.elems = nullptr;
         A.n = m->n_elem;
         const unsigned grid = (unsigned)((A.n + L::kElems - 1) / L::kElems);
-        k_tangent<T, VT, true><<<grid, L::kThreads, smem, s>>>(A, u, nullptr, nullptr, nullptr, blocks, Re);
+        k_tangent<T, VT, true><<<grid, L::kThreads, smem, s>>>(A, u, nullptr, nullptr, nullptr, (VT *)ws, Re);
         JETSCI_CUDA_TRY(cudaGetLastError());
     }
-    return launch_gather_rows<VT>(m, blocks, false, Re, vals, R, s);
+    return launch_gather_rows<VT>(m, (const VT *)ws, Re, vals, R, s);
 }
 
 jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double *R, int precision,

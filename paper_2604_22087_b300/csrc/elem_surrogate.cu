@@ -326,7 +326,7 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
                                                            (float *)ws, Re);
             JETSCI_CUDA_TRY(cudaGetLastError());
         }
-        return launch_gather_rows<float>(m, (const float *)ws, true, Re, vals, R, s);
+        return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);
     }
     JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_elem_surrogate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));

@@ -341,7 +341,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
             k_tf32<0><<<grid, 128, smem, s>>>(A, u, nullptr, (float *)ws, Re, nullptr);
             JETSCI_CUDA_TRY(cudaGetLastError());
         }
-        return launch_gather_rows<float>(m, (const float *)ws, true, Re, vals, R, s);
+        return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);
     }
     JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));

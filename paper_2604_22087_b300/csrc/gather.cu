@@ -26,45 +26,22 @@ constexpr int kAccStride = 12;  // accumulator values per slot (3 x 3 block, 16-
 template <typename VT>
 constexpr int row_chunk() { return 2; }
 
-// Block K_e(la, lb) (rows at node la) into y[3 i + k]: compact symmetric layout (blocks.cuh),
-// the pair (lb, la) of lb < la read transposed; or caller blocks [e][24][24].
-template <typename VT, bool kFull>
+// Block K_e(la, lb) (rows at node la) of the rows layout [e][24][24] into y[3 i + k].
+template <typename VT>
 __device__ __forceinline__ void load_block(const VT *__restrict__ blocks, int64_t e, int la, int lb, VT y[9]) {
-    if constexpr (kFull) {
-        const VT *p = blocks + 576 * e + 72 * la + 3 * lb;
+    const VT *p = blocks + 576 * e + 72 * la + 3 * lb;
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int k = 0; k < 3; k++) y[3 * i + k] = __ldg(p + 24 * i + k);
-    } else {
-        const bool tr = la > lb;
-        const VT *p = blocks + kBlkStride * blk_index(e, tr ? lb : la, tr ? la : lb);
-        VT x[kBlkStride];
-#pragma unroll
-        for (int c = 0; c < kBlkStride * (int)sizeof(VT) / 16; c++)
-            reinterpret_cast<uint4 *>(x)[c] = __ldg(reinterpret_cast<const uint4 *>(p) + c);
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int k = 0; k < 3; k++) y[3 * i + k] = tr ? x[3 * k + i] : x[3 * i + k];
-    }
+        for (int k = 0; k < 3; k++) y[3 * i + k] = __ldg(p + 24 * i + k);
 }
 
-// Brings element e's blocks into L2 in whole lines (the blocks of the node rows that follow
-// then hit L2 instead of fetching 48-byte pieces from DRAM one node at a time).
-template <typename VT, bool kFull>
+// Brings element e's rows into L2 in whole lines (the blocks of the node rows that follow then
+// hit L2 instead of fetching short pieces from DRAM one node at a time).
+template <typename VT>
 __device__ __forceinline__ void prefetch_element(const VT *__restrict__ blocks, int64_t e) {
-    if constexpr (kFull) {
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blocks + 576 * e), "r"(576u * (unsigned)sizeof(VT))
-                     : "memory");
-    } else {
-        const VT *off = blocks + kBlkStride * blk_index(e, 0, 1);  // its 28 pairs a < b, contiguous
-        const VT *dia = blocks + kBlkStride * blk_index(e, 0, 0);  // its 8 pairs a == a, contiguous
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(off), "r"(28u * kBlkStride * (unsigned)sizeof(VT))
-                     : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(dia), "r"(8u * kBlkStride * (unsigned)sizeof(VT))
-                     : "memory");
-    }
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blocks + 576 * e), "r"(576u * (unsigned)sizeof(VT))
+                 : "memory");
 }
 
 __device__ __forceinline__ int warp_max(int v) {
@@ -80,7 +57,7 @@ __device__ __forceinline__ int warp_max(int v) {
 // collide, and every contribution to an entry arrives in element order.  A lane loads the
 // blocks of several elements before adding any (they are in flight together).  Nodes with more
 // than 32 neighbours take one pass per 32 slots.
-template <typename VT, bool kFull>
+template <typename VT>
 __global__ void __launch_bounds__(32 * kRowWarps) k_gather_rows(int64_t n_nodes, const int64_t *__restrict__ ne_ptr,
                                                                 const uint32_t *__restrict__ ne,
                                                                 const uint8_t *__restrict__ slot,
@@ -123,13 +100,13 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_gather_rows(int64_t n_nodes,
                 sw = __ldg(reinterpret_cast<const uint2 *>(slot + 64 * (int64_t)(tm >> 3) + 8 * (tm & 7)));
                 // the element's first node (local node 0, the lowest id on ordered meshes) pulls
                 // the whole element into L2 (measured 4-5% faster at 128^3)
-                if ((tm & 7) == 0 && sc == 0) prefetch_element<VT, kFull>(blocks, tm >> 3);
+                if ((tm & 7) == 0 && sc == 0) prefetch_element<VT>(blocks, tm >> 3);
             }
             VT y[kChunk][9];
 #pragma unroll
             for (int j = 0; j < kChunk; j++) {
                 const uint32_t t = __shfl_sync(0xffffffffu, tm, gl0 + j);
-                if (j < nc && sc < n_sc) load_block<VT, kFull>(blocks, t >> 3, (int)(t & 7), lb, y[j]);
+                if (j < nc && sc < n_sc) load_block<VT>(blocks, t >> 3, (int)(t & 7), lb, y[j]);
             }
 #pragma unroll
             for (int j = 0; j < kChunk; j++) {
@@ -196,28 +173,23 @@ jetsci_status ensure_block_workspace(jetsci_mesh m, size_t values_bytes, cudaStr
 }
 
 template <typename VT>
-jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, bool full, const double *Re, VT *vals,
-                                 double *R, cudaStream_t s) {
+jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, const double *Re, VT *vals, double *R,
+                                 cudaStream_t s) {
     if (m->n_nodes == 0) return JETSCI_OK;
     constexpr int kNodes = kRowWarps * kNodesPerWarp;
     const unsigned grid = (unsigned)((m->n_nodes + kNodes - 1) / kNodes);
     // several blocks per SM need more shared memory than the default carveout gives
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(full ? k_gather_rows<VT, true> : k_gather_rows<VT, false>,
-                                         cudaFuncAttributePreferredSharedMemoryCarveout,
+    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_gather_rows<VT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared));
-    if (full)
-        k_gather_rows<VT, true><<<grid, 32 * kRowWarps, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot,
-                                                                m->d_rowptr, blocks, Re, vals, R);
-    else
-        k_gather_rows<VT, false><<<grid, 32 * kRowWarps, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot,
-                                                                 m->d_rowptr, blocks, Re, vals, R);
+    k_gather_rows<VT><<<grid, 32 * kRowWarps, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot, m->d_rowptr,
+                                                      blocks, Re, vals, R);
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
 }
 
-template jetsci_status launch_gather_rows<float>(jetsci_mesh, const float *, bool, const double *, float *,
-                                                 double *, cudaStream_t);
-template jetsci_status launch_gather_rows<double>(jetsci_mesh, const double *, bool, const double *, double *,
-                                                  double *, cudaStream_t);
+template jetsci_status launch_gather_rows<float>(jetsci_mesh, const float *, const double *, float *, double *,
+                                                 cudaStream_t);
+template jetsci_status launch_gather_rows<double>(jetsci_mesh, const double *, const double *, double *, double *,
+                                                  cudaStream_t);
 
 }  // namespace jetsci

@@ -106,10 +106,11 @@ jetsci_status launch_insert_blocks(jetsci_mesh m, const void *Ke, void *vals, bo
 // being captured and the workspace is too small.  Sets *blocks and *Re.
 jetsci_status ensure_block_workspace(jetsci_mesh m, size_t values_bytes, cudaStream_t s, void **blocks, double **Re);
 // Row pass of the row-gather assembly: vals (all nnz entries) and, if R != NULL, R (all n_dof
-// entries) are overwritten from element blocks, compact (blocks.cuh) or [n_elem][24][24] (full).
+// entries) are overwritten from element rows [n_elem][24][24] (blocks.cuh) and, for R, the
+// residual vectors Re [n_elem][8][3].
 template <typename VT>
-jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, bool full, const double *Re, VT *vals,
-                                 double *R, cudaStream_t s);
+jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, const double *Re, VT *vals, double *R,
+                                 cudaStream_t s);
 jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
                                    const double *R, double *g, int precision, cudaStream_t s);
 
