@@ -731,12 +731,8 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
 
 template <typename T, typename VT, bool kRows>
 static jetsci_status tangent_setup(size_t smem) {
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
     // The FP64 tangent needs 56 KB of shared memory per 8-element block: take the largest carveout.
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tangent<T, VT, kRows>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared));
-    return JETSCI_OK;
+    return kernel_attrs_once<k_tangent<T, VT, kRows>>(smem, true);
 }
 
 template <typename T, typename VT>

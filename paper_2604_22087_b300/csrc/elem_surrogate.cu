@@ -317,8 +317,7 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
             return st;
         if (!R) Re = nullptr;
         if (m->n_elem > 0) {
-            JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_elem_surrogate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
+            if (jetsci_status st = kernel_attrs_once<k_elem_surrogate<true>>(smem, false)) return st;
             A.elems = nullptr;
             A.n = m->n_elem;
             const unsigned grid = (unsigned)((A.n + 15) / 16);
@@ -328,7 +327,7 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
         }
         return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);
     }
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_elem_surrogate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (jetsci_status st = kernel_attrs_once<k_elem_surrogate<false>>(smem, false)) return st;
     if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;

@@ -334,7 +334,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
             return st;
         if (!R) Re = nullptr;
         if (m->n_elem > 0) {
-            JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (jetsci_status st = kernel_attrs_once<k_tf32<0>>(smem, false)) return st;
             A.elems = nullptr;
             A.n = m->n_elem;
             const unsigned grid = (unsigned)((A.n + kTgElems - 1) / kTgElems);
@@ -343,7 +343,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
         }
         return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);
     }
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (jetsci_status st = kernel_attrs_once<k_tf32<1>>(smem, false)) return st;
     JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;

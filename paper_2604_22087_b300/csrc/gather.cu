@@ -179,8 +179,7 @@ jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, const double *
     constexpr int kNodes = kRowWarps * kNodesPerWarp;
     const unsigned grid = (unsigned)((m->n_nodes + kNodes - 1) / kNodes);
     // several blocks per SM need more shared memory than the default carveout gives
-    JETSCI_CUDA_TRY(cudaFuncSetAttribute(k_gather_rows<VT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared));
+    if (jetsci_status st = kernel_attrs_once<k_gather_rows<VT>>(0, true)) return st;
     k_gather_rows<VT><<<grid, 32 * kRowWarps, 0, s>>>(m->n_nodes, m->d_ne_ptr, m->d_ne, m->d_slot, m->d_rowptr,
                                                       blocks, Re, vals, R);
     JETSCI_CUDA_TRY(cudaGetLastError());

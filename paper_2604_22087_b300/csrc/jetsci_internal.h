@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -74,6 +75,25 @@ jetsci_status cuda_fail(cudaError_t err, const char *what);
 // Checks that the current device is the mesh's device (switches to it) and records
 // the stream; returns JETSCI_OK or an error.
 jetsci_status enter(jetsci_mesh m, void *stream, cudaStream_t *s);
+
+// Sets Kernel's dynamic shared-memory limit (if max_dyn_smem > 0) and, if asked, the largest
+// shared-memory carveout, once per device: these are not stream operations, and doing them once
+// keeps every later call of the library free of them (so it can run inside a CUDA graph capture).
+template <auto Kernel>
+inline jetsci_status kernel_attrs_once(size_t max_dyn_smem, bool max_carveout) {
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    JETSCI_CUDA_TRY(cudaGetDevice(&dev));
+    const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return JETSCI_OK;
+    if (max_dyn_smem > 0)
+        JETSCI_CUDA_TRY(cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dyn_smem));
+    if (max_carveout)
+        JETSCI_CUDA_TRY(cudaFuncSetAttribute(Kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+    done.fetch_or(bit, std::memory_order_release);
+    return JETSCI_OK;
+}
 
 // Calls f(elems, n) for the element list of every colour in colour order.  Within one list no
 // two elements share a node; the lists are launched in a fixed order on one stream, so the
