@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
     __shared__ int32_t s_elem[16];
     const int t = threadIdx.x;
     const int l = t & 7, es = t >> 3;
-    if (t < 32) tc::tmem_alloc(&sm.tmem_base, kMlpTmemCols);
+    constexpr uint32_t kCols = TANGENT ? kMlpTmemCols : kMlpFwdTmemCols;
+    if (t < 32) tc::tmem_alloc(&sm.tmem_base, kCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
         tc::fence_mbar_init();
@@ -108,7 +109,8 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
     // ---------------- phase 2
     uint32_t phase_ctr = 0;
     float y[6], Jm[6][6];
-    const bool ok = mlp_forward_jacobian(sm, phase_ctr, y, Jm);
+    // the residual needs S only: the Jacobian's six directions run for the tangent alone
+    const bool ok = TANGENT ? mlp_forward_jacobian(sm, phase_ctr, y, Jm) : mlp_forward(sm, phase_ctr, y);
     float S[6], D[6][6];
     bool ok_state = true;
     const int phs = ph == 1 ? 1 : 0;
@@ -117,8 +119,9 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
         for (int c = 0; c < 6; c++) {
             const float sc = phs ? cfg.out_scale[1][c] : cfg.out_scale[0][c];
             S[c] = y[c] * sc + (phs ? cfg.out_shift[1][c] : cfg.out_shift[0][c]);
+            if (TANGENT)
 #pragma unroll
-            for (int d = 0; d < 6; d++) D[c][d] = Jm[c][d] * sc / cfg.in_scale;
+                for (int d = 0; d < 6; d++) D[c][d] = Jm[c][d] * sc / cfg.in_scale;
         }
     } else {
         // plain compressible neo-Hookean: S = mu I + (lam lnJ - mu) C^-1,
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
         for (int a = 0; a < 6; a++) {
             const int I = voigt_i(a), Jj = voigt_j(a);
             S[a] = (lam * lnJ - mu) * Ci[I][Jj] + (I == Jj ? mu : 0.0f);
+            if (TANGENT)
 #pragma unroll
             for (int b = 0; b < 6; b++) {
                 const int Kk = voigt_i(b), L = voigt_j(b);
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
     if (!TANGENT) {
         tc::fence_before_sync();
         __syncthreads();
-        if (t < 32) tc::tmem_dealloc(sm.tmem_base, kMlpTmemCols);
+        if (t < 32) tc::tmem_dealloc(sm.tmem_base, kCols);
         return;
     }
     __syncthreads();  // every MLP tile consumed: the region becomes the point records
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (t < 32) tc::tmem_dealloc(sm.tmem_base, kMlpTmemCols);
+    if (t < 32) tc::tmem_dealloc(sm.tmem_base, kCols);
     // ---------------- phase 3b: thread = (element es, node a = l)
     const int32_t eid = s_elem[es];
     if (eid < 0) return;
@@ -327,13 +331,14 @@ jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, doub
         }
         return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);
     }
-    if (jetsci_status st = kernel_attrs_once<k_elem_surrogate<false>>(smem, false)) return st;
+    // residual only: the forward pass needs the tile's first kMlpFwdSmem bytes (five CTAs per SM)
+    if (jetsci_status st = kernel_attrs_once<k_elem_surrogate<false>>(kMlpFwdSmem, false)) return st;
     if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     for_each_colour(m, [&](const int32_t *elems, int64_t n) {
         A.elems = elems;
         A.n = n;
         unsigned grid = (unsigned)((A.n + 15) / 16);
-        k_elem_surrogate<false><<<grid, 128, smem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
+        k_elem_surrogate<false><<<grid, 128, kMlpFwdSmem, s>>>(A, u, surrogate_image(sg), surrogate_params(sg), cfg,
                                                         nullptr, R);
     });
     JETSCI_CUDA_TRY(cudaGetLastError());

@@ -12,6 +12,8 @@
 // TMEM).
 #pragma once
 
+#include <cstddef>
+
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -55,20 +57,23 @@ __device__ __forceinline__ void silu_and_prime(float z, float &a, float &ds) {
 // Shared-memory workspace of one 128-point tile for the forward + input-Jacobian pass.  The
 // six Jacobian directions run in two rounds of three (the forward pass is recomputed in the
 // second round), so a tile needs 256 TMEM columns and about 91 KB of shared memory and two
-// CTAs fit on one SM.
+// CTAs fit on one SM.  The forward pass alone (the residual) uses everything before `tan`
+// (kMlpFwdSmem, about 43 KB) and 64 TMEM columns, so five CTAs fit.
 constexpr int kMlpTmemCols = 256;
+constexpr int kMlpFwdTmemCols = 64;
 
 struct __align__(128) MlpTileSmem {
     unsigned char w[kImgFwdBytes];       // W1p, W2, W3, W4p
-    unsigned char x[128 * 16 * 2];       // inputs [128][16]
-    unsigned char act[128 * 64 * 2];     // activations [128][64]
-    unsigned char tan[3][128 * 64 * 2];  // tangent rows of the round's three directions
     float b[3][64];
     float b4[8];
     float w1t[8][64];                    // FP32 W1 transposed (tangent seeds), [input][unit]
     uint64_t mbar;
     uint32_t tmem_base;
+    alignas(128) unsigned char x[128 * 16 * 2];  // inputs [128][16]; x, act and tan are contiguous
+    unsigned char act[128 * 64 * 2];             // activations [128][64]
+    unsigned char tan[3][128 * 64 * 2];          // tangent rows of the round's three directions
 };
+constexpr size_t kMlpFwdSmem = offsetof(MlpTileSmem, tan);
 
 // Cooperative load of the forward weights into shared memory (all 128 threads).
 __device__ __forceinline__ void mlp_load_weights(MlpTileSmem &sm, const unsigned char *__restrict__ img,
@@ -127,6 +132,41 @@ __device__ __forceinline__ void smem_to_tensor_sync() {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+}
+
+// Forward pass only (the residual needs S, not dS/dE) for the tile whose inputs are already in
+// sm.x: on return thread t holds y[6] (normalised outputs).  Returns false if a tensor-core wait
+// timed out.
+__device__ inline bool mlp_forward(MlpTileSmem &sm, uint32_t &phase, float y[6]) {
+    const int t = threadIdx.x;
+    const uint32_t tm = sm.tmem_base;
+    smem_to_tensor_sync();
+    if (t == 0) tc::gemm_bf16_128xN(tm, sm.x, sm.w + kImgW1, 64, 16);
+    bool ok = mma_sync_bounded(&sm.mbar, phase);
+#pragma unroll 1
+    for (int layer = 0; layer < 3; layer++) {
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float z[16], a[16], bias[16];
+            tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
+            ld_f32x16(&sm.b[layer][c0], bias);
+#pragma unroll
+            for (int j = 0; j < 16; j++) a[j] = silu_f(z[j] + bias[j]);
+            st_bf16x8(sm.act, t, c0 / 8, 64, a);
+            st_bf16x8(sm.act, t, c0 / 8 + 1, 64, a + 8);
+        }
+        smem_to_tensor_sync();
+        if (t == 0) {
+            const unsigned char *W = sm.w + (layer == 0 ? kImgW2 : layer == 1 ? kImgW3 : kImgW4);
+            tc::gemm_bf16_128xN(tm, sm.act, W, layer < 2 ? 64 : 16, 64);
+        }
+        ok = mma_sync_bounded(&sm.mbar, phase) && ok;
+    }
+    float v[16];
+    tc::tmem_ld16(tc::tmem_lane_addr(tm, 0), v);
+#pragma unroll
+    for (int c = 0; c < 6; c++) y[c] = v[c] + sm.b4[c];
+    return ok;
 }
 
 // Runs the forward and input-Jacobian pass for the tile whose inputs are already in sm.x
