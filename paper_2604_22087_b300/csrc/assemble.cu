@@ -15,6 +15,7 @@ namespace jetsci {
 struct ElemArgs {
     const int32_t *__restrict__ conn;
     const double *__restrict__ coords;
+    const double *__restrict__ geom;    // per-element reference geometry (read by the FP64 kernels)
     const int32_t *__restrict__ phase;
     const Material *__restrict__ mats;
     const double *__restrict__ E_elem;
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     int32_t node;
     GaussKinematics<T> K;
     T cu[3];
-    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
     T Q[3][3];
     const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q);
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         int32_t node;
         GaussKinematics<T> K;
         T cu[3];
-        gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+        gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
         const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
         // Per law: W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau of the geometric term,
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
     int32_t node;
     GaussKinematics<T> K;
     T cu[3];
-    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
     const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
     T Dv[3][3];
@@ -612,16 +613,18 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
 #pragma unroll
             for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * aj[0][k] + Dv[i][1] * aj[1][k] + Dv[i][2] * aj[2][k];
         const T ltr = lam * (hp[0][0] + hp[1][1] + hp[2][2]);
-        // A0 = adj(Jp) adj(Jp)^T (symmetric)
+        // A0 = adj(Jp) adj(Jp)^T (symmetric; read from the geometry cache for FP64)
         T A0[3][3];
+        if constexpr (std::is_same<T, double>::value) {
+            const double *p = geom_point(A.geom, e, l);
+            constexpr int kIdx[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
 #pragma unroll
-        for (int n = 0; n < 3; n++)
+            for (int n = 0; n < 3; n++)
 #pragma unroll
-            for (int d = n; d < 3; d++) {
-                const T t = K.aJ[n][0] * K.aJ[d][0] + K.aJ[n][1] * K.aJ[d][1] + K.aJ[n][2] * K.aJ[d][2];
-                A0[n][d] = t;
-                A0[d][n] = t;
-            }
+                for (int d = 0; d < 3; d++) A0[n][d] = p[8 * (kGeomA0 + kIdx[n][d])];
+        } else {
+            adj_gram(K.aJ, A0);
+        }
         const T s1 = mu * rdJ, s2 = K.dJ * rdj * rdj;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
@@ -660,7 +663,7 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
     int32_t node;
     GaussKinematics<T> K;
     T cu[3];
-    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu);
+    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, true);
     T Q[3][3];
     const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q);
@@ -677,6 +680,47 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
     }
 }
 
+// ---------------------------------------------------------------------------- geometry cache
+// Fills the mesh's per-element reference geometry (element.cuh) with the same arithmetic the
+// kernels use when they form it from the coordinates.
+__global__ void __launch_bounds__(128) k_fill_geom(const int32_t *__restrict__ conn, const double *__restrict__ coords,
+                                                   int64_t n, double *__restrict__ geom) {
+    const int l = threadIdx.x & 7;
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool active = slot < n;
+    const int64_t e = active ? slot : n - 1;
+    int32_t node;
+    GaussKinematics<double> K;
+    double cu[3];
+    gauss_kinematics_coords<double>(conn, coords, nullptr, e, l, node, K, cu);
+    double A0[3][3];
+    adj_gram(K.aJ, A0);
+    if (!active) return;
+    double *p = geom + (int64_t)kGeomFields * 8 * e + l;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            p[8 * (kGeomJp + 3 * i + j)] = K.Jp[i][j];
+            p[8 * (kGeomAJ + 3 * i + j)] = K.aJ[i][j];
+        }
+    p[8 * kGeomDJ] = K.dJ;
+    p[8 * (kGeomA0 + 0)] = A0[0][0];
+    p[8 * (kGeomA0 + 1)] = A0[1][1];
+    p[8 * (kGeomA0 + 2)] = A0[2][2];
+    p[8 * (kGeomA0 + 3)] = A0[1][2];
+    p[8 * (kGeomA0 + 4)] = A0[0][2];
+    p[8 * (kGeomA0 + 5)] = A0[0][1];
+}
+
+jetsci_status launch_fill_geom(jetsci_mesh m, cudaStream_t s) {
+    if (m->n_elem == 0) return JETSCI_OK;
+    const unsigned grid = (unsigned)((8 * m->n_elem + 127) / 128);
+    k_fill_geom<<<grid, 128, 0, s>>>(m->d_conn, m->d_coords, m->n_elem, m->d_geom);
+    JETSCI_CUDA_TRY(cudaGetLastError());
+    return JETSCI_OK;
+}
+
 // ---------------------------------------------------------------------------- block insertion
 // Caller blocks Ke[e][24][24] go through the row pass of the row-gather assembly: each CSR row
 // is the element-ordered sum of its blocks, written once (no clearing, no colouring).
@@ -691,6 +735,7 @@ static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
     ElemArgs A;
     A.conn = m->d_conn;
     A.coords = m->d_coords;
+    A.geom = m->d_geom;
     A.phase = m->d_phase;
     A.mats = m->d_mats;
     A.E_elem = E_elem;

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
     int32_t node;
     GaussKinematics<float> K;
     float cu[3];
-    gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
+    gauss_kinematics_coords<float>(A.conn, A.coords, u, e, l, node, K, cu);
     const int ph = A.phase[e];
     const Material mt = A.mats[ph];
     float H[3][3], F[3][3];

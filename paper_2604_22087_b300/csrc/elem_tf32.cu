@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         int32_t node;
         GaussKinematics<float> K;
         float cu[3];
-        gauss_kinematics<float>(A.conn, A.coords, u, e, l, node, K, cu);
+        gauss_kinematics_coords<float>(A.conn, A.coords, u, e, l, node, K, cu);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
         const float lam = (float)mt.lam, mu = (float)mt.mu;
         // W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau, m, and the residual moment Q

@@ -17,6 +17,8 @@
 // turns per-Gauss-point stress moments back into nodal forces.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -239,13 +241,24 @@ struct GaussKinematics {
     T Du[3][3];  // 8 du/dxi
 };
 
+// Reference geometry of an element at its 8 Gauss points, kept per mesh for the FP64 kernels
+// (FP64 arithmetic is the scarce resource on this GPU, HBM bandwidth is not): Jp (9), adj(Jp)
+// (9), det Jp (1) and A0 = adj(Jp) adj(Jp)^T (6: 00 11 22 12 02 01), as
+// [element][field][Gauss point] doubles, so that an element's 8 lanes read 64 contiguous
+// bytes per field.
+constexpr int kGeomJp = 0, kGeomAJ = 9, kGeomDJ = 18, kGeomA0 = 19, kGeomFields = 25;
+
+__device__ __forceinline__ const double *geom_point(const double *__restrict__ geom, int64_t e, int l) {
+    return geom + (int64_t)kGeomFields * 8 * e + l;
+}
+
 // Gathers coordinates and one nodal field for element e, forms coefficients (FP64) and the
 // kinematics at the lane's Gauss point.  `node` receives the global node of the lane.
 template <typename T>
-__device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ conn,
-                                                 const double *__restrict__ coords,
-                                                 const double *__restrict__ u, int64_t e, int l,
-                                                 int32_t &node, GaussKinematics<T> &K, T cu[3]) {
+__device__ __forceinline__ void gauss_kinematics_coords(const int32_t *__restrict__ conn,
+                                                        const double *__restrict__ coords,
+                                                        const double *__restrict__ u, int64_t e, int l,
+                                                        int32_t &node, GaussKinematics<T> &K, T cu[3]) {
     node = conn[8 * e + hex_node_of_lane(l)];
     double X[3], U[3];
 #pragma unroll
@@ -270,6 +283,54 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
     }
     adj3(K.Jp, K.aJ);
     K.dJ = K.Jp[0][0] * K.aJ[0][0] + K.Jp[0][1] * K.aJ[1][0] + K.Jp[0][2] * K.aJ[2][0];
+}
+
+// The kinematics of gauss_kinematics_coords.  FP64 elements read Jp, adj(Jp) and det Jp from
+// the mesh's geometry cache `geom` (filled by gauss_kinematics_coords, so the values are the
+// same) and gather only the nodal field; FP32 and two-float elements form them from the
+// coordinates (geom is not used).
+template <typename T>
+__device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ conn,
+                                                 const double *__restrict__ coords,
+                                                 const double *__restrict__ u, int64_t e, int l,
+                                                 int32_t &node, GaussKinematics<T> &K, T cu[3],
+                                                 const double *__restrict__ geom) {
+    if constexpr (std::is_same<T, double>::value) {
+        node = conn[8 * e + hex_node_of_lane(l)];
+        const T g = 0.57735026918962576451;
+        K.xi = (l & 1) ? g : -g;
+        K.eta = (l & 2) ? g : -g;
+        K.zeta = (l & 4) ? g : -g;
+        const double *p = geom_point(geom, e, l);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const double Ui = u ? u[3 * (int64_t)node + i] : 0.0;
+            cu[i] = monomial_coeff<T>(Ui, l);
+            ref_gradient(cu[i], K.xi, K.eta, K.zeta, K.Du[i]);
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                K.Jp[i][j] = p[8 * (kGeomJp + 3 * i + j)];
+                K.aJ[i][j] = p[8 * (kGeomAJ + 3 * i + j)];
+            }
+        }
+        K.dJ = p[8 * kGeomDJ];
+    } else {
+        (void)geom;
+        gauss_kinematics_coords<T>(conn, coords, u, e, l, node, K, cu);
+    }
+}
+
+// A0 = adj(Jp) adj(Jp)^T of the matrix-free neo-Hookean product (symmetric).
+template <typename T>
+__device__ __forceinline__ void adj_gram(const T aJ[3][3], T A0[3][3]) {
+#pragma unroll
+    for (int n = 0; n < 3; n++)
+#pragma unroll
+        for (int d = n; d < 3; d++) {
+            const T t = aJ[n][0] * aJ[d][0] + aJ[n][1] * aJ[d][1] + aJ[n][2] * aJ[d][2];
+            A0[n][d] = t;
+            A0[d][n] = t;
+        }
 }
 
 // Displacement gradient H = grad_X u = (8 du/dxi) Jp^-1 at the lane's Gauss point.

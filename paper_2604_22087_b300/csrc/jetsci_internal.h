@@ -39,6 +39,8 @@ struct jetsci_mesh_s {
 
     int32_t *d_conn = nullptr;          // [n_elem*8]
     double *d_coords = nullptr;         // [n_nodes*3]
+    double *d_geom = nullptr;           // [n_elem][25][8]: reference geometry at the Gauss points
+                                        // (element.cuh, kGeom*), read by the FP64 kernels
     int32_t *d_phase = nullptr;         // [n_elem]
     int64_t *d_rowptr = nullptr;        // [n_dof+1]
     int32_t *d_col = nullptr;           // [nnz]
@@ -131,6 +133,8 @@ jetsci_status ensure_block_workspace(jetsci_mesh m, size_t values_bytes, cudaStr
 template <typename VT>
 jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, const double *Re, VT *vals, double *R,
                                  cudaStream_t s);
+// Fills m->d_geom (element.cuh, kGeom*) from the connectivity and coordinates.
+jetsci_status launch_fill_geom(jetsci_mesh m, cudaStream_t s);
 jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
                                    const double *R, double *g, int precision, cudaStream_t s);
 

@@ -122,6 +122,7 @@ static void free_mesh(jetsci_mesh m) {
     if (!m) return;
     cudaFree(m->d_conn);
     cudaFree(m->d_coords);
+    cudaFree(m->d_geom);
     cudaFree(m->d_phase);
     cudaFree(m->d_rowptr);
     cudaFree(m->d_col);
@@ -265,6 +266,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     jetsci_status st;
     if ((st = dev_alloc(&m->d_conn, 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_coords, 3 * n_nodes))) return st;
+    if ((st = dev_alloc(&m->d_geom, (size_t)25 * 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_phase, n_elem))) return st;
     if ((st = dev_alloc(&m->d_rowptr, m->n_dof + 1))) return st;
     if ((st = dev_alloc(&m->d_col, m->nnz))) return st;
@@ -329,6 +331,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
         k_block_min_colour<<<g8, 256, 0, s>>>(n_elem, m->d_conn, d_nbr_ptr, m->d_slot, d_colour, d_block_min);
         k_first_writer<<<g8, 256, 0, s>>>(n_elem, m->d_conn, d_nbr_ptr, m->d_slot, d_colour, d_block_min,
                                           m->d_first);
+        if (jetsci_status gs = launch_fill_geom(m, s)) { cleanup_tmp(); return gs; }
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
