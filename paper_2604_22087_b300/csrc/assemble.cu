@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         int32_t node;
         GaussKinematics<T> K;
         T cu[3];
-        gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
+        gauss_kinematics<T, false>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
         const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
         // Per law: W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau of the geometric term,
@@ -617,11 +617,12 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
         T A0[3][3];
         if constexpr (std::is_same<T, double>::value) {
             const double *p = geom_point(A.geom, e, l);
-            constexpr int kIdx[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
-#pragma unroll
-            for (int n = 0; n < 3; n++)
-#pragma unroll
-                for (int d = 0; d < 3; d++) A0[n][d] = p[8 * (kGeomA0 + kIdx[n][d])];
+            const double2 a01 = geom_pair(p, kGeomA0 / 2), a23 = geom_pair(p, kGeomA0 / 2 + 1),
+                          a45 = geom_pair(p, kGeomA0 / 2 + 2);  // 00 11 | 22 12 | 02 01
+            A0[0][0] = a01.x, A0[1][1] = a01.y, A0[2][2] = a23.x;
+            A0[1][2] = A0[2][1] = a23.y;
+            A0[0][2] = A0[2][0] = a45.x;
+            A0[0][1] = A0[1][0] = a45.y;
         } else {
             adj_gram(K.aJ, A0);
         }
@@ -696,21 +697,22 @@ __global__ void __launch_bounds__(128) k_fill_geom(const int32_t *__restrict__ c
     double A0[3][3];
     adj_gram(K.aJ, A0);
     if (!active) return;
-    double *p = geom + (int64_t)kGeomFields * 8 * e + l;
+    double *p = geom + (int64_t)kGeomFields * 8 * e + 2 * l;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            p[8 * (kGeomJp + 3 * i + j)] = K.Jp[i][j];
-            p[8 * (kGeomAJ + 3 * i + j)] = K.aJ[i][j];
+            *geom_field(p, kGeomJp + 3 * i + j) = K.Jp[i][j];
+            *geom_field(p, kGeomAJ + 3 * i + j) = K.aJ[i][j];
         }
-    p[8 * kGeomDJ] = K.dJ;
-    p[8 * (kGeomA0 + 0)] = A0[0][0];
-    p[8 * (kGeomA0 + 1)] = A0[1][1];
-    p[8 * (kGeomA0 + 2)] = A0[2][2];
-    p[8 * (kGeomA0 + 3)] = A0[1][2];
-    p[8 * (kGeomA0 + 4)] = A0[0][2];
-    p[8 * (kGeomA0 + 5)] = A0[0][1];
+    *geom_field(p, kGeomDJ) = K.dJ;
+    *geom_field(p, kGeomDJ + 1) = 0.0;
+    *geom_field(p, kGeomA0 + 0) = A0[0][0];
+    *geom_field(p, kGeomA0 + 1) = A0[1][1];
+    *geom_field(p, kGeomA0 + 2) = A0[2][2];
+    *geom_field(p, kGeomA0 + 3) = A0[1][2];
+    *geom_field(p, kGeomA0 + 4) = A0[0][2];
+    *geom_field(p, kGeomA0 + 5) = A0[0][1];
 }
 
 jetsci_status launch_fill_geom(jetsci_mesh m, cudaStream_t s) {

@@ -242,14 +242,21 @@ struct GaussKinematics {
 };
 
 // Reference geometry of an element at its 8 Gauss points, kept per mesh for the FP64 kernels
-// (FP64 arithmetic is the scarce resource on this GPU, HBM bandwidth is not): Jp (9), adj(Jp)
-// (9), det Jp (1) and A0 = adj(Jp) adj(Jp)^T (6: 00 11 22 12 02 01), as
-// [element][field][Gauss point] doubles, so that an element's 8 lanes read 64 contiguous
-// bytes per field.
-constexpr int kGeomJp = 0, kGeomAJ = 9, kGeomDJ = 18, kGeomA0 = 19, kGeomFields = 25;
+// (FP64 arithmetic is the scarce resource on this GPU, HBM bandwidth is not): fields Jp (0-8),
+// adj(Jp) (9-17), det Jp (18), an unused slot (19) and A0 = adj(Jp) adj(Jp)^T (20-25: 00 11 22
+// 12 02 01), stored in pairs as [element][field / 2][Gauss point][2] doubles, so that a lane
+// reads two fields with one 16-byte load and an element's 8 lanes read 128 contiguous bytes.
+constexpr int kGeomJp = 0, kGeomAJ = 9, kGeomDJ = 18, kGeomA0 = 20, kGeomFields = 26;
+constexpr int kGeomKinPairs = 10;  // pairs holding Jp, adj(Jp) and det Jp
 
 __device__ __forceinline__ const double *geom_point(const double *__restrict__ geom, int64_t e, int l) {
-    return geom + (int64_t)kGeomFields * 8 * e + l;
+    return geom + (int64_t)kGeomFields * 8 * e + 2 * l;
+}
+// field f of the lane's Gauss point (p from geom_point)
+__device__ __forceinline__ double *geom_field(double *p, int f) { return p + 16 * (f >> 1) + (f & 1); }
+// fields 2k and 2k + 1
+__device__ __forceinline__ double2 geom_pair(const double *__restrict__ p, int k) {
+    return __ldg(reinterpret_cast<const double2 *>(p + 16 * k));
 }
 
 // Gathers coordinates and one nodal field for element e, forms coefficients (FP64) and the
@@ -288,8 +295,9 @@ __device__ __forceinline__ void gauss_kinematics_coords(const int32_t *__restric
 // The kinematics of gauss_kinematics_coords.  FP64 elements read Jp, adj(Jp) and det Jp from
 // the mesh's geometry cache `geom` (filled by gauss_kinematics_coords, so the values are the
 // same) and gather only the nodal field; FP32 and two-float elements form them from the
-// coordinates (geom is not used).
-template <typename T>
+// coordinates (geom is not used).  kPairs: 16-byte loads of two fields (fewer load
+// instructions) or 8-byte loads of one (fewer live registers, for the register-bound tangent).
+template <typename T, bool kPairs = true>
 __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ conn,
                                                  const double *__restrict__ coords,
                                                  const double *__restrict__ u, int64_t e, int l,
@@ -302,18 +310,37 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
         K.eta = (l & 2) ? g : -g;
         K.zeta = (l & 4) ? g : -g;
         const double *p = geom_point(geom, e, l);
+        if constexpr (kPairs) {
+            double gf[2 * kGeomKinPairs];
+#pragma unroll
+            for (int k = 0; k < kGeomKinPairs; k++) {
+                const double2 v = geom_pair(p, k);
+                gf[2 * k] = v.x;
+                gf[2 * k + 1] = v.y;
+            }
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    K.Jp[i][j] = gf[kGeomJp + 3 * i + j];
+                    K.aJ[i][j] = gf[kGeomAJ + 3 * i + j];
+                }
+            K.dJ = gf[kGeomDJ];
+        }
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             const double Ui = u ? u[3 * (int64_t)node + i] : 0.0;
             cu[i] = monomial_coeff<T>(Ui, l);
             ref_gradient(cu[i], K.xi, K.eta, K.zeta, K.Du[i]);
+            if constexpr (!kPairs)
 #pragma unroll
-            for (int j = 0; j < 3; j++) {
-                K.Jp[i][j] = p[8 * (kGeomJp + 3 * i + j)];
-                K.aJ[i][j] = p[8 * (kGeomAJ + 3 * i + j)];
-            }
+                for (int j = 0; j < 3; j++) {
+                    const int fj = kGeomJp + 3 * i + j, fa = kGeomAJ + 3 * i + j;
+                    K.Jp[i][j] = p[16 * (fj >> 1) + (fj & 1)];
+                    K.aJ[i][j] = p[16 * (fa >> 1) + (fa & 1)];
+                }
         }
-        K.dJ = p[8 * kGeomDJ];
+        if constexpr (!kPairs) K.dJ = p[16 * (kGeomDJ >> 1) + (kGeomDJ & 1)];
     } else {
         (void)geom;
         gauss_kinematics_coords<T>(conn, coords, u, e, l, node, K, cu);

@@ -39,7 +39,7 @@ struct jetsci_mesh_s {
 
     int32_t *d_conn = nullptr;          // [n_elem*8]
     double *d_coords = nullptr;         // [n_nodes*3]
-    double *d_geom = nullptr;           // [n_elem][25][8]: reference geometry at the Gauss points
+    double *d_geom = nullptr;           // [n_elem][13][8][2]: reference geometry at the Gauss points
                                         // (element.cuh, kGeom*), read by the FP64 kernels
     int32_t *d_phase = nullptr;         // [n_elem]
     int64_t *d_rowptr = nullptr;        // [n_dof+1]

@@ -266,7 +266,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     jetsci_status st;
     if ((st = dev_alloc(&m->d_conn, 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_coords, 3 * n_nodes))) return st;
-    if ((st = dev_alloc(&m->d_geom, (size_t)25 * 8 * n_elem))) return st;
+    if ((st = dev_alloc(&m->d_geom, (size_t)26 * 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_phase, n_elem))) return st;
     if ((st = dev_alloc(&m->d_rowptr, m->n_dof + 1))) return st;
     if ((st = dev_alloc(&m->d_col, m->nnz))) return st;
