@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         int32_t node;
         GaussKinematics<T> K;
         T cu[3];
-        gauss_kinematics<T, false>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
+        gauss_kinematics<T, false, false>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
         const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
         // Per law: W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau of the geometric term,
@@ -613,16 +613,16 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
 #pragma unroll
             for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * aj[0][k] + Dv[i][1] * aj[1][k] + Dv[i][2] * aj[2][k];
         const T ltr = lam * (hp[0][0] + hp[1][1] + hp[2][2]);
-        // A0 = adj(Jp) adj(Jp)^T (symmetric; read from the geometry cache for FP64)
+        // A0 = adj(Jp) adj(Jp)^T (symmetric; read from the geometry cache for FP64 and two-float)
         T A0[3][3];
-        if constexpr (std::is_same<T, double>::value) {
+        if constexpr (std::is_same<T, double>::value || std::is_same<T, df64>::value) {
             const double *p = geom_point(A.geom, e, l);
             const double2 a01 = geom_pair(p, kGeomA0 / 2), a23 = geom_pair(p, kGeomA0 / 2 + 1),
                           a45 = geom_pair(p, kGeomA0 / 2 + 2);  // 00 11 | 22 12 | 02 01
-            A0[0][0] = a01.x, A0[1][1] = a01.y, A0[2][2] = a23.x;
-            A0[1][2] = A0[2][1] = a23.y;
-            A0[0][2] = A0[2][0] = a45.x;
-            A0[0][1] = A0[1][0] = a45.y;
+            A0[0][0] = from_double<T>(a01.x), A0[1][1] = from_double<T>(a01.y), A0[2][2] = from_double<T>(a23.x);
+            A0[1][2] = A0[2][1] = from_double<T>(a23.y);
+            A0[0][2] = A0[2][0] = from_double<T>(a45.x);
+            A0[0][1] = A0[1][0] = from_double<T>(a45.y);
         } else {
             adj_gram(K.aJ, A0);
         }

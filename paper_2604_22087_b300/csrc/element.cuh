@@ -292,20 +292,23 @@ __device__ __forceinline__ void gauss_kinematics_coords(const int32_t *__restric
     K.dJ = K.Jp[0][0] * K.aJ[0][0] + K.Jp[0][1] * K.aJ[1][0] + K.Jp[0][2] * K.aJ[2][0];
 }
 
-// The kinematics of gauss_kinematics_coords.  FP64 elements read Jp, adj(Jp) and det Jp from
-// the mesh's geometry cache `geom` (filled by gauss_kinematics_coords, so the values are the
-// same) and gather only the nodal field; FP32 and two-float elements form them from the
+// The kinematics of gauss_kinematics_coords.  FP64 and two-float elements read Jp, adj(Jp) and
+// det Jp from the mesh's geometry cache `geom` (FP64, filled by gauss_kinematics_coords: the
+// same values for FP64; two-float elements split them, keeping the ~48 bits their own
+// arithmetic would have) and gather only the nodal field; FP32 elements form them from the
 // coordinates (geom is not used).  kPairs: 16-byte loads of two fields (fewer load
 // instructions) or 8-byte loads of one (fewer live registers, for the register-bound tangent).
-template <typename T, bool kPairs = true>
+// kCachedDf64 = false: two-float elements form the geometry from the coordinates as well (the
+// issue-bound two-float tangent was 1.3% slower reading the cache).
+template <typename T, bool kPairs = true, bool kCachedDf64 = true>
 __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ conn,
                                                  const double *__restrict__ coords,
                                                  const double *__restrict__ u, int64_t e, int l,
                                                  int32_t &node, GaussKinematics<T> &K, T cu[3],
                                                  const double *__restrict__ geom) {
-    if constexpr (std::is_same<T, double>::value) {
+    if constexpr (std::is_same<T, double>::value || (kCachedDf64 && std::is_same<T, df64>::value)) {
         node = conn[8 * e + hex_node_of_lane(l)];
-        const T g = 0.57735026918962576451;
+        const T g = (T)0.57735026918962576451;
         K.xi = (l & 1) ? g : -g;
         K.eta = (l & 2) ? g : -g;
         K.zeta = (l & 4) ? g : -g;
@@ -322,10 +325,10 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    K.Jp[i][j] = gf[kGeomJp + 3 * i + j];
-                    K.aJ[i][j] = gf[kGeomAJ + 3 * i + j];
+                    K.Jp[i][j] = from_double<T>(gf[kGeomJp + 3 * i + j]);
+                    K.aJ[i][j] = from_double<T>(gf[kGeomAJ + 3 * i + j]);
                 }
-            K.dJ = gf[kGeomDJ];
+            K.dJ = from_double<T>(gf[kGeomDJ]);
         }
 #pragma unroll
         for (int i = 0; i < 3; i++) {
@@ -336,11 +339,11 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     const int fj = kGeomJp + 3 * i + j, fa = kGeomAJ + 3 * i + j;
-                    K.Jp[i][j] = p[16 * (fj >> 1) + (fj & 1)];
-                    K.aJ[i][j] = p[16 * (fa >> 1) + (fa & 1)];
+                    K.Jp[i][j] = from_double<T>(p[16 * (fj >> 1) + (fj & 1)]);
+                    K.aJ[i][j] = from_double<T>(p[16 * (fa >> 1) + (fa & 1)]);
                 }
         }
-        if constexpr (!kPairs) K.dJ = p[16 * (kGeomDJ >> 1) + (kGeomDJ & 1)];
+        if constexpr (!kPairs) K.dJ = from_double<T>(p[16 * (kGeomDJ >> 1) + (kGeomDJ & 1)]);
     } else {
         (void)geom;
         gauss_kinematics_coords<T>(conn, coords, u, e, l, node, K, cu);
