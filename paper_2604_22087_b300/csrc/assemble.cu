@@ -405,17 +405,23 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                         const T lam = cf[0], m = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
                         l0 = lam * a0, l1 = lam * a1, l2 = lam * a2, m0 = m * a0, m1 = m * a1, m2 = m * a2;
                     }
-                    gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
-                    Kab[0][0] = fma_t(l0, b0, fma_t(m0, b0, Kab[0][0]));
-                    Kab[0][1] = fma_t(l0, b1, fma_t(m1, b0, Kab[0][1]));
-                    Kab[0][2] = fma_t(l0, b2, fma_t(m2, b0, Kab[0][2]));
-                    Kab[1][0] = fma_t(l1, b0, fma_t(m0, b1, Kab[1][0]));
-                    Kab[1][1] = fma_t(l1, b1, fma_t(m1, b1, Kab[1][1]));
-                    Kab[1][2] = fma_t(l1, b2, fma_t(m2, b1, Kab[1][2]));
-                    Kab[2][0] = fma_t(l2, b0, fma_t(m0, b2, Kab[2][0]));
-                    Kab[2][1] = fma_t(l2, b1, fma_t(m1, b2, Kab[2][1]));
-                    Kab[2][2] = fma_t(l2, b2, fma_t(m2, b2, Kab[2][2]));
+                    gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
+                    Kab[0][0] = acc_t(l0, b0, acc_t(m0, b0, Kab[0][0]));
+                    Kab[0][1] = acc_t(l0, b1, acc_t(m1, b0, Kab[0][1]));
+                    Kab[0][2] = acc_t(l0, b2, acc_t(m2, b0, Kab[0][2]));
+                    Kab[1][0] = acc_t(l1, b0, acc_t(m0, b1, Kab[1][0]));
+                    Kab[1][1] = acc_t(l1, b1, acc_t(m1, b1, Kab[1][1]));
+                    Kab[1][2] = acc_t(l1, b2, acc_t(m2, b1, Kab[1][2]));
+                    Kab[2][0] = acc_t(l2, b0, acc_t(m0, b2, Kab[2][0]));
+                    Kab[2][1] = acc_t(l2, b1, acc_t(m1, b2, Kab[2][1]));
+                    Kab[2][2] = acc_t(l2, b2, acc_t(m2, b2, Kab[2][2]));
                 }
+                // (two-float running sums are normalised once, here)
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) Kab[i][k] = acc_norm(Kab[i][k]);
+                gs = acc_norm(gs);
                 Kab[0][0] += gs;
                 Kab[1][1] += gs;
                 Kab[2][2] += gs;
@@ -457,19 +463,23 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                         const T lm = cf[0] + cf[1];
                         s0 = lm * b0, s1 = lm * b1, s2 = lm * b2;
                     }
-                    gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
-                    k00 = fma_t(s0, b0, k00);
-                    k11 = fma_t(s1, b1, k11);
-                    k22 = fma_t(s2, b2, k22);
-                    k12 = fma_t(s1, b2, k12);
-                    k02 = fma_t(s0, b2, k02);
-                    k01 = fma_t(s0, b1, k01);
+                    gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
+                    k00 = acc_t(s0, b0, k00);
+                    k11 = acc_t(s1, b1, k11);
+                    k22 = acc_t(s2, b2, k22);
+                    k12 = acc_t(s1, b2, k12);
+                    k02 = acc_t(s0, b2, k02);
+                    k01 = acc_t(s0, b1, k01);
                     if (R) {
-                        Ra0 = fma_t(cf[2], b0, fma_t(cf[7], b1, fma_t(cf[6], b2, Ra0)));
-                        Ra1 = fma_t(cf[7], b0, fma_t(cf[3], b1, fma_t(cf[5], b2, Ra1)));
-                        Ra2 = fma_t(cf[6], b0, fma_t(cf[5], b1, fma_t(cf[4], b2, Ra2)));
+                        Ra0 = acc_t(cf[2], b0, acc_t(cf[7], b1, acc_t(cf[6], b2, Ra0)));
+                        Ra1 = acc_t(cf[7], b0, acc_t(cf[3], b1, acc_t(cf[5], b2, Ra1)));
+                        Ra2 = acc_t(cf[6], b0, acc_t(cf[5], b1, acc_t(cf[4], b2, Ra2)));
                     }
                 }
+                k00 = acc_norm(k00), k11 = acc_norm(k11), k22 = acc_norm(k22);
+                k12 = acc_norm(k12), k02 = acc_norm(k02), k01 = acc_norm(k01);
+                gs = acc_norm(gs);
+                Ra0 = acc_norm(Ra0), Ra1 = acc_norm(Ra1), Ra2 = acc_norm(Ra2);
                 Kab[0][0] = k00 + gs;
                 Kab[1][1] = k11 + gs;
                 Kab[2][2] = k22 + gs;

@@ -204,6 +204,14 @@ __device__ __forceinline__ df64 my_rcp<df64>(df64 x) { return df_rcp(x); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ df64 fma_t(df64 a, df64 b, df64 c) { return df_fma(a, b, c); }
+// Running-sum steps (acc_t) and their final normalisation (acc_norm): fma_t for FP64 and FP32;
+// two-float sums skip the per-step renormalisation (df64.cuh, df_fma_acc).
+__device__ __forceinline__ double acc_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float acc_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df64 acc_t(df64 a, df64 b, df64 c) { return df_fma_acc(a, b, c); }
+__device__ __forceinline__ double acc_norm(double a) { return a; }
+__device__ __forceinline__ float acc_norm(float a) { return a; }
+__device__ __forceinline__ df64 acc_norm(df64 a) { return df_acc_norm(a); }
 
 // Material of element e as (law, lambda, mu) in T.
 struct ElemMaterial {
