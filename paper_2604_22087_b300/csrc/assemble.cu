@@ -1,7 +1,10 @@
 // Element kernels: residual, consistent tangent into CSR, matrix-free tangent product and
-// the material-gradient (adjoint) pass.  All scatters are coloured read-modify-writes:
+// the material-gradient (adjoint) pass.  Their scatters are coloured read-modify-writes:
 // within one colour no two elements share a node, colours run in a fixed order, so the
-// sums are race-free without atomics and bitwise reproducible.
+// sums are race-free without atomics and bitwise reproducible.  The FP32 tangent instead
+// writes element rows for the row-gather assembly (gather.cu), as do the TF32 and surrogate
+// element passes.  FP64 and two-float kernels read the mesh's reference-geometry cache
+// (element.cuh), filled here at mesh creation.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -109,9 +112,10 @@ struct TangentLayout {
     static constexpr int kCoef = 9;
     enum { kG = 0, kTG = 1, kLG = 2, kMG = 3 };
     // FP64 values: each CSR block's first writer stores and no clearing pass is needed (saves
-    // the 4 GB memset at 128^3).  FP32 and two-float were measured slower that way (the
+    // the 4 GB memset at 128^3).  The two-float kernel was measured slower that way (the
     // partial-sector first stores and the divergent store/accumulate paths cost more than the
-    // clearing pass), so they clear the array and accumulate.
+    // clearing pass), so it clears the array and accumulates; FP32 values are assembled by row
+    // gather instead of by scatter.
     static constexpr bool kFirstWrites = std::is_same<T, double>::value;
 };
 
