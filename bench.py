@@ -2,8 +2,9 @@
 
 One step = the whole hot path over one synthetic workload: consistent-tangent CSR assembly
 with the residual fused (gather, shape gradients, constitutive update, R_e and K_e, coloured
-scatter), the tangent product K.v both from the assembled CSR matrix and matrix-free, and the
-FP64 residual norm.  Workload (default): 128^3 hex8 unidirectional-fibre RVE (2,097,152
+scatter; the call also stores the neo-Hookean state per Gauss point), the tangent product K.v
+both from the assembled CSR matrix and matrix-free (at that stored linearisation, as a
+Newton-Krylov product at one iterate would be), and the FP64 residual norm.  Workload (default): 128^3 hex8 unidirectional-fibre RVE (2,097,152
 elements, 6,440,067 DOFs, 513,599,625 CSR non-zeros), compressible neo-Hookean per phase at a
 1% uniaxial stretch plus 1e-4 noise, FP64.  Metric: elements per second of that step.
 
@@ -36,14 +37,15 @@ METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % o
 
 # Work per element of the dominant kernel, k_tangent<double,double>:
 # executed FP64 operations of the formulation (ncu on the 64^3 fibre RVE: 7,400 DFMA x 2 +
-# 676 DADD + 1,456 DMUL per element) and the algorithmic bytes (write-once CSR values 1,959 +
-# slot map and masks 96 + u, R and connectivity 82 + the reference-geometry cache 1,216).
-TANGENT_FP64_FLOP_PER_ELEM = 16_932.0
-TANGENT_BYTES_PER_ELEM_FP64 = 3_353.0
+# 676 DADD + 1,464 DMUL per element) and the algorithmic bytes (write-once CSR values 1,959 +
+# slot map and masks 96 + u, R and connectivity 82 + the reference-geometry cache 1,216 + the
+# stored linearisation 768).
+TANGENT_FP64_FLOP_PER_ELEM = 16_940.0
+TANGENT_BYTES_PER_ELEM_FP64 = 4_121.0
 # DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
 # coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
-TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 13_538.0
+TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_195.0
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
 # index (a node's three rows share one column list); v and y are per-row and stay in L2.
 SPMV_BYTES_PER_NNZ = {"fp64": 8.0 + 4.0 / 3.0, "fp32": 4.0 + 4.0 / 3.0}
@@ -447,7 +449,8 @@ def main():
         if ev is not None:
             ev[1].record(stream)
         mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals, stream=stream)
-        mesh.apply_tangent(u, v, y=y, stream=stream)
+        # matrix-free K(u) v at the linearisation the tangent call just stored (same u)
+        mesh.apply_tangent(None, v, y=y, stream=stream)
         mesh.norm2(R, out=nrm, stream=stream)
 
     def barrier():
@@ -510,7 +513,7 @@ def main():
         with torch.cuda.stream(cs):
             cs.wait_event(ev_y)
             y_h.copy_(y2, non_blocking=True)
-        mesh.apply_tangent(uk, v, y=y, stream=stream)
+        mesh.apply_tangent(None, v, y=y, stream=stream)  # at the linearisation of the tangent at uk
         mesh.norm2(R, out=nrm, stream=stream)
         with torch.cuda.stream(stream):
             n_h.copy_(nrm, non_blocking=True)
@@ -601,6 +604,13 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
         ms = timeit(lambda: mesh.apply_tangent(u, v, y=y, precision=p, stream=stream), stream)
         torch.cuda.synchronize()
         rec(f"apply_matrix_free_{name}", ms, {"err_vs_oracle": so.errors(None, None, gather_rows(y, so.nodes), rp_h, col_h)})
+        if p == J.FP64:
+            # at the linearisation stored by the FP64 tangent call above (u not read again)
+            mesh.tangent_csr(u, vals=vv, R=R, precision=p, stream=stream)
+            ms = timeit(lambda: mesh.apply_tangent(None, v, y=y, precision=p, stream=stream), stream)
+            torch.cuda.synchronize()
+            rec("apply_matrix_free_fp64_stored_linearisation", ms,
+                {"err_vs_oracle": so.errors(None, None, gather_rows(y, so.nodes), rp_h, col_h)})
         if p in (J.FP64, J.FP32):
             # 100 back-to-back products on the assembled matrix (the paper's repeated-SpMV
             # comparison, Section V); ms is per product

@@ -19,6 +19,8 @@ struct ElemArgs {
     const int32_t *__restrict__ conn;
     const double *__restrict__ coords;
     const double *__restrict__ geom;    // per-element reference geometry (read by the FP64 kernels)
+    double *lin;                        // FP64 linearisation store (element.cuh, kLin*): written by
+                                        // the FP64 residual and tangent when set
     const int32_t *__restrict__ phase;
     const Material *__restrict__ mats;
     const double *__restrict__ E_elem;
@@ -61,7 +63,10 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
     T Q[3][3];
-    const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q);
+    NeoHookeanState<T> st;
+    const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q, &st);
+    if constexpr (std::is_same<T, double>::value)
+        if (A.lin && active && mt.law != JETSCI_LINEAR_ELASTIC) lin_store(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
     T f[3];
     nodal_force_of_moment(Q, K, l, f);
     if (active) {
@@ -303,6 +308,8 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             neo_hookean_state(K, lam, mu, st);
             ok = st.ok;
             m = st.m;
+            if constexpr (std::is_same<T, double>::value)
+                if (A.lin && active) lin_store(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
 #pragma unroll
             for (int d = 0; d < 3; d++)
 #pragma unroll
@@ -581,7 +588,9 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 // Q = Y adj(Jp)^T directly:
 //   Q = (mu / det Jp) Dv adj(Jp) adj(Jp)^T + (det Jp / det j^2) M' adj(j)^T,
 //   M' = m h'^T + lam tr(h') I,  h' = Dv adj(j) = det j h.
-template <typename T>
+// kReuse (FP64 only): the neo-Hookean state comes from the mesh's linearisation store (the
+// last FP64 residual or tangent, at its u) instead of u; u is not read.
+template <typename T, bool kReuse>
 __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__restrict__ u,
                                                   const double *__restrict__ v, double *__restrict__ y) {
     const int l = threadIdx.x & 7;
@@ -590,8 +599,13 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
     const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
     int32_t node;
     GaussKinematics<T> K;
-    T cu[3];
-    gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
+    if constexpr (kReuse) {
+        static_assert(std::is_same<T, double>::value, "the linearisation store is FP64");
+        gauss_geometry(A.conn, A.geom, e, l, node, K);
+    } else {
+        T cu[3];
+        gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
+    }
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
     const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
     T Dv[3][3];
@@ -616,11 +630,19 @@ __global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__re
 #pragma unroll
             for (int d = 0; d < 3; d++) Q[i][d] = Y[i][0] * K.aJ[d][0] + Y[i][1] * K.aJ[d][1] + Y[i][2] * K.aJ[d][2];
     } else {
-        NeoHookeanState<T> st;
-        neo_hookean_state(K, lam, mu, st);
-        ok = st.ok;
-        const T m = st.m, rdj = st.rdj, rdJ = st.rdJ;
-        const T(&aj)[3][3] = st.aj;
+        T m, rdj, rdJ, aj[3][3];
+        if constexpr (kReuse) {
+            lin_load(A.lin, e, l, aj, m, rdJ, rdj);  // (states outside the law were flagged when stored)
+        } else {
+            NeoHookeanState<T> st;
+            neo_hookean_state(K, lam, mu, st);
+            ok = st.ok;
+            m = st.m, rdj = st.rdj, rdJ = st.rdJ;
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) aj[i][k] = st.aj[i][k];
+        }
         T hp[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -752,6 +774,7 @@ static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
     A.conn = m->d_conn;
     A.coords = m->d_coords;
     A.geom = m->d_geom;
+    A.lin = nullptr;
     A.phase = m->d_phase;
     A.mats = m->d_mats;
     A.E_elem = E_elem;
@@ -776,8 +799,12 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
                               const double *E_elem, cudaStream_t s) {
     JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     ElemArgs A = make_args(m, E_elem);
-    if (precision == JETSCI_FP64)
+    if (precision == JETSCI_FP64) {
+        A.lin = m->d_lin;  // the linearisation at u, for matrix-free products at this state
+        m->lin_valid = true;
+        m->lin_E = E_elem;
         residual_colours<double>(m, A, u, R, s);
+    }
     else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
         residual_colours<float>(m, A, u, R, s);
     else if (precision == JETSCI_DF64)
@@ -843,6 +870,9 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
     // FP64 needs no clearing of vals (first writers store, TangentLayout::kFirstWrites).
     if (precision == JETSCI_FP64) {
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
+        A.lin = m->d_lin;  // the linearisation at u, for matrix-free products at this state
+        m->lin_valid = true;
+        m->lin_E = E_elem;
         return tangent_colours<double, double>(m, A, u, (double *)vals, R, s);
     }
     if (precision == JETSCI_FP32) return tangent_rows<float, float>(m, A, u, (float *)vals, R, s);
@@ -856,7 +886,7 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
     return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the tangent");
 }
 
-template <typename T>
+template <typename T, bool kReuse = false>
 static void apply_colours(jetsci_mesh m, ElemArgs A, const double *u, const double *v, double *y,
                           cudaStream_t s) {
     for (int c = 0; c < m->n_colours; c++) {
@@ -864,7 +894,7 @@ static void apply_colours(jetsci_mesh m, ElemArgs A, const double *u, const doub
         A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
         if (A.n == 0) continue;
         unsigned grid = (unsigned)((8 * A.n + 127) / 128);
-        k_apply_mf<T><<<grid, 128, 0, s>>>(A, u, v, y);
+        k_apply_mf<T, kReuse><<<grid, 128, 0, s>>>(A, u, v, y);
     }
 }
 
@@ -873,7 +903,10 @@ jetsci_status launch_apply_mf(jetsci_mesh m, const double *u, const double *v, d
     if (precision == JETSCI_TF32) return launch_tf32(m, u, v, nullptr, nullptr, y, E_elem, s);
     JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     ElemArgs A = make_args(m, E_elem);
-    if (precision == JETSCI_FP64)
+    if (!u) {  // at the stored FP64 linearisation (checked by the caller)
+        A.lin = m->d_lin;
+        apply_colours<double, true>(m, A, nullptr, v, y, s);
+    } else if (precision == JETSCI_FP64)
         apply_colours<double>(m, A, u, v, y, s);
     else if (precision == JETSCI_FP32)
         apply_colours<float>(m, A, u, v, y, s);

@@ -50,7 +50,15 @@ extern "C" jetsci_status jetsci_apply_tangent(jetsci_mesh m, const double *u, co
         bool fp32 = precision == JETSCI_FP32 || precision == JETSCI_TF32 || precision == JETSCI_SURROGATE;
         return launch_spmv(m, vals, fp32, v, y, s);
     }
-    if (!u) return fail(JETSCI_ERR_ARG, "u is NULL");
+    if (!u) {
+        // K(u) v at the stored linearisation of the last FP64 residual or tangent call
+        if (precision != JETSCI_FP64)
+            return fail(JETSCI_ERR_ARG, "u is NULL: a stored linearisation exists for JETSCI_FP64 only");
+        if (!m->lin_valid)
+            return fail(JETSCI_ERR_ARG, "u is NULL and no FP64 residual or tangent call has stored a linearisation");
+        if (E_elem != m->lin_E)
+            return fail(JETSCI_ERR_ARG, "u is NULL: E_elem differs from the call that stored the linearisation");
+    }
     return launch_apply_mf(m, u, v, y, precision, E_elem, s);
 }
 

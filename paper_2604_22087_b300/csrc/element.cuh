@@ -267,6 +267,39 @@ __device__ __forceinline__ double2 geom_pair(const double *__restrict__ p, int k
     return __ldg(reinterpret_cast<const double2 *>(p + 16 * k));
 }
 
+// Linearisation of the neo-Hookean state at the last FP64 residual or tangent call, kept per
+// mesh for matrix-free products at that state: adj(j) (0-8), m (9), 1 / det Jp (10) and
+// 1 / det j (11) per element and Gauss point, in pairs as [element][6][Gauss point][2] doubles.
+constexpr int kLinAj = 0, kLinM = 9, kLinRdJ = 10, kLinRdj = 11, kLinPairs = 6;
+
+__device__ __forceinline__ void lin_store(double *__restrict__ lin, int64_t e, int l, const double aj[3][3], double m,
+                                          double rdJ, double rdj) {
+    const double f[2 * kLinPairs] = {aj[0][0], aj[0][1], aj[0][2], aj[1][0], aj[1][1], aj[1][2],
+                                     aj[2][0], aj[2][1], aj[2][2], m,        rdJ,      rdj};
+    double2 *p = reinterpret_cast<double2 *>(lin + (int64_t)2 * kLinPairs * 8 * e + 2 * l);
+#pragma unroll
+    for (int k = 0; k < kLinPairs; k++) p[8 * k] = make_double2(f[2 * k], f[2 * k + 1]);
+}
+
+__device__ __forceinline__ void lin_load(const double *__restrict__ lin, int64_t e, int l, double aj[3][3], double &m,
+                                         double &rdJ, double &rdj) {
+    const double2 *p = reinterpret_cast<const double2 *>(lin + (int64_t)2 * kLinPairs * 8 * e + 2 * l);
+    double f[2 * kLinPairs];
+#pragma unroll
+    for (int k = 0; k < kLinPairs; k++) {
+        const double2 v = __ldg(p + 8 * k);
+        f[2 * k] = v.x;
+        f[2 * k + 1] = v.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) aj[i][j] = f[kLinAj + 3 * i + j];
+    m = f[kLinM];
+    rdJ = f[kLinRdJ];
+    rdj = f[kLinRdj];
+}
+
 // Gathers coordinates and one nodal field for element e, forms coefficients (FP64) and the
 // kinematics at the lane's Gauss point.  `node` receives the global node of the lane.
 template <typename T>
@@ -356,6 +389,33 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
         (void)geom;
         gauss_kinematics_coords<T>(conn, coords, u, e, l, node, K, cu);
     }
+}
+
+// The reference geometry of the lane's Gauss point alone (FP64, from the cache): node, xi,
+// eta, zeta, Jp, adj(Jp), det Jp; K.Du is not formed.
+__device__ __forceinline__ void gauss_geometry(const int32_t *__restrict__ conn, const double *__restrict__ geom,
+                                               int64_t e, int l, int32_t &node, GaussKinematics<double> &K) {
+    node = conn[8 * e + hex_node_of_lane(l)];
+    const double g = 0.57735026918962576451;
+    K.xi = (l & 1) ? g : -g;
+    K.eta = (l & 2) ? g : -g;
+    K.zeta = (l & 4) ? g : -g;
+    const double *p = geom_point(geom, e, l);
+    double gf[2 * kGeomKinPairs];
+#pragma unroll
+    for (int k = 0; k < kGeomKinPairs; k++) {
+        const double2 v = geom_pair(p, k);
+        gf[2 * k] = v.x;
+        gf[2 * k + 1] = v.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            K.Jp[i][j] = gf[kGeomJp + 3 * i + j];
+            K.aJ[i][j] = gf[kGeomAJ + 3 * i + j];
+        }
+    K.dJ = gf[kGeomDJ];
 }
 
 // A0 = adj(Jp) adj(Jp)^T of the matrix-free neo-Hookean product (symmetric).
@@ -529,7 +589,8 @@ __device__ __forceinline__ void neo_hookean_state(const GaussKinematics<T> &K, T
 // lane's Gauss point.  Linear law: P = sigma(H), H = Du Jp^-1.  Neo-Hookean: P = tau F^-T and
 // F^-T adj(Jp)^T = (det Jp / det j) adj(j)^T, so Q = (det Jp / det j) tau adj(j)^T.
 template <typename T>
-__device__ __forceinline__ bool residual_moment(const GaussKinematics<T> &K, int law, T lam, T mu, T Q[3][3]) {
+__device__ __forceinline__ bool residual_moment(const GaussKinematics<T> &K, int law, T lam, T mu, T Q[3][3],
+                                                NeoHookeanState<T> *state = nullptr) {
     if (law == JETSCI_LINEAR_ELASTIC) {
         const T rdJ = my_rcp(K.dJ);
         T H[3][3];
@@ -552,6 +613,7 @@ __device__ __forceinline__ bool residual_moment(const GaussKinematics<T> &K, int
     }
     NeoHookeanState<T> s;
     neo_hookean_state(K, lam, mu, s);
+    if (state) *state = s;
     const T sc = K.dJ * s.rdj;
     T ts[3][3];
 #pragma unroll

@@ -39,6 +39,9 @@ struct jetsci_mesh_s {
 
     int32_t *d_conn = nullptr;          // [n_elem*8]
     double *d_coords = nullptr;         // [n_nodes*3]
+    double *d_lin = nullptr;            // [n_elem][6][8][2]: FP64 neo-Hookean linearisation (element.cuh)
+    bool lin_valid = false;             // d_lin holds the state of an FP64 residual/tangent call
+    const double *lin_E = nullptr;      // ... made with this per-element modulus array (or NULL)
     double *d_geom = nullptr;           // [n_elem][13][8][2]: reference geometry at the Gauss points
                                         // (element.cuh, kGeom*), read by the FP64 kernels
     int32_t *d_phase = nullptr;         // [n_elem]

@@ -107,6 +107,48 @@ def test_apply_tangent_csr_fp64(case):
     assert relerr(y.cpu().numpy(), ref["y_csr"]) <= FP64_TOL
 
 
+def test_matrix_free_at_stored_linearisation(case):
+    """An FP64 tangent (or residual) stores the neo-Hookean state at its u; a matrix-free
+    product with u = NULL applies K at that state.  It must equal the product that forms the
+    state from u (the same arithmetic on the same values) and the oracle."""
+    prob, mesh, _, ref = case
+    J = jetsci()
+    u, v = cuda(prob.u), cuda(prob.v)
+    y_direct = mesh.apply_tangent(u, v)
+    mesh.tangent_csr(u)
+    y_lin = mesh.apply_tangent(None, v)
+    assert relerr(y_lin.cpu().numpy(), y_direct.cpu().numpy()) <= 1e-14
+    assert relerr(y_lin.cpu().numpy(), ref["y_mf"]) <= FP64_TOL
+    # a residual at another state replaces the linearisation
+    u2 = u * 0.5
+    mesh.residual(u2)
+    y2 = mesh.apply_tangent(None, v)
+    assert relerr(y2.cpu().numpy(), mesh.apply_tangent(u2, v).cpu().numpy()) <= 1e-14
+    # other precisions do not touch it
+    mesh.tangent_csr(u, precision=J.FP32)
+    assert relerr(mesh.apply_tangent(None, v).cpu().numpy(), y2.cpu().numpy()) == 0.0
+
+
+def test_matrix_free_linearisation_errors():
+    J = jetsci()
+    prob = dict(PROBLEMS)["ragged_neohookean"]
+    mesh = J.Mesh.of(prob)
+    u, v = cuda(prob.u), cuda(prob.v)
+    with pytest.raises(J.JetsciError) as ei:  # nothing stored yet
+        mesh.apply_tangent(None, v)
+    assert ei.value.status == 1
+    mesh.residual(u)
+    with pytest.raises(J.JetsciError):  # stored in FP64 only
+        mesh.apply_tangent(None, v, precision=J.FP32)
+    E = torch.full((mesh.n_elem,), 1e9, dtype=torch.float64, device="cuda")
+    with pytest.raises(J.JetsciError):  # the state belongs to the phase moduli, not to E
+        mesh.apply_tangent(None, v, E_elem=E)
+    mesh.residual(u, E_elem=E)
+    assert relerr(mesh.apply_tangent(None, v, E_elem=E).cpu().numpy(),
+                  mesh.apply_tangent(u, v, E_elem=E).cpu().numpy()) <= 1e-14
+    mesh.close()
+
+
 def test_norm2_fp64(case):
     prob, mesh, _, ref = case
     n = mesh.norm2(cuda(ref["R"])).item()
