@@ -4,8 +4,9 @@
 // K_ab = sum over the elements e holding both a and b of K_e(a, b) (the assembly of Section
 // III-B, K = sum_e P_e^T K_e P_e), summed in ascending element order, so the values are
 // deterministic and independent of launch shapes; R_a = sum_e R_e(a) likewise.  The pass needs
-// no clearing of the outputs, no atomics and no colouring: it reads each element block about
-// twice (once per node of the pair) and writes each value once, contiguously.
+// no clearing of the outputs, no atomics and no colouring: node a reads the element rows
+// 3a..3a+2 of its elements (each element row is read once, by its own node) and writes each
+// CSR value once, contiguously.
 #include <cuda_runtime.h>
 
 #include "blocks.cuh"
@@ -22,9 +23,10 @@ constexpr int kSlots = 32;      // neighbour slots per accumulation pass (more t
 constexpr int kAccStride = 12;  // accumulator values per slot (3 x 3 block, 16-byte aligned)
 
 // elements whose blocks a lane loads at once (in flight together); measured at 128^3: 2 is
-// faster than 4 and 8, whose registers cost more occupancy than the deeper prefetch gains
-template <typename VT>
-constexpr int row_chunk() { return 2; }
+// faster than 4 and 8, whose registers cost more occupancy than the deeper prefetch gains, and
+// than staging whole element rows in shared memory by asynchronous copies (2.14 and 2.59 ms
+// against 2.07 ms)
+constexpr int kChunk = 2;
 
 // Block K_e(la, lb) (rows at node la) of the rows layout [e][24][24] into y[3 i + k].
 template <typename VT>
@@ -65,7 +67,6 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_gather_rows(int64_t n_nodes,
                                                                 const VT *__restrict__ blocks,
                                                                 const double *__restrict__ Re,
                                                                 VT *__restrict__ vals, double *__restrict__ R) {
-    constexpr int kChunk = row_chunk<VT>();
     constexpr int kV16 = 16 / (int)sizeof(VT);
     __shared__ __align__(16) VT acc_s[kRowWarps * kNodesPerWarp][kSlots * kAccStride];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
