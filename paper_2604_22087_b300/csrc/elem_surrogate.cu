@@ -12,6 +12,11 @@
 // K_ab[i][k] += (F Y_i G_b)_k where Y_i is the symmetric 3x3 form of row i of B_a^T (c W D).
 // This is the consistent tangent sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL
 // with the Voigt tangent; it is not symmetric for the surrogate, so all 64 node pairs are formed.
+//
+// The tangent (TANGENT) runs over all elements in order in one launch and writes each element's
+// 24 x 24 rows and nodal forces to the row-gather workspace (gather.cu forms the CSR rows and R).
+// The residual alone runs the forward pass only (no Jacobian directions: 64 TMEM columns and the
+// forward part of the tile's shared memory, five CTAs per SM) and scatters R by colour.
 #include <cuda_runtime.h>
 
 #include "blocks.cuh"
