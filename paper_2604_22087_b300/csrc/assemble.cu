@@ -371,6 +371,9 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
     static_assert(L::kElems % kGroup == 0 && kGroupOff % 32 == 0 && kGroupItems % 32 == 0,
                   "items of one kind per warp");
     if constexpr (!kRows) {
+        // (Gauss-point loops unrolled by 2; by 1 for two-float elements, whose long unrolled
+        // arithmetic otherwise stalls on instruction fetch: 0.9% faster at 128^3)
+        constexpr int kUnrollQ = std::is_same<T, df64>::value ? 1 : 2;
         for (int it = threadIdx.x; it < L::kElems * 36; it += blockDim.x) {
             const int grp = it / kGroupItems, r = it - kGroupItems * grp;
             const bool off = r < kGroupOff;
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 #pragma unroll
                     for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
                 T gs = T(0);
-#pragma unroll 2
+#pragma unroll kUnrollQ
                 for (int q = 0; q < 8; q++) {
                     const T *qa = pa + q * L::kPoint;
                     const T *qb = pb + q * L::kPoint;
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                 // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
                 T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
                 T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
-#pragma unroll 2
+#pragma unroll kUnrollQ
                 for (int q = 0; q < 8; q++) {
                     const T *qa = pa + q * L::kPoint;
                     const T *cf = pc + q * L::kCoef;
