@@ -106,9 +106,12 @@ struct TangentLayout {
     // Elements per block (phase 1: one thread per element and Gauss point).  Measured at 128^3:
     // 8 is 4-5% faster than 16 for FP64 and FP32; the two-float kernel needs 16.  The FP64 block
     // adds four warps that only join the pair loop (phase 2): 6% faster again (two warps: 5%,
-    // six: slower; FP32 and two-float: slower with any).
+    // six: slower; the two-float kernel: slower with any).
     static constexpr int kElems = std::is_same<T, df64>::value ? 16 : 8;
-    static constexpr int kThreads = kPre ? 192 : 8 * kElems;
+    // The FP32 element pass (rows mode) adds one warp to the pair loop too: its items' blocks
+    // are held in registers until the matrices are assembled, and three items per thread
+    // instead of five were 5% faster (four warps: slower).
+    static constexpr int kThreads = kPre ? 192 : (std::is_same<T, float>::value ? 96 : 8 * kElems);
     static constexpr int kNumVec = kPre ? 4 : 2;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
