@@ -153,7 +153,7 @@ def make_problem(n):
 
 def config_dict(prob, n):
     return {"workload": f"fibre RVE {n}^3 hex8 neo-Hookean (50% fibres, E 3.5/70 GPa), 1% stretch + 1e-4 noise; "
-                        f"step = tangent CSR with fused residual + K.v (CSR SpMV and matrix-free) + ||R||, FP64",
+                        f"step = tangent CSR with fused residual + K.v (CSR SpMV, and matrix-free at the linearisation the tangent stored) + ||R||, FP64",
             "n_elem": prob.n_elem, "n_dof": prob.n_dof, "fibre_fraction": prob.meta.get("fibre_fraction"),
             "l2": "inputs larger than L2 (CSR values 4.1 GB written and read every step)"}
 
