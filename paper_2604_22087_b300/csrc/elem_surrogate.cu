@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int k = 0; k < 3; k++)
-                    Kab[b][i][k] += M[i][k][0] * g0 + M[i][k][1] * g1 + M[i][k][2] * g2 + (i == k ? geo : 0.0f);
+                    Kab[b][i][k] = fmaf(M[i][k][0], g0, fmaf(M[i][k][1], g1, fmaf(M[i][k][2], g2,
+                                   i == k ? Kab[b][i][k] + geo : Kab[b][i][k])));  // one chain per entry
         }
     }
     // rows 3a .. 3a+2 of K_e: 72 contiguous values of the workspace [element][24][24]
