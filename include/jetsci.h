@@ -99,7 +99,12 @@ typedef struct {
  * them: the CSR pattern of K (rows = DOFs; per row the columns sorted ascending;
  * DOFs of one node are interleaved so each row's columns come in node-sorted
  * 3-wide blocks), an element colouring (no two elements of one colour share a
- * node) and the element-to-CSR slot map.
+ * node) and the element-to-CSR slot map.  It also keeps, per element, the reference
+ * geometry at the 8 Gauss points (Jp, adj(Jp), det Jp and adj(Jp) adj(Jp)^T in FP64,
+ * 1,664 bytes, read by the FP64 and two-float kernels instead of re-forming it from the
+ * coordinates) and room for one FP64 linearisation (768 bytes; see jetsci_apply_tangent).
+ * Device memory at creation is about 2.6 KB per element plus 12 bytes per CSR entry
+ * (column index and, allocated by the caller, FP64 values).
  *
  * coords_host [n_nodes*3] (x,y,z per node), conn_host [n_elem*8] (node ids in the
  * hex8 order above), phase_host [n_elem] (index into mats; may be NULL = all 0),
