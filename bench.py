@@ -37,15 +37,15 @@ METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % o
 
 # Work per element of the dominant kernel, k_tangent<double,double>:
 # executed FP64 operations of the formulation (ncu on the 64^3 fibre RVE: 7,400 DFMA x 2 +
-# 676 DADD + 1,464 DMUL per element) and the algorithmic bytes (write-once CSR values 1,959 +
+# 628 DADD + 1,432 DMUL per element) and the algorithmic bytes (write-once CSR values 1,959 +
 # slot map and masks 96 + u, R and connectivity 82 + the reference-geometry cache 1,216 + the
 # stored linearisation 768).
-TANGENT_FP64_FLOP_PER_ELEM = 16_940.0
+TANGENT_FP64_FLOP_PER_ELEM = 16_860.0
 TANGENT_BYTES_PER_ELEM_FP64 = 4_121.0
 # DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
 # coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
-TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_195.0
+TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_212.0
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
 # index (a node's three rows share one column list); v and y are per-row and stay in L2.
 SPMV_BYTES_PER_NNZ = {"fp64": 8.0 + 4.0 / 3.0, "fp32": 4.0 + 4.0 / 3.0}

@@ -331,9 +331,16 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         // c (tau + m I), tau = 0 in the linear law's tangent
         const T t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
         const T t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
-        // 1 +- xi, 1 +- eta, 1 +- zeta at the lane's Gauss point
-        const T xp = T(1) + K.xi, xm = T(1) - K.xi, yp = T(1) + K.eta, ym = T(1) - K.eta;
-        const T zp = T(1) + K.zeta, zm = T(1) - K.zeta;
+        // 1 +- xi, 1 +- eta, 1 +- zeta at the lane's Gauss point (selected for FP64: element.cuh)
+        T xp, xm, yp, ym, zp, zm;
+        if constexpr (std::is_same<T, double>::value) {
+            xp = (l & 1) ? kGaussP : kGaussM, xm = (l & 1) ? kGaussM : kGaussP;
+            yp = (l & 2) ? kGaussP : kGaussM, ym = (l & 2) ? kGaussM : kGaussP;
+            zp = (l & 4) ? kGaussP : kGaussM, zm = (l & 4) ? kGaussM : kGaussP;
+        } else {
+            xp = T(1) + K.xi, xm = T(1) - K.xi, yp = T(1) + K.eta, ym = T(1) - K.eta;
+            zp = T(1) + K.zeta, zm = T(1) - K.zeta;
+        }
         T *pv = sm.v + es * L::kElem + l * L::kPoint;
 #pragma unroll
         for (int a = 0; a < 8; a++) {

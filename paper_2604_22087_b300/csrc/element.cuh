@@ -150,6 +150,23 @@ __device__ __forceinline__ T reduce_scatter8(const T v[8], int l) {
 // Reference-coordinate bit pattern (xi, eta, zeta) of hex8 local node a: {0,1,3,2,4,5,7,6}.
 __host__ __device__ constexpr int hex_bits_of_node(int a) { return a ^ ((a >> 1) & 1); }
 
+// Gauss coordinate g = 1/sqrt 3 and the values that products of two of the lane's Gauss
+// coordinates (each +-g) and the factors 1 +- g take, rounded as the FP64 operations round them.
+// FP64 elements select these by sign instead of computing them: B300's FP64 pipe bounds the
+// FP64 kernels, and the selection runs on the integer pipes with bit-identical results.
+constexpr double kGaussG = 0.57735026918962576451;
+constexpr double kGaussG2 = kGaussG * kGaussG;                      // (+-g)(+-g) = +-g^2
+constexpr double kGaussP = 1.0 + kGaussG, kGaussM = 1.0 - kGaussG;  // 1 +- g
+
+// a b for two Gauss coordinates a, b in {+g, -g}: +-g^2 with the sign of a b.
+template <typename T>
+__device__ __forceinline__ T gauss_coord_product(T a, T b) { return a * b; }
+template <>
+__device__ __forceinline__ double gauss_coord_product<double>(double a, double b) {
+    const int s = (__double2hiint(a) ^ __double2hiint(b)) & (int)0x80000000;
+    return __hiloint2double(__double2hiint(kGaussG2) | s, __double2loint(kGaussG2));
+}
+
 // 8 * reference derivatives at the lane's Gauss point from 8 * monomial coefficients held
 // by lanes 1..7 (component held by the calling lane in `c`):
 //   d/dxi   = c_xi   + c_xieta eta + c_xizeta zeta + c_xietazeta eta zeta
@@ -159,9 +176,9 @@ template <typename T>
 __device__ __forceinline__ void ref_gradient(T c, T xi, T eta, T zeta, T out[3]) {
     T c1 = shfl8(c, 1), c2 = shfl8(c, 2), c3 = shfl8(c, 3), c4 = shfl8(c, 4);
     T c5 = shfl8(c, 5), c6 = shfl8(c, 6), c7 = shfl8(c, 7);
-    out[0] = c1 + c3 * eta + c5 * zeta + c7 * (eta * zeta);
-    out[1] = c2 + c3 * xi + c6 * zeta + c7 * (xi * zeta);
-    out[2] = c4 + c5 * xi + c6 * eta + c7 * (xi * eta);
+    out[0] = c1 + c3 * eta + c5 * zeta + c7 * gauss_coord_product(eta, zeta);
+    out[1] = c2 + c3 * xi + c6 * zeta + c7 * gauss_coord_product(xi, zeta);
+    out[2] = c4 + c5 * xi + c6 * eta + c7 * gauss_coord_product(xi, eta);
 }
 
 template <typename T>
@@ -320,7 +337,7 @@ __device__ __forceinline__ void gauss_kinematics_coords(const int32_t *__restric
         cx[i] = monomial_coeff<T>(X[i], l);
         cu[i] = monomial_coeff<T>(U[i], l);
     }
-    const T g = (T)0.57735026918962576451;
+    const T g = (T)kGaussG;
     K.xi = (l & 1) ? g : -g;
     K.eta = (l & 2) ? g : -g;
     K.zeta = (l & 4) ? g : -g;
@@ -349,7 +366,7 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
                                                  const double *__restrict__ geom) {
     if constexpr (std::is_same<T, double>::value || (kCachedDf64 && std::is_same<T, df64>::value)) {
         node = conn[8 * e + hex_node_of_lane(l)];
-        const T g = (T)0.57735026918962576451;
+        const T g = (T)kGaussG;
         K.xi = (l & 1) ? g : -g;
         K.eta = (l & 2) ? g : -g;
         K.zeta = (l & 4) ? g : -g;
@@ -396,7 +413,7 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
 __device__ __forceinline__ void gauss_geometry(const int32_t *__restrict__ conn, const double *__restrict__ geom,
                                                int64_t e, int l, int32_t &node, GaussKinematics<double> &K) {
     node = conn[8 * e + hex_node_of_lane(l)];
-    const double g = 0.57735026918962576451;
+    const double g = kGaussG;
     K.xi = (l & 1) ? g : -g;
     K.eta = (l & 2) ? g : -g;
     K.zeta = (l & 4) ? g : -g;
@@ -646,7 +663,8 @@ __device__ __forceinline__ void nodal_force_of_moment(const T Q[3][3], const Gau
         mom[3] = Q0 * K.eta + Q1 * K.xi;
         mom[5] = Q0 * K.zeta + Q2 * K.xi;
         mom[6] = Q1 * K.zeta + Q2 * K.eta;
-        mom[7] = Q0 * (K.eta * K.zeta) + Q1 * (K.xi * K.zeta) + Q2 * (K.xi * K.eta);
+        mom[7] = Q0 * gauss_coord_product(K.eta, K.zeta) + Q1 * gauss_coord_product(K.xi, K.zeta) +
+                 Q2 * gauss_coord_product(K.xi, K.eta);
         // sum over the 8 Gauss points with moment m landing at lane m
         const T mine = reduce_scatter8(mom, l);
         f[i] = butterfly_transpose(mine, l) * T(1.0 / 512.0);
