@@ -14,6 +14,7 @@ namespace jetsci {
 // shuffle reduction occupies the narrow FP64 pipe as much as a product does.  AT is the
 // accumulation type (FP64 for FP64 values, FP32 for FP32 values).
 constexpr int kSpmvLanes = 4;
+constexpr int kSpmvDepth = 4;
 
 template <typename VT, typename AT>
 __global__ void __launch_bounds__(256) k_spmv(int64_t n_nodes, const int64_t *__restrict__ rowptr,
@@ -26,12 +27,35 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n_nodes, const int64_t *__
     AT s0 = 0, s1 = 0, s2 = 0;
     if (active) {
         const int64_t r0 = rowptr[3 * node];
-        const int64_t len = rowptr[3 * node + 1] - r0;
+        const int len = (int)(rowptr[3 * node + 1] - r0);
         const VT *v0 = vals + r0;
         const VT *v1 = v0 + len;
         const VT *v2 = v1 + len;
         const int32_t *c = col + r0;
-        for (int64_t t = lane; t < len; t += kSpmvLanes) {
+        // kSpmvDepth strided entries are loaded before any is used (the column -> v -> product
+        // chain of one entry would otherwise leave each lane with one load in flight); the sums
+        // still take the lane's entries in order, so the result does not depend on the depth.
+        int t = lane;
+        for (; t + (kSpmvDepth - 1) * kSpmvLanes < len; t += kSpmvDepth * kSpmvLanes) {
+            int32_t cj[kSpmvDepth];
+            AT x[kSpmvDepth], a0[kSpmvDepth], a1[kSpmvDepth], a2[kSpmvDepth];
+#pragma unroll
+            for (int j = 0; j < kSpmvDepth; j++) cj[j] = __ldg(c + t + j * kSpmvLanes);
+#pragma unroll
+            for (int j = 0; j < kSpmvDepth; j++) {
+                x[j] = (AT)__ldg(v + cj[j]);
+                a0[j] = (AT)__ldg(v0 + t + j * kSpmvLanes);
+                a1[j] = (AT)__ldg(v1 + t + j * kSpmvLanes);
+                a2[j] = (AT)__ldg(v2 + t + j * kSpmvLanes);
+            }
+#pragma unroll
+            for (int j = 0; j < kSpmvDepth; j++) {
+                s0 += a0[j] * x[j];
+                s1 += a1[j] * x[j];
+                s2 += a2[j] * x[j];
+            }
+        }
+        for (; t < len; t += kSpmvLanes) {
             const AT x = (AT)__ldg(v + __ldg(c + t));
             s0 += (AT)__ldg(v0 + t) * x;
             s1 += (AT)__ldg(v1 + t) * x;
