@@ -5,13 +5,14 @@
 // surrogate inputs.  Phase 2: the MLP forward and input-Jacobian pass on the tensor cores
 // (BF16, FP32 accumulate in TMEM) gives S and D = dS/dE; points with any |E_ij| > range take
 // S and D of the plain neo-Hookean law instead.  Phase 3a (thread = Gauss point): residual
-// contribution, and F, G_b (all nodes), c W D and c S (c = w detJ, W = diag(1,1,1,2,2,2))
+// contribution, and the reference gradients G_b (all nodes) and the first elasticity tensor
+//   A_iJkL = c (F_iI CC_IJKL F_kK + delta_ik S_JL)   (c = w detJ, CC_IJKL from D = dS/dE)
 // into shared memory.  Phase 3b (thread = element node a):
-//   K_ab = sum_q [ B_a^T (c W D) B_b + (G_a . c S G_b) I ]
-// with B_b = dE/du_b (Voigt, tensor components, B_b[v][k] = sym(F_k (x) G_b)_v), evaluated as
-// K_ab[i][k] += (F Y_i G_b)_k where Y_i is the symmetric 3x3 form of row i of B_a^T (c W D).
-// This is the consistent tangent sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL
-// with the Voigt tangent; it is not symmetric for the surrogate, so all 64 node pairs are formed.
+//   K_ab[i][k] = sum_q sum_L M[i][k][L] G_bL,  M[i][k][L] = sum_J G_aJ A_iJkL,
+// the consistent tangent sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL.  Forming
+// A once per point (about 430 multiply-adds) leaves 81 + 8 x 27 per node and point, against
+// about 530 when each node contracted B_a^T (c W D) B_b itself.  The tangent is not symmetric
+// for the surrogate, so all 64 node pairs are formed.
 //
 // The tangent (TANGENT) runs over all elements in order in one launch and writes each element's
 // 24 x 24 rows and nodal forces to the row-gather workspace (gather.cu forms the CSR rows and R).
@@ -44,15 +45,20 @@ struct SurArgs {
     uint32_t *fallback_count;  // Gauss points that used the plain law (may be NULL)
 };
 
-// Per-point phase-3 record, in the (reused) input / activation / tangent region of the tile.
-struct PointRec {
-    float F[3][3];
-    float G[8][3];
-    float cWD[6][6];
-    float cS[6];
-};
-static_assert(sizeof(PointRec) * 128 <= 128 * 16 * 2 + 128 * 64 * 2 + 3 * 128 * 64 * 2, "phase-3 records do not fit");
+// Per-point phase-3 record, in the (reused) input / activation / tangent region of the tile:
+// G[8][3] (reference shape gradients of the eight nodes), then the point's first elasticity
+// tensor times c = w detJ,
+//   A[i][J][k][L] = c (F_iI CC_IJKL F_kK + delta_ik S_JL),
+// as three 28-float blocks (one per i, [J][k][L], the last float padding) so that phase 3b
+// reads each block with seven 16-byte loads.  Points are kRec floats apart and every element's
+// eight points a further 4 floats, which puts the four elements a warp reads in phase 3b on
+// distinct banks.
+constexpr int kRec = 108, kRecA = 24, kRecBlk = 28;
+__device__ __forceinline__ int rec_off(int p) { return p * kRec + (p >> 3) * 4; }
+static_assert((128 * kRec + 16 * 4) * 4 <= 128 * 16 * 2 + 128 * 64 * 2 + 3 * 128 * 64 * 2, "phase-3 records do not fit");
 
+// Voigt index of the tensor component (I, J): [11, 22, 33, 23, 13, 12].
+__host__ __device__ constexpr int voigt_of(int I, int J) { return I == J ? I : 6 - I - J; }
 
 template <bool TANGENT>
 __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const double *__restrict__ u,
@@ -195,15 +201,12 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
         return;
     }
     __syncthreads();  // every MLP tile consumed: the region becomes the point records
-    PointRec *rec = reinterpret_cast<PointRec *>(sm.x);
+    float *recs = reinterpret_cast<float *>(sm.x);
     {
-        PointRec &me = rec[t];
+        float *me = recs + rec_off(t);
         const float rdJ = 1.0f / K.dJ;
         const float c = K.dJ * (1.0f / 512.0f);
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) me.F[i][j] = F[i][j];
+        float Gv[24];
 #pragma unroll
         for (int a = 0; a < 8; a++) {
             const int nb = hex_node_of_lane(a);  // the map is an involution: node -> sign bits
@@ -211,20 +214,52 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
             const float fx = 1.0f + s0 * K.xi, fy = 1.0f + s1 * K.eta, fz = 1.0f + s2 * K.zeta;
             const float n0 = s0 * fy * fz, n1 = fx * s1 * fz, n2 = fx * fy * s2;
 #pragma unroll
-            for (int j = 0; j < 3; j++) me.G[a][j] = (K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2) * rdJ;
+            for (int j = 0; j < 3; j++) Gv[3 * a + j] = (K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2) * rdJ;
         }
 #pragma unroll
-        for (int v = 0; v < 6; v++) {
-            const float w = v < 3 ? c : 2.0f * c;
+        for (int c4 = 0; c4 < 6; c4++)
+            reinterpret_cast<float4 *>(me)[c4] = make_float4(Gv[4 * c4], Gv[4 * c4 + 1], Gv[4 * c4 + 2], Gv[4 * c4 + 3]);
+        // c CC in Voigt pairs: D differentiates w.r.t. tensor components with a shear column
+        // standing for both E_KL and E_LK, so CC_IJKL = D[IJ][KL] / 2 for K != L
+        float Cv[6][6];
 #pragma unroll
-            for (int b = 0; b < 6; b++) me.cWD[v][b] = w * D[v][b];
-            me.cS[v] = c * S[v];
+        for (int v = 0; v < 6; v++)
+#pragma unroll
+            for (int d = 0; d < 6; d++) Cv[v][d] = (d < 3 ? c : 0.5f * c) * D[v][d];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            // Z[J][KL] = sum_I F_iI c CC_IJKL
+            float Z[3][6];
+#pragma unroll
+            for (int J = 0; J < 3; J++)
+#pragma unroll
+                for (int d = 0; d < 6; d++)
+                    Z[J][d] = F[i][0] * Cv[voigt_of(0, J)][d] + F[i][1] * Cv[voigt_of(1, J)][d] +
+                              F[i][2] * Cv[voigt_of(2, J)][d];
+            float Ai[kRecBlk];
+#pragma unroll
+            for (int J = 0; J < 3; J++)
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+#pragma unroll
+                    for (int L = 0; L < 3; L++) {
+                        float sacc = F[k][0] * Z[J][voigt_of(0, L)] + F[k][1] * Z[J][voigt_of(1, L)] +
+                                     F[k][2] * Z[J][voigt_of(2, L)];
+                        if (k == i) sacc += c * S[voigt_of(J, L)];
+                        Ai[9 * J + 3 * k + L] = sacc;
+                    }
+            Ai[27] = 0.0f;
+#pragma unroll
+            for (int c4 = 0; c4 < kRecBlk / 4; c4++)
+                reinterpret_cast<float4 *>(me + kRecA + kRecBlk * i)[c4] =
+                    make_float4(Ai[4 * c4], Ai[4 * c4 + 1], Ai[4 * c4 + 2], Ai[4 * c4 + 3]);
         }
     }
     tc::fence_before_sync();
     __syncthreads();
     if (t < 32) tc::tmem_dealloc(sm.tmem_base, kCols);
     // ---------------- phase 3b: thread = (element es, node a = l)
+    //   K_ab[i][k] += sum_L M[i][k][L] G_bL,  M[i][k][L] = sum_J G_aJ A[i][J][k][L]
     const int32_t eid = s_elem[es];
     if (eid < 0) return;
     const int a = l;
@@ -237,56 +272,37 @@ __global__ void __launch_bounds__(128, 2) k_elem_surrogate(SurArgs A, const doub
             for (int k = 0; k < 3; k++) Kab[b][i][k] = 0.0f;
 #pragma unroll 1
     for (int q = 0; q < 8; q++) {
-        const PointRec &r = rec[8 * es + q];
-        float Fq[3][3], ga[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            ga[i] = r.G[a][i];
-#pragma unroll
-            for (int j = 0; j < 3; j++) Fq[i][j] = r.F[i][j];
-        }
-        // B_a[v][i] (Voigt tensor component v of sym(F_i (x) G_a))
-        float Ba[6][3];
-#pragma unroll
-        for (int v = 0; v < 6; v++) {
-            const int I = voigt_i(v), Jj = voigt_j(v);
-#pragma unroll
-            for (int i = 0; i < 3; i++) Ba[v][i] = 0.5f * (Fq[i][I] * ga[Jj] + Fq[i][Jj] * ga[I]);
-        }
-        // M_i = F Yhat_i with Yhat_i the symmetric form of Y_i = B_a^T (c W D) row i
+        const float *r = recs + rec_off(8 * es + q);
+        const float ga0 = r[3 * a], ga1 = r[3 * a + 1], ga2 = r[3 * a + 2];
         float M[3][3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            float Y[6];
+            float Ai[kRecBlk];
 #pragma unroll
-            for (int w = 0; w < 6; w++) {
-                float sacc = 0.0f;
-#pragma unroll
-                for (int v = 0; v < 6; v++) sacc += Ba[v][i] * r.cWD[v][w];
-                Y[w] = sacc;
+            for (int c4 = 0; c4 < kRecBlk / 4; c4++) {
+                const float4 x = reinterpret_cast<const float4 *>(r + kRecA + kRecBlk * i)[c4];
+                Ai[4 * c4] = x.x, Ai[4 * c4 + 1] = x.y, Ai[4 * c4 + 2] = x.z, Ai[4 * c4 + 3] = x.w;
             }
-            const float Yh[3][3] = {{Y[0], 0.5f * Y[5], 0.5f * Y[4]},
-                                    {0.5f * Y[5], Y[1], 0.5f * Y[3]},
-                                    {0.5f * Y[4], 0.5f * Y[3], Y[2]}};
 #pragma unroll
             for (int k = 0; k < 3; k++)
 #pragma unroll
-                for (int J2 = 0; J2 < 3; J2++)
-                    M[i][k][J2] = Fq[k][0] * Yh[0][J2] + Fq[k][1] * Yh[1][J2] + Fq[k][2] * Yh[2][J2];
+                for (int L = 0; L < 3; L++)
+                    M[i][k][L] = fmaf(ga0, Ai[3 * k + L], fmaf(ga1, Ai[9 + 3 * k + L], ga2 * Ai[18 + 3 * k + L]));
         }
-        const float sg0 = r.cS[0] * ga[0] + r.cS[5] * ga[1] + r.cS[4] * ga[2];
-        const float sg1 = r.cS[5] * ga[0] + r.cS[1] * ga[1] + r.cS[3] * ga[2];
-        const float sg2 = r.cS[4] * ga[0] + r.cS[3] * ga[1] + r.cS[2] * ga[2];
+        float Gb[24];
+#pragma unroll
+        for (int c4 = 0; c4 < 6; c4++) {
+            const float4 x = reinterpret_cast<const float4 *>(r)[c4];
+            Gb[4 * c4] = x.x, Gb[4 * c4 + 1] = x.y, Gb[4 * c4 + 2] = x.z, Gb[4 * c4 + 3] = x.w;
+        }
 #pragma unroll
         for (int b = 0; b < 8; b++) {
-            const float g0 = r.G[b][0], g1 = r.G[b][1], g2 = r.G[b][2];
-            const float geo = sg0 * g0 + sg1 * g1 + sg2 * g2;
+            const float g0 = Gb[3 * b], g1 = Gb[3 * b + 1], g2 = Gb[3 * b + 2];
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
                 for (int k = 0; k < 3; k++)
-                    Kab[b][i][k] = fmaf(M[i][k][0], g0, fmaf(M[i][k][1], g1, fmaf(M[i][k][2], g2,
-                                   i == k ? Kab[b][i][k] + geo : Kab[b][i][k])));  // one chain per entry
+                    Kab[b][i][k] = fmaf(M[i][k][0], g0, fmaf(M[i][k][1], g1, fmaf(M[i][k][2], g2, Kab[b][i][k])));
         }
     }
     // rows 3a .. 3a+2 of K_e: 72 contiguous values of the workspace [element][24][24]
