@@ -102,8 +102,9 @@ typedef struct {
  * node) and the element-to-CSR slot map.  It also keeps, per element, the reference
  * geometry at the 8 Gauss points (Jp, adj(Jp), det Jp and adj(Jp) adj(Jp)^T in FP64,
  * 1,664 bytes, read by the FP64 and two-float kernels instead of re-forming it from the
- * coordinates) and room for one FP64 linearisation (768 bytes; see jetsci_apply_tangent).
- * Device memory at creation is about 2.6 KB per element plus 12 bytes per CSR entry
+ * coordinates), room for one FP64 linearisation (768 bytes; see jetsci_apply_tangent) and
+ * for one set of element residual vectors (192 bytes; see jetsci_material_grad).
+ * Device memory at creation is about 2.8 KB per element plus 12 bytes per CSR entry
  * (column index and, allocated by the caller, FP64 values).
  *
  * coords_host [n_nodes*3] (x,y,z per node), conn_host [n_elem*8] (node ids in the
@@ -143,6 +144,9 @@ jetsci_status jetsci_mesh_check(jetsci_mesh mesh, uint32_t *flags_host);
  * u_dev [n_dof] FP64, R_dev [n_dof] FP64 (overwritten).  E_elem_dev [n_elem] FP64 or
  * NULL: per-element Young's modulus replacing the phase's (the phase's nu and law are
  * kept).  precision: JETSCI_FP64, FP32, DF64 or SURROGATE (TF32 acts as FP32 here).
+ * With E_elem_dev given (FP64, FP32, TF32, DF64) the call also keeps its element vectors
+ * R_e in the mesh (192 bytes per element, allocated with the mesh) for
+ * jetsci_material_grad with u_dev = NULL; the next such call replaces them.
  */
 jetsci_status jetsci_residual(jetsci_mesh mesh, const double *u_dev, double *R_dev,
                               int32_t precision, const double *E_elem_dev, void *stream);
@@ -189,6 +193,13 @@ jetsci_status jetsci_apply_tangent(jetsci_mesh mesh, const double *u_dev, const 
  * dL/dE_e = R[dofs_e] . R_e(u; E = 1).  R_dev must be jetsci_residual(u, E) of the
  * same mesh/precision.  E_elem_dev [n_elem] or NULL (phase moduli); dLdE_dev [n_elem]
  * FP64 (overwritten).  precision: JETSCI_FP64, FP32 or DF64.
+ * u_dev = NULL: the gradient at the state of the last jetsci_residual call with a
+ * per-element modulus field, from the element vectors that call kept:
+ * dL/dE_e = R[dofs_e] . R_e / E_e, with no element arithmetic (the backward pass of
+ * L = 1/2 ||R||^2 right after its forward residual).  E_elem_dev must be the pointer that
+ * call used, with the same contents and nonzero entries, and precision the one it used;
+ * otherwise (no such call, a surrogate residual since, another pointer or precision)
+ * JETSCI_ERR_ARG.  The calls must be ordered on the stream(s).
  */
 jetsci_status jetsci_material_grad(jetsci_mesh mesh, const double *u_dev,
                                    const double *E_elem_dev, const double *R_dev,

@@ -21,6 +21,8 @@ struct ElemArgs {
     const double *__restrict__ geom;    // per-element reference geometry (read by the FP64 kernels)
     double *lin;                        // FP64 linearisation store (element.cuh, kLin*): written by
                                         // the FP64 residual and tangent when set
+    double *re;                         // element residual store [n_elem][8][3]: written by the
+                                        // residual when set (for the material gradient)
     const int32_t *__restrict__ phase;
     const Material *__restrict__ mats;
     const double *__restrict__ E_elem;
@@ -49,8 +51,10 @@ __device__ __forceinline__ void put_or_add(VT *dst, VT v, bool first) {
 
 // ---------------------------------------------------------------------------- residual
 // R_e(a,i) = sum_q w detJ P_iJ G_aJ, scattered into R (FP64 in every precision); the stress
-// moment comes from residual_moment (spatial form for the neo-Hookean law).
-template <typename T>
+// moment comes from residual_moment (spatial form for the neo-Hookean law).  kKeep: also
+// writes each element's R_e to A.re (a separate instantiation: the FP32 kernel without it stays
+// at 56 registers, one block per SM more than with it).
+template <typename T, bool kKeep>
 __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__restrict__ u,
                                                   double *__restrict__ R) {
     const int l = threadIdx.x & 7;
@@ -75,6 +79,9 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
         raise_flag(A.flags, bits);
 #pragma unroll
         for (int i = 0; i < 3; i++) R[3 * (int64_t)node + i] += to_double(f[i]);
+        if constexpr (kKeep)
+#pragma unroll
+            for (int i = 0; i < 3; i++) A.re[24 * e + 3 * hex_node_of_lane(l) + i] = to_double(f[i]);
     }
 }
 
@@ -730,6 +737,29 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
     }
 }
 
+// The same gradient from the element vectors a residual call with E_elem kept: R_e(u; E) =
+// E_e R_e(u; 1), so dL/dE_e = R[dofs_e] . R_e / E_e, a gather and a dot per element (lane =
+// local node) with no element arithmetic.
+__global__ void __launch_bounds__(128) k_material_grad_stored(const int32_t *__restrict__ conn,
+                                                              const double *__restrict__ re,
+                                                              const double *__restrict__ E_elem, int64_t n,
+                                                              const double *__restrict__ R, double *__restrict__ g,
+                                                              uint32_t *flags) {
+    const int a = threadIdx.x & 7;
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool active = slot < n;
+    const int64_t e = active ? slot : n - 1;
+    const int64_t node = conn[8 * e + a];
+    const double *r = re + 24 * e + 3 * a;
+    double d = R[3 * node] * r[0] + R[3 * node + 1] * r[1] + R[3 * node + 2] * r[2];
+    d = allreduce8(d);
+    if (active && a == 0) {
+        const double ge = d / E_elem[e];
+        if (!isfinite(ge)) raise_flag(flags, JETSCI_FLAG_NONFINITE);
+        g[e] = ge;
+    }
+}
+
 // ---------------------------------------------------------------------------- geometry cache
 // Fills the mesh's per-element reference geometry (element.cuh) with the same arithmetic the
 // kernels use when they form it from the coordinates.
@@ -788,6 +818,7 @@ static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
     A.coords = m->d_coords;
     A.geom = m->d_geom;
     A.lin = nullptr;
+    A.re = nullptr;
     A.phase = m->d_phase;
     A.mats = m->d_mats;
     A.E_elem = E_elem;
@@ -804,7 +835,10 @@ static void residual_colours(jetsci_mesh m, ElemArgs A, const double *u, double 
         A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
         if (A.n == 0) continue;
         unsigned grid = (unsigned)((8 * A.n + 127) / 128);
-        k_residual<T><<<grid, 128, 0, s>>>(A, u, R);
+        if (A.re)
+            k_residual<T, true><<<grid, 128, 0, s>>>(A, u, R);
+        else
+            k_residual<T, false><<<grid, 128, 0, s>>>(A, u, R);
     }
 }
 
@@ -812,6 +846,14 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
                               const double *E_elem, cudaStream_t s) {
     JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
     ElemArgs A = make_args(m, E_elem);
+    if (E_elem) {
+        // keep R_e for jetsci_material_grad at this state (u = NULL there); the surrogate
+        // residual keeps none, so it leaves no element vectors to use
+        m->re_valid = precision != JETSCI_SURROGATE;
+        m->re_E = E_elem;
+        m->re_prec = precision == JETSCI_TF32 ? JETSCI_FP32 : precision;
+        if (m->re_valid) A.re = m->d_re;
+    }
     if (precision == JETSCI_FP64) {
         A.lin = m->d_lin;  // the linearisation at u, for matrix-free products at this state
         m->lin_valid = true;
@@ -936,6 +978,11 @@ jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double 
     ElemArgs A = make_args(m, E_elem);
     A.n = m->n_elem;
     unsigned grid = (unsigned)((8 * A.n + 127) / 128);
+    if (!u) {  // from the element vectors of the last residual call with E_elem (checked by the caller)
+        k_material_grad_stored<<<grid, 128, 0, s>>>(m->d_conn, m->d_re, E_elem, A.n, R, g, m->d_flags);
+        JETSCI_CUDA_TRY(cudaGetLastError());
+        return JETSCI_OK;
+    }
     if (precision == JETSCI_FP64)
         k_material_grad<double><<<grid, 128, 0, s>>>(A, u, R, g);
     else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)

@@ -69,7 +69,16 @@ extern "C" jetsci_status jetsci_material_grad(jetsci_mesh m, const double *u, co
     if (st) return st;
     if (!valid_precision(precision)) return fail(JETSCI_ERR_ARG, "invalid precision");
     if (m->n_elem == 0) return JETSCI_OK;
-    if (!u || !R || !g) return fail(JETSCI_ERR_ARG, "u, R or dLdE is NULL");
+    if (!R || !g) return fail(JETSCI_ERR_ARG, "R or dLdE is NULL");
+    if (!u) {
+        // from the element vectors kept by the last residual call with a per-element modulus field
+        if (!m->re_valid)
+            return fail(JETSCI_ERR_ARG, "u is NULL and no jetsci_residual call with E_elem has kept element residuals");
+        if (!E_elem || E_elem != m->re_E)
+            return fail(JETSCI_ERR_ARG, "u is NULL: E_elem differs from the residual call that kept the element vectors");
+        if ((precision == JETSCI_TF32 ? JETSCI_FP32 : precision) != m->re_prec)
+            return fail(JETSCI_ERR_ARG, "u is NULL: precision differs from the residual call that kept the element vectors");
+    }
     return launch_material_grad(m, u, E_elem, R, g, precision, s);
 }
 

@@ -42,6 +42,11 @@ struct jetsci_mesh_s {
     double *d_lin = nullptr;            // [n_elem][6][8][2]: FP64 neo-Hookean linearisation (element.cuh)
     bool lin_valid = false;             // d_lin holds the state of an FP64 residual/tangent call
     const double *lin_E = nullptr;      // ... made with this per-element modulus array (or NULL)
+    double *d_re = nullptr;             // [n_elem][8][3]: element residual vectors R_e kept by the last
+                                        // residual call given a per-element modulus field
+    bool re_valid = false;              // d_re holds such a call's R_e ...
+    const double *re_E = nullptr;       // ... made with this E_elem array ...
+    int32_t re_prec = -1;               // ... in this precision (TF32 recorded as FP32)
     double *d_geom = nullptr;           // [n_elem][13][8][2]: reference geometry at the Gauss points
                                         // (element.cuh, kGeom*), read by the FP64 kernels
     int32_t *d_phase = nullptr;         // [n_elem]

@@ -126,6 +126,9 @@ class Mesh:
         self.n_dof, self.nnz, self.n_colours = nd.value, nnz.value, nc.value
         self._rowptr_ptr, self._col_ptr = rp.value, cp.value
         self.device = torch.cuda.current_device()
+        # counts the residual calls given E_elem: each replaces the element vectors the library
+        # keeps for material_grad(None, ...), so MaterialGrad can tell whether its own are current
+        self.residual_with_E_calls = 0
 
     @classmethod
     def of(cls, problem, stream=None):
@@ -174,6 +177,8 @@ class Mesh:
         R = self.new_vector() if R is None else _dev_f64(R, self.n_dof, "R")
         _dev_f64(E_elem, self.n_elem, "E_elem")
         _check(lib.jetsci_residual(self._h, _ptr(u), _ptr(R), precision, _ptr(E_elem), _stream(stream)))
+        if E_elem is not None:
+            self.residual_with_E_calls += 1
         return R
 
     def tangent_csr(self, u, vals=None, R=None, precision=FP64, E_elem=None, stream=None):
@@ -214,7 +219,10 @@ class Mesh:
         return y
 
     def material_grad(self, u, R, E_elem=None, g=None, precision=FP64, stream=None):
-        _dev_f64(u, self.n_dof, "u")
+        """dL/dE_e for L = 1/2 ||R||^2.  u=None: at the state of the last residual call given
+        E_elem (the same tensor and precision), from the element vectors that call kept."""
+        if u is not None:
+            _dev_f64(u, self.n_dof, "u")
         _dev_f64(R, self.n_dof, "R")
         _dev_f64(E_elem, self.n_elem, "E_elem")
         g = torch.empty(self.n_elem, dtype=torch.float64, device="cuda") if g is None else g
@@ -241,16 +249,20 @@ class MaterialGrad(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, E, mesh, u, precision=FP64):
-        R = mesh.residual(u, precision=precision, E_elem=E.detach().contiguous())
+        Ed = E.detach().contiguous()
+        R = mesh.residual(u, precision=precision, E_elem=Ed)
         nrm = mesh.norm2(R)
-        ctx.mesh, ctx.precision = mesh, precision
-        ctx.save_for_backward(E, u, R)
+        ctx.mesh, ctx.precision, ctx.calls = mesh, precision, mesh.residual_with_E_calls
+        ctx.save_for_backward(E, u, R, Ed)
         return 0.5 * nrm[0] * nrm[0]
 
     @staticmethod
     def backward(ctx, gout):
-        E, u, R = ctx.saved_tensors
-        g = ctx.mesh.material_grad(u, R, E_elem=E.detach().contiguous(), precision=ctx.precision)
+        E, u, R, Ed = ctx.saved_tensors
+        # the element vectors kept by this forward's residual call, unless another residual call
+        # with E_elem has replaced them since; then the gradient pass recomputes them from u
+        kept = ctx.mesh.residual_with_E_calls == ctx.calls
+        g = ctx.mesh.material_grad(None if kept else u, R, E_elem=Ed, precision=ctx.precision)
         return g * gout, None, None, None
 
 

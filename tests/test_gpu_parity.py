@@ -201,6 +201,46 @@ def test_material_gradient_fp64():
     assert abs(L.item() - 0.5 * oracle.norm2(R_ref) ** 2) <= 1e-13 * L.item()
 
 
+def test_material_gradient_from_kept_element_vectors():
+    """A residual call given E_elem keeps its element vectors R_e; the gradient with u = NULL
+    forms R[dofs_e] . R_e / E_e from them.  It must match the gradient pass that recomputes
+    R_e(u; E = 1) (another formula on the same state) and the oracle in FP64, DF64 and FP32,
+    and be refused with nothing kept, for another E_elem pointer or another precision.  Through
+    torch.autograd a second forward in between makes the backward recompute instead."""
+    prob = I.lognormal_problem(12, seed=4)
+    J = jetsci()
+    mesh = J.Mesh.of(prob)
+    om = oracle.Mesh.of(prob)
+    u, E = cuda(prob.u), cuda(prob.E_elem)
+    R_ref = oracle.residual(om, prob.u)
+    g_ref = oracle.material_grad(om, prob.u, R_ref)
+    Rd = cuda(R_ref)
+    with pytest.raises(J.JetsciError) as ei:  # nothing kept yet
+        mesh.material_grad(None, Rd, E_elem=E)
+    assert ei.value.status == 1
+    mesh.residual(u)  # the phase moduli: keeps nothing
+    with pytest.raises(J.JetsciError):
+        mesh.material_grad(None, Rd, E_elem=E)
+    # (precision, kept vs recomputed, vs oracle): FP32 as the FP32 residual bound
+    for p, tol_same, tol_ref in ((J.FP64, 1e-13, FP64_TOL), (J.DF64, 1e-13, FP64_TOL), (J.FP32, 1e-5, 2e-4)):
+        R = mesh.residual(u, E_elem=E, precision=p)
+        g_kept = mesh.material_grad(None, R, E_elem=E, precision=p).cpu().numpy()
+        g_rec = mesh.material_grad(u, R, E_elem=E, precision=p).cpu().numpy()
+        assert relerr(g_kept, g_rec) <= tol_same, p
+        assert relerr(g_kept, g_ref) <= tol_ref, p
+    with pytest.raises(J.JetsciError):  # kept by an FP32 call
+        mesh.material_grad(None, Rd, E_elem=E, precision=J.FP64)
+    with pytest.raises(J.JetsciError):  # another array with the same values
+        mesh.material_grad(None, Rd, E_elem=E.clone(), precision=J.FP32)
+    assert mesh.check() == 0
+    Et = E.clone().requires_grad_(True)
+    L1 = J.MaterialGrad.apply(Et, mesh, u)
+    J.MaterialGrad.apply(Et, mesh, u * 0.5)  # replaces the element vectors L1's forward kept
+    L1.backward()
+    assert relerr(Et.grad.cpu().numpy(), g_ref) <= FP64_TOL
+    mesh.close()
+
+
 @pytest.mark.parametrize("name", ["FP64", "FP32", "DF64", "TF32"])
 def test_tangent_overwrites_every_value(case, name):
     """The tangent does not clear the value array: in the coloured scatter (FP64) each CSR
