@@ -627,6 +627,24 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
         if p not in (J.FP64, J.DF64):
             del vv
             torch.cuda.empty_cache()
+    # The same step with two-float (DF64) element arithmetic on the FP32 pipes: tangent CSR with
+    # fused R (FP64 values), CSR K.v, matrix-free DF64 K.v (formed from u: the stored
+    # linearisation is FP64-only) and the FP64 norm.  An FP64-accurate alternative reported
+    # beside the IEEE FP64 headline, never in its place.
+    nrm = torch.empty(1, dtype=torch.float64, device="cuda")
+    y2 = mesh.new_vector()
+
+    def df64_step():
+        mesh.tangent_csr(u, vals=vals64, R=R, precision=J.DF64, stream=stream)
+        mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals64, precision=J.DF64, stream=stream)
+        mesh.apply_tangent(u, v, y=y, precision=J.DF64, stream=stream)
+        mesh.norm2(R, out=nrm, stream=stream)
+
+    ms = timeit(df64_step, stream)
+    torch.cuda.synchronize()
+    err = so.errors(gather_rows(R, so.nodes), gather_vals(vals64, rp_h, so.nodes), gather_rows(y, so.nodes), rp_h,
+                    col_h)
+    rec("step_df64", ms, {"err_vs_oracle": err})
     if not args.no_extras:
         s, tinfo = train_surrogate(J, torch, I)
         out["surrogate_training"] = tinfo
