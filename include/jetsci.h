@@ -138,6 +138,18 @@ jetsci_status jetsci_mesh_copy_pattern(jetsci_mesh mesh, int64_t *rowptr, int32_
  * *flags_host and clears it.  Returns JETSCI_ERR_NONFINITE if any bit was set. */
 jetsci_status jetsci_mesh_check(jetsci_mesh mesh, uint32_t *flags_host);
 
+/* Structural check of the assembly data built at creation (the precomputed pattern and maps
+ * that Section III-B's element-batched assembly and Section III-C's COO preallocation fix
+ * before any values), run on the device.  counts_host [4] receives the number of violations
+ * of: [0] element node ids outside [0, n_nodes); [1] the colouring (two elements of one
+ * colour sharing a node, or an element not in exactly one colour); [2] the slot map (an
+ * element node pair (a, b) whose slot does not hold node b's three DOF columns in each of
+ * node a's three CSR rows); [3] the first-writer masks (a CSR node-pair block without exactly
+ * one first writer).  All zero for a valid mesh; otherwise JETSCI_ERR_MESH with the counts in
+ * the message.  A debugging aid: it allocates and frees about 4 * (n_nodes + n_elem + nnz / 9)
+ * bytes of device memory and synchronises `stream`. */
+jetsci_status jetsci_mesh_validate(jetsci_mesh mesh, uint64_t *counts_host, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Global residual R(u) = sum_e P_e^T R_e (Section II-A, R(u) = 0), with
  * R_e(a,i) = sum_q w_q detJ_q (F S)_iJ G_aJ.

@@ -274,3 +274,38 @@ def roller_bcs(coords: np.ndarray, stretch: float = 0.01, tol: float = 1e-12):
     for n in np.where(np.abs(x[:, 2]) < tol)[0]:
         dofs.append(3 * n + 2); vals.append(0.0)
     return np.array(dofs, dtype=np.int64), np.array(vals, dtype=np.float64)
+
+
+# Named, seed-pinned workloads.  Each entry gives the problem (mesh, phases, materials, u, v and,
+# for the adjoint workload, E_elem), the precision(s) the workload is run in, and, for the
+# surrogate workload, how its training set is drawn.  Calling a preset builds its inputs.
+PRESETS = {
+    "sphere16_linear": dict(
+        build=lambda: sphere_composite(16, seed=1, law=LAW_LINEAR_ELASTIC),
+        precisions=("fp64",),
+        about="16^3 two-phase sphere RVE (12 inclusions, r = 0.12), linear elastic, u ~ U[+-1e-3]"),
+    "fibre128_neohookean": dict(
+        build=lambda: fibre_composite(128, seed=2, law=LAW_NEO_HOOKEAN),
+        precisions=("fp64",),
+        about="128^3 unidirectional fibre RVE (r = 0.05, 50%), neo-Hookean, 1% stretch + 1e-4 noise"),
+    "fibre128_mixed_precision": dict(
+        build=lambda: fibre_composite(128, seed=2, law=LAW_NEO_HOOKEAN),
+        precisions=("fp32", "tf32"),
+        about="the 128^3 fibre RVE with FP32 / TF32 element arithmetic, FP64 residual scatter and norm"),
+    "lognormal64_adjoint": dict(
+        build=lambda: lognormal_problem(64, seed=4),
+        precisions=("fp64", "fp32"),
+        about="64^3 linear elastic, lognormal E (median 10 GPa, sigma_log 0.5, 3-voxel blur), dL/dE"),
+    "fibre128_surrogate": dict(
+        build=lambda: fibre_composite(128, seed=2, law=LAW_NEO_HOOKEAN),
+        precisions=("surrogate",),
+        training=lambda: strain_samples(1 << 20, seed=5),
+        about="the 128^3 fibre RVE with the MLP surrogate trained on 2^20 strains |E_ij| <= 0.05"),
+}
+
+
+def preset(name: str) -> Problem:
+    """Builds the inputs of a named workload (PRESETS)."""
+    if name not in PRESETS:
+        raise KeyError(f"unknown preset {name!r}; known: {sorted(PRESETS)}")
+    return PRESETS[name]["build"]()

@@ -27,7 +27,7 @@ _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_MESH", 5:
 # Names the C ABI exports (include/jetsci.h); checked by the CPU tests.
 EXPORTS = [
     "jetsci_mesh_create", "jetsci_mesh_destroy", "jetsci_mesh_info", "jetsci_mesh_check",
-    "jetsci_mesh_copy_pattern",
+    "jetsci_mesh_copy_pattern", "jetsci_mesh_validate",
     "jetsci_residual", "jetsci_tangent_csr", "jetsci_apply_tangent", "jetsci_material_grad",
     "jetsci_assemble_element_blocks", "jetsci_norm2", "jetsci_norm2_static", "jetsci_last_error",
     "jetsci_version",
@@ -59,6 +59,7 @@ def _load():
                              C.POINTER(i32)],
         "jetsci_mesh_check": [_vp, C.POINTER(C.c_uint32)],
         "jetsci_mesh_copy_pattern": [_vp, _vp, _vp, _vp],
+        "jetsci_mesh_validate": [_vp, C.POINTER(C.c_uint64), _vp],
         "jetsci_residual": [_vp, _vp, _vp, i32, _vp, _vp],
         "jetsci_tangent_csr": [_vp, _vp, _vp, _vp, i32, _vp, _vp],
         "jetsci_apply_tangent": [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp],
@@ -164,6 +165,17 @@ class Mesh:
         if st != 0 and st != 5:
             _check(st)
         return f.value
+
+    def validate(self, stream=None, raise_on_fail=True):
+        """Device check of the creation-time assembly data; returns the violation counts
+        {node_ids, colouring, slot_map, first_writers} (all 0 for a valid mesh).  Any nonzero
+        count raises JetsciError (JETSCI_ERR_MESH) unless raise_on_fail is False."""
+        c = (C.c_uint64 * 4)()
+        st = lib.jetsci_mesh_validate(self._h, c, _stream(stream))
+        counts = dict(zip(("node_ids", "colouring", "slot_map", "first_writers"), [int(x) for x in c]))
+        if st != 0 and (raise_on_fail or st != 4):
+            _check(st)
+        return counts
 
     # ------------------------------------------------------------------ compute calls
     def new_vector(self):
@@ -367,6 +379,20 @@ class Surrogate:
 
     def layers(self):
         return unpack_layers(self.params())
+
+    def save(self, path, **meta):
+        """Checkpoint as .npz: the parameters (FP64 copy of the library's weights), the input
+        scale, the fallback range and the per-phase output scalings, plus any metadata given
+        (for example the training seed and step count).  Surrogate.load restores it."""
+        np.savez(path, params=self.params(), in_scale=self.cfg.in_scale, range=self.cfg.range,
+                 out_scale=np.array(self.cfg.out_scale[:]), out_shift=np.array(self.cfg.out_shift[:]), **meta)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """A surrogate on the current CUDA device from a checkpoint written by save()."""
+        z = np.load(path)
+        return cls(z["params"], float(z["in_scale"]), float(z["range"]), z["out_scale"], z["out_shift"],
+                   stream=stream)
 
     @staticmethod
     def label(materials, E6, phase, stream=None):

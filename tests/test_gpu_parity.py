@@ -149,6 +149,45 @@ def test_matrix_free_linearisation_errors():
     mesh.close()
 
 
+def test_mesh_structure_validator(case):
+    """The device validator of the creation-time assembly data (colouring, slot map, first-writer
+    masks, node ids) finds nothing on the structured, distorted and ragged meshes."""
+    _, mesh, _, _ = case
+    assert mesh.validate() == dict(node_ids=0, colouring=0, slot_map=0, first_writers=0)
+
+
+def test_mesh_structure_validator_detects_a_swapped_column():
+    """Two column indices of node 0's first CSR row swapped in the mesh's own pattern (4-byte
+    host-to-device copies into its device array, in bounds) must show as slot-map violations;
+    with the entries restored the mesh validates clean again."""
+    from cuda.bindings import runtime as cudart
+    J = jetsci()
+    prob = dict(PROBLEMS)["ragged_neohookean"]
+    mesh = J.Mesh.of(prob)
+    rp, col = mesh.pattern(device="cpu")
+    a = int(rp[0])
+    b = a + 3  # first column of node 0's second neighbour
+    orig = col.numpy()[[a, b]].copy()
+
+    def put(idx, val):
+        buf = np.array([val], dtype=np.int32)
+        (err,) = cudart.cudaMemcpy(mesh._col_ptr + 4 * idx, buf.ctypes.data, 4,
+                                   cudart.cudaMemcpyKind.cudaMemcpyHostToDevice)
+        assert err == cudart.cudaError_t.cudaSuccess
+
+    put(a, orig[1])
+    put(b, orig[0])
+    with pytest.raises(J.JetsciError) as ei:
+        mesh.validate()
+    assert ei.value.status == 4
+    bad = mesh.validate(raise_on_fail=False)
+    assert bad["slot_map"] >= 2 and bad["node_ids"] == 0 and bad["colouring"] == 0
+    put(a, orig[0])
+    put(b, orig[1])
+    assert mesh.validate() == dict(node_ids=0, colouring=0, slot_map=0, first_writers=0)
+    mesh.close()
+
+
 def test_norm2_fp64(case):
     prob, mesh, _, ref = case
     n = mesh.norm2(cuda(ref["R"])).item()
@@ -278,6 +317,7 @@ def test_shuffled_numbering_general_colouring():
                      g.uniform(-3e-3, 3e-3, coords.size), g.uniform(-1, 1, coords.size))
     mesh = J.Mesh.of(prob)
     assert mesh.n_colours > 8
+    assert mesh.validate() == dict(node_ids=0, colouring=0, slot_map=0, first_writers=0)  # general colouring, slot map and first writers
     om = oracle.Mesh.of(prob)
     rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
     vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
@@ -334,6 +374,7 @@ def test_high_valence_node_and_isolated_node(name):
     J = jetsci()
     prob = high_valence_problem()
     mesh = J.Mesh.of(prob)
+    assert mesh.validate() == dict(node_ids=0, colouring=0, slot_map=0, first_writers=0)  # slots up to 84, an empty node
     rp, col = mesh.pattern()
     rp = rp.cpu().numpy()
     assert (rp[1] - rp[0]) // 3 == 85 and rp[-1] == rp[-4]  # node 0: 85 neighbours; last node: none
@@ -424,6 +465,12 @@ def full_size():
 # FP32/TF32 bounds are those of the small-case tests (derivations there).
 FULL_SIZE_FORMS = [("FP64", FP64_TOL, FP64_TOL, FP64_TOL), ("DF64", FP64_TOL, FP64_TOL, FP64_TOL),
                    ("FP32", 2e-4, 5e-5, 2e-4), ("TF32", 2e-4, 3e-3, 1e-2)]
+
+
+def test_full_size_mesh_validates(full_size):
+    """The 128^3 mesh's colouring, slot map (513.6 M CSR entries) and first-writer masks."""
+    _, mesh, _, _ = full_size
+    assert mesh.validate() == dict(node_ids=0, colouring=0, slot_map=0, first_writers=0)
 
 
 @pytest.mark.parametrize("form", FULL_SIZE_FORMS, ids=[f[0] for f in FULL_SIZE_FORMS])

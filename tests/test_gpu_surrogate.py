@@ -162,6 +162,23 @@ def test_adam_first_step_on_device(data):
     assert np.max(np.abs(p1 - expect)) <= 1e-3 * 1e-4 + 1e-7 * np.max(np.abs(p0))
 
 
+def test_checkpoint_round_trip(data, tmp_path):
+    """save() then load() restores the weights and scalings: the restored surrogate evaluates
+    S and D bit for bit like the original, and metadata given to save() is kept."""
+    E6, ph, E6d, phd = data
+    s = J().Surrogate(_layers(7), **config())
+    path = tmp_path / "surrogate.npz"
+    s.save(path, seed=7)
+    t = J().Surrogate.load(path)
+    assert np.array_equal(s.params(), t.params())
+    S1, D1 = s.eval(E6d, phd)
+    S2, D2 = t.eval(E6d, phd)
+    assert torch.equal(S1, S2) and torch.equal(D1, D2)
+    assert int(np.load(path)["seed"]) == 7
+    s.close()
+    t.close()
+
+
 def test_training_reduces_error_and_beats_the_baselines():
     """Train on NH labels with the library's kernels; the trained network is far closer to
     the plain law than the untrained network and than small-strain Hooke."""
