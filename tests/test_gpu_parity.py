@@ -8,6 +8,8 @@ arithmetic: unit roundoff 6e-8 times the depth of the per-Gauss-point computatio
 (~10) gives ~6e-5; the tests use 2e-4 for R and K.v and 5e-5 for CSR values (no
 cross-element cancellation inside one entry beyond the 8-fold sum).
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 import torch
@@ -445,6 +447,56 @@ def test_inverted_element_sets_flag_not_fault():
     mesh.residual(u)
     assert mesh.check() & J.FLAG_BAD_ELEMENT
     assert mesh.check() == 0  # cleared
+
+
+def test_nonfinite_input_sets_flag_not_fault():
+    """A NaN in u reaches the flag word through the residual, the FP64 and FP32 tangents and the
+    matrix-free product (a non-finite force, or a state whose det F is not positive); every call
+    completes, the check reads and clears the word (JETSCI_ERR_NONFINITE from the C call), and a
+    clean input afterwards leaves it clear."""
+    J = jetsci()
+    prob = dict(PROBLEMS)["ragged_neohookean"]
+    mesh = J.Mesh.of(prob)
+    u, v = cuda(prob.u), cuda(prob.v)
+    bad = u.clone()
+    bad[7] = float("nan")
+    for call in (lambda: mesh.residual(bad), lambda: mesh.tangent_csr(bad, R=mesh.new_vector()),
+                 lambda: mesh.tangent_csr(bad, R=mesh.new_vector(), precision=J.FP32),
+                 lambda: mesh.apply_tangent(bad, v)):
+        call()
+        flags = C.c_uint32()
+        assert J.lib.jetsci_mesh_check(mesh.handle, C.byref(flags)) == 5
+        assert flags.value & (J.FLAG_NONFINITE | J.FLAG_BAD_STATE)
+        assert mesh.check() == 0  # read and cleared
+    mesh.residual(u)
+    mesh.tangent_csr(u)
+    assert mesh.check() == 0
+    mesh.close()
+
+
+def test_newton_and_cg_iteration_caps_report_not_converged():
+    """Forced caps: one Newton step, or three CG iterations per step, cannot reach 1e-10; the
+    driver returns JETSCI_ERR_NOT_CONVERGED (6) with the iterations it ran and the capped CG solves
+    counted, and leaves u finite."""
+    J = jetsci()
+    coords, conn = I.box_mesh(5, 4, 4, distort=0.15, seed=2)
+    g = np.random.default_rng(2)
+    phase = (g.uniform(size=len(conn)) < 0.4).astype(np.int32)
+    prob = I.Problem("newton_box", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                     np.zeros(coords.size), np.zeros(coords.size))
+    dofs, vals = I.roller_bcs(coords, 0.01)
+    mesh = J.Mesh.of(prob)
+    u = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(J.JetsciError) as ei:
+        J.newton_solve(mesh, u, dofs, vals, rtol=1e-10, max_newton=1, cg_rtol=1e-10)
+    assert ei.value.status == 6
+    u.zero_()
+    info = J.newton_solve(mesh, u, dofs, vals, rtol=1e-10, max_newton=3, cg_rtol=1e-10, max_cg=3,
+                          raise_on_fail=False)
+    assert info.newton_iters == 3 and info.cg_capped == 3 and info.cg_iters_total == 9
+    assert info.final_rel_residual > 1e-10
+    assert torch.isfinite(u).all()
+    mesh.close()
 
 
 @pytest.fixture(scope="module")
