@@ -47,29 +47,24 @@ def _tensor(v):
     return np.array([[v[0], v[5], v[4]], [v[5], v[1], v[3]], [v[4], v[3], v[2]]])
 
 
-def assemble(mesh: fem.Mesh, u, layers, in_scale, rng, out_scale, out_shift):
-    """Dense K (n_dof x n_dof), R (n_dof) and the number of fallback Gauss points."""
-    n_dof = mesh.n_dof
-    K = np.zeros((n_dof, n_dof))
-    R = np.zeros(n_dof)
-    recs = []
-    E6_all, ph_all = [], []
-    for e in range(mesh.n_elem):
-        en = mesh.conn[e].astype(np.int64)
-        X = mesh.coords[en]
-        ue = u[(3 * en[:, None] + np.arange(3))].reshape(8, 3)
-        for G, detJ in _geometry(X):
-            F = np.eye(3) + ue.T @ G
-            E6_all.append(_voigt(0.5 * (F.T @ F - np.eye(3))))
-            ph_all.append(int(mesh.phase[e]))
-            recs.append((e, en, G, detJ, F))
-    E6_all = np.array(E6_all)
-    ph_all = np.array(ph_all)
-    S_net, D_net = mlp.surrogate_stress(layers, E6_all, ph_all, in_scale, out_scale, out_shift)
+def element(mesh: fem.Mesh, e: int, u, layers, in_scale, rng, out_scale, out_shift):
+    """Element e: R_e [24], K_e [24, 24] (rows and columns (a, i)), the number of its Gauss
+    points that fell back to the plain law, and the strains E [8, 6] (Voigt, tensor shear)."""
+    en = mesh.conn[e].astype(np.int64)
+    X = mesh.coords[en]
+    ue = u[(3 * en[:, None] + np.arange(3))].reshape(8, 3)
+    p = int(mesh.phase[e])
+    pts = []
+    for G, detJ in _geometry(X):
+        F = np.eye(3) + ue.T @ G
+        pts.append((G, detJ, F, _voigt(0.5 * (F.T @ F - np.eye(3)))))
+    E6 = np.array([q[3] for q in pts])
+    S_net, D_net = mlp.surrogate_stress(layers, E6, np.full(8, p), in_scale, out_scale, out_shift)
+    Re = np.zeros(24)
+    Ke = np.zeros((24, 24))
     fallback = 0
-    for r, (e, en, G, detJ, F) in enumerate(recs):
-        p = ph_all[r]
-        if np.all(np.abs(E6_all[r]) <= rng):
+    for r, (G, detJ, F, _) in enumerate(pts):
+        if np.all(np.abs(E6[r]) <= rng):
             S = _tensor(S_net[r])
             D = D_net[r]
             CC = np.zeros((3, 3, 3, 3))
@@ -85,9 +80,53 @@ def assemble(mesh: fem.Mesh, u, layers, in_scale, rng, out_scale, out_shift):
             S, CC = fem.neo_hookean(lam, mu, F)
         P = F @ S
         A = np.einsum("ik,JL->iJkL", np.eye(3), S) + np.einsum("iI,IJKL,kK->iJkL", F, CC, F)
-        Re = detJ * (P @ G.T).T.ravel()  # [a, i]
-        Ke = detJ * np.einsum("aJ,iJkL,bL->aibk", G, A, G).reshape(24, 24)
+        Re += detJ * (P @ G.T).T.ravel()  # [a, i]
+        Ke += detJ * np.einsum("aJ,iJkL,bL->aibk", G, A, G).reshape(24, 24)
+    return Re, Ke, fallback, E6
+
+
+def assemble(mesh: fem.Mesh, u, layers, in_scale, rng, out_scale, out_shift):
+    """Dense K (n_dof x n_dof), R (n_dof), the number of fallback Gauss points and the strains
+    of every Gauss point (element by element)."""
+    n_dof = mesh.n_dof
+    K = np.zeros((n_dof, n_dof))
+    R = np.zeros(n_dof)
+    fallback = 0
+    E6_all = []
+    for e in range(mesh.n_elem):
+        Re, Ke, fb, E6 = element(mesh, e, u, layers, in_scale, rng, out_scale, out_shift)
+        en = mesh.conn[e].astype(np.int64)
         d = (3 * en[:, None] + np.arange(3)).ravel()
         R[d] += Re
         K[np.ix_(d, d)] += Ke
-    return K, R, fallback, E6_all
+        fallback += fb
+        E6_all.append(E6)
+    return K, R, fallback, np.concatenate(E6_all) if E6_all else np.zeros((0, 6))
+
+
+def sampled_rows(mesh: fem.Mesh, u, nodes, layers, in_scale, rng, out_scale, out_shift, adjacency=None):
+    """Rows of R and K at a sample of nodes, summed element by element over the elements around
+    each node (for meshes too big to assemble densely).  Returns dict node -> (R[3],
+    {col: K[3]}), and the strains [m, 6] and phases [m] of the Gauss points of those elements."""
+    ptr, eidx = adjacency if adjacency is not None else fem.node_elements(mesh.conn, mesh.n_nodes)
+    out, E6s, phs, cache = {}, [], [], {}
+    for n in nodes:
+        n = int(n)
+        R = np.zeros(3)
+        krow = {}
+        for e in eidx[ptr[n]:ptr[n + 1]]:
+            e = int(e)
+            if e not in cache:
+                cache[e] = element(mesh, e, u, layers, in_scale, rng, out_scale, out_shift)
+                E6s.append(cache[e][3])
+                phs.append(np.full(8, int(mesh.phase[e])))
+            Re, Ke = cache[e][0], cache[e][1]
+            en = mesh.conn[e].astype(np.int64)
+            a = int(np.where(en == n)[0][0])
+            R += Re[3 * a:3 * a + 3]
+            for b in range(8):
+                for k in range(3):
+                    c = 3 * int(en[b]) + k
+                    krow[c] = krow.get(c, np.zeros(3)) + Ke[3 * a:3 * a + 3, 3 * b + k]
+        out[n] = (R, krow)
+    return out, np.concatenate(E6s), np.concatenate(phs)

@@ -519,6 +519,38 @@ FULL_SIZE_FORMS = [("FP64", FP64_TOL, FP64_TOL, FP64_TOL), ("DF64", FP64_TOL, FP
                    ("FP32", 2e-4, 5e-5, 2e-4), ("TF32", 2e-4, 3e-3, 1e-2)]
 
 
+def test_full_size_adjoint_sampled_elements():
+    """The 64^3 lognormal adjoint workload at its full size, in the bench's launch configuration:
+    dL/dE from the kept element vectors and from the recomputing pass, FP64, on 32 sampled
+    elements against the oracle (R at each element's nodes summed element by element)."""
+    J = jetsci()
+    prob = I.lognormal_problem(64, seed=4)
+    mesh = J.Mesh.of(prob)
+    u, E = cuda(prob.u), cuda(prob.E_elem)
+    R = mesh.residual(u, E_elem=E)
+    g_kept = mesh.material_grad(None, R, E_elem=E).cpu().numpy()
+    g_rec = mesh.material_grad(u, R, E_elem=E).cpu().numpy()
+    om = oracle.Mesh.of(prob)
+    ptr, eidx = oracle.node_elements(prob.conn, prob.n_nodes)
+    sample = np.random.default_rng(7).choice(prob.n_elem, 32, replace=False)
+    g_ref = []
+    for e in sample:
+        nodes = prob.conn[e].astype(np.int64)
+        Rn = np.zeros(24)
+        for a, n in enumerate(nodes):
+            for e2 in eidx[ptr[n]:ptr[n + 1]]:
+                Re2 = oracle.element_of(om, int(e2), prob.u, tangent=False)
+                a2 = int(np.where(prob.conn[e2] == n)[0][0])
+                Rn[3 * a:3 * a + 3] += Re2[3 * a2:3 * a2 + 3]
+        Re = oracle.element_of(om, int(e), prob.u, tangent=False)
+        g_ref.append(float(Rn @ Re) / float(prob.E_elem[e]))
+    g_ref = np.array(g_ref)
+    assert relerr(g_kept[sample], g_ref) <= FP64_TOL
+    assert relerr(g_rec[sample], g_ref) <= FP64_TOL
+    assert mesh.check() == 0
+    mesh.close()
+
+
 def test_full_size_mesh_validates(full_size):
     """The 128^3 mesh's colouring, slot map (513.6 M CSR entries) and first-writer masks."""
     _, mesh, _, _ = full_size

@@ -100,3 +100,50 @@ def test_surrogate_fallback_equals_plain_law():
     assert rel(r["Kg"], r["K"]) <= 5e-5 * 4
     om = oracle.Mesh.of(prob)
     assert rel(r["R"], oracle.residual(om, prob.u)) <= 1e-13
+
+
+def test_full_size_surrogate_sampled_rows():
+    """The 128^3 fibre RVE through the fused surrogate tangent in the bench's launch
+    configuration: rows of R and of the CSR values at sampled nodes against the oracle's
+    surrogate element routine (summed element by element), within the small case's bounds
+    computed from the Gauss points of the sampled elements."""
+    prob = I.fibre_composite(128, seed=2)
+    cfg = config()
+    g = np.random.default_rng(4)
+    s = J().Surrogate([(W, g.uniform(-0.1, 0.1, b.shape)) for W, b in I.mlp_init(4)], **cfg)
+    mesh = J().Mesh.of(prob)
+    J().attach_surrogate(mesh, s)
+    u = torch.as_tensor(prob.u).cuda()
+    R = mesh.new_vector()
+    vals = mesh.tangent_csr(u, R=R, precision=J().SURROGATE)
+    assert J().surrogate_fallbacks(mesh) == 0 and mesh.check() == 0
+    rp, col = mesh.pattern(device="cpu")
+    rp, col = rp.numpy(), col.numpy()
+    Rg, vg = R.cpu().numpy(), vals.cpu().numpy().astype(np.float64)
+    layers = s.layers()
+    om = oracle.Mesh.of(prob)
+    nodes = np.concatenate([[0, prob.n_nodes - 1], np.random.default_rng(0).choice(prob.n_nodes, 10, replace=False)])
+    rows, E6, ph = surrogate_fem.sampled_rows(om, prob.u, nodes, layers, cfg["in_scale"], cfg["range_"],
+                                              cfg["out_scale"], cfg["out_shift"])
+    assert np.max(np.abs(E6)) < cfg["range_"] - 1e-5
+    x = mlp.surrogate_inputs(E6, ph, cfg["in_scale"])
+    sc = cfg["out_scale"][ph]
+    y = mlp.forward(layers, x)
+    tol_S = 4 * np.max(2 * forward_bound(layers, x) * sc) / np.max(np.abs(y * sc)) + 2e-4
+    Jm = mlp.input_jacobian(layers, x)
+    tol_D = 4 * np.max(2 * jacobian_bound(layers, x) * sc[:, :, None]) / np.max(np.abs(Jm * sc[:, :, None])) + 2e-4
+    eR = sR = eK = sK = 0.0
+    for n in nodes:
+        n = int(n)
+        Rn, krow = rows[n]
+        eR, sR = max(eR, np.max(np.abs(Rg[3 * n:3 * n + 3] - Rn))), max(sR, np.max(np.abs(Rn)))
+        for i in range(3):
+            r = 3 * n + i
+            cs = col[rp[r]:rp[r + 1]]
+            kref = np.array([krow[c][i] for c in cs])
+            eK, sK = max(eK, np.max(np.abs(vg[rp[r]:rp[r + 1]] - kref))), max(sK, np.max(np.abs(kref)))
+    assert eR / sR <= tol_S, (eR / sR, tol_S)
+    assert eK / sK <= tol_D, (eK / sK, tol_D)
+    J().attach_surrogate(mesh, None)
+    mesh.close()
+    s.close()
