@@ -645,6 +645,28 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
     err = so.errors(gather_rows(R, so.nodes), gather_vals(vals64, rp_h, so.nodes), gather_rows(y, so.nodes), rp_h,
                     col_h)
     rec("step_df64", ms, {"err_vs_oracle": err})
+
+    # The same step with FP32 element arithmetic (FP32 CSR values, matrix-free FP32 K.v from u).
+    vals32 = mesh.new_values(J.FP32)
+
+    def fp32_step():
+        mesh.tangent_csr(u, vals=vals32, R=R, precision=J.FP32, stream=stream)
+        mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals32, precision=J.FP32, stream=stream)
+        mesh.apply_tangent(u, v, y=y, precision=J.FP32, stream=stream)
+        mesh.norm2(R, out=nrm, stream=stream)
+
+    rec("step_fp32", timeit(fp32_step, stream))
+    del vals32
+    torch.cuda.empty_cache()
+
+    # The calls a surrogate step has (tangent CSR + R, CSR K.v, norm; there is no matrix-free
+    # surrogate product), in plain FP64, for a like-for-like comparison with step_surrogate.
+    def fp64_csr_step():
+        mesh.tangent_csr(u, vals=vals64, R=R, stream=stream)
+        mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals64, stream=stream)
+        mesh.norm2(R, out=nrm, stream=stream)
+
+    rec("step_fp64_csr_only", timeit(fp64_csr_step, stream))
     if not args.no_extras:
         s, tinfo = train_surrogate(J, torch, I)
         out["surrogate_training"] = tinfo
@@ -657,6 +679,14 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
         rec("tangent_csr_surrogate", ms, {"err_vs_oracle_neo_hookean": err, "fallback_gauss_points": fb,
                                           "gauss_points": 8 * prob.n_elem})
         rec("residual_surrogate", timeit(lambda: mesh.residual(u, R=R, precision=J.SURROGATE, stream=stream), stream))
+
+        def surrogate_step():
+            mesh.tangent_csr(u, vals=vv, R=R, precision=J.SURROGATE, stream=stream)
+            mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vv, precision=J.SURROGATE, stream=stream)
+            mesh.norm2(R, out=nrm, stream=stream)
+
+        ms = timeit(surrogate_step, stream)
+        rec("step_surrogate", ms, {"vs_step_fp64_csr_only": out["step_fp64_csr_only"]["ms"] / ms})
         J.attach_surrogate(mesh, None)
         del vv
         torch.cuda.empty_cache()
