@@ -609,12 +609,10 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 //   Q = (mu / det Jp) Dv adj(Jp) adj(Jp)^T + (det Jp / det j^2) M' adj(j)^T,
 //   M' = m h'^T + lam tr(h') I,  h' = Dv adj(j) = det j h.
 // kReuse (FP64 only): the neo-Hookean state comes from the mesh's linearisation store (the
-// last FP64 residual or tangent, at its u) instead of u; u is not read.  That variant asks for
-// six blocks per SM (80 registers, 16 bytes spilled): 7.93 -> 7.85 ms at 128^3 against five
-// blocks at 92 registers; seven (72 registers, 64 bytes spilled) measured 7.94 ms.
+// last FP64 residual or tangent, at its u) instead of u; u is not read.
 template <typename T, bool kReuse>
-__global__ void __launch_bounds__(128, kReuse ? 6 : 1) k_apply_mf(ElemArgs A, const double *__restrict__ u,
-                                                  const double *__restrict__ v, double *__restrict__ y) {
+__device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__restrict__ u,
+                                                 const double *__restrict__ v, double *__restrict__ y) {
     const int l = threadIdx.x & 7;
     const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const bool active = slot < A.n;
@@ -708,6 +706,23 @@ __global__ void __launch_bounds__(128, kReuse ? 6 : 1) k_apply_mf(ElemArgs A, co
 #pragma unroll
         for (int i = 0; i < 3; i++) y[3 * (int64_t)node + i] += to_double(f[i]);
     }
+}
+
+template <typename T, bool kReuse>
+__global__ void __launch_bounds__(128) k_apply_mf(ElemArgs A, const double *__restrict__ u,
+                                                  const double *__restrict__ v, double *__restrict__ y) {
+    apply_mf_element<T, kReuse>(A, u, v, y);
+}
+
+// The product at the stored linearisation asks for six blocks per SM (80 registers, 16 bytes
+// spilled): 7.93 -> 7.85 ms at 128^3 against five at 92 registers; seven (72 registers, 64
+// bytes spilled) measured 7.94 ms.  The other instantiations keep the compiler's own choice: an
+// explicit minimum of one block let it take far more registers (the FP32 product 0.90 -> 1.08 ms).
+template <>
+__global__ void __launch_bounds__(128, 6) k_apply_mf<double, true>(ElemArgs A, const double *__restrict__ u,
+                                                                   const double *__restrict__ v,
+                                                                   double *__restrict__ y) {
+    apply_mf_element<double, true>(A, u, v, y);
 }
 
 // ---------------------------------------------------------------------------- adjoint
