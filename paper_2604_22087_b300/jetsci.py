@@ -257,7 +257,11 @@ def version():
 class MaterialGrad(torch.autograd.Function):
     """L(E) = 1/2 ||R(u; E)||^2 with dL/dE from the library's adjoint kernel.
 
-    forward(mesh, u, E, precision) -> L (0-dim float64 CUDA tensor)."""
+    forward(mesh, u, E, precision) -> L (0-dim float64 CUDA tensor).  The backward pass uses the
+    element vectors its forward residual kept when no other residual call given E_elem went
+    through Mesh.residual on the same mesh in between, and recomputes them from u otherwise.
+    Residual calls made on the mesh's handle directly through the C ABI are not seen: mix them
+    with this Function only when each backward follows its own forward."""
 
     @staticmethod
     def forward(ctx, E, mesh, u, precision=FP64):
