@@ -441,3 +441,30 @@ def test_surrogate_oracle_tangent_is_fd_of_its_residual():
     for r in range(len(Kref)):
         Kref[r, col[rp[r]:rp[r + 1]]] = vals[rp[r]:rp[r + 1]]
     assert rel(R0, Rref) < 1e-13 and rel(K0, Kref) < 1e-13
+
+
+def test_surrogate_oracle_sampled_rows_equal_its_dense_assembly():
+    """The element-by-element rows at sampled nodes (used at sizes the dense assembly cannot
+    reach) are the rows of the dense assembly exactly, on a distorted two-phase box; the
+    strains and phases returned are those of the elements around the sampled nodes."""
+    from oracle import surrogate_fem
+    coords, conn = I.box_mesh(3, 2, 2, distort=0.2, seed=6)
+    g = np.random.default_rng(6)
+    phase = (g.uniform(size=len(conn)) < 0.5).astype(np.int32)
+    M = oracle.Mesh(coords, conn, phase, I.composite_materials(NH))
+    layers = _tiny_layers(11)
+    sc = np.array([[2e8] * 6, [3e9] * 6]); sh = np.zeros((2, 6))
+    u = g.uniform(-3e-3, 3e-3, coords.size)
+    K, R, fb, E6 = surrogate_fem.assemble(M, u, layers, 0.05, 0.05, sc, sh)
+    nodes = np.array([0, 5, len(coords) - 1])
+    rows, E6s, phs = surrogate_fem.sampled_rows(M, u, nodes, layers, 0.05, 0.05, sc, sh)
+    for n in nodes:
+        Rn, krow = rows[int(n)]
+        assert np.array_equal(Rn, R[3 * n:3 * n + 3])
+        assert set(krow) == set(np.nonzero(np.any(K[3 * n:3 * n + 3] != 0, axis=0))[0])
+        for c, col in krow.items():
+            assert np.array_equal(col, K[3 * n:3 * n + 3, c])
+    ptr, eidx = oracle.node_elements(conn, len(coords))
+    around = sorted({int(e) for n in nodes for e in eidx[ptr[n]:ptr[n + 1]]})
+    assert E6s.shape == (8 * len(around), 6) and phs.shape == (8 * len(around),)
+    assert set(phs.tolist()) <= {0, 1}
