@@ -52,3 +52,15 @@ def test_product_library_has_no_oracle_symbols(J):
     assert "or_element" not in out and "or_residual" not in out
     syms = set(re.findall(r"\b(jetsci_\w+)\b", out))
     assert set(declared_functions()) <= syms
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/jetsci.h compiles as ISO C99 (pedantic, all warnings as errors) and as C++: the
+    boundary needs no C++ or CUDA types from its callers."""
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "jetsci.h"\nint main(void) { return (int)sizeof(jetsci_material); }\n')
+    inc = os.path.join(ROOT, "include")
+    for cmd in (["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                ["g++", "-std=c++11", "-Wall", "-Werror", "-fsyntax-only", "-x", "c++", "-I", inc, str(src)]):
+        out = subprocess.run(cmd, capture_output=True, text=True)
+        assert out.returncode == 0, out.stderr
