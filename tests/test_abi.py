@@ -64,3 +64,32 @@ def test_header_is_plain_c(tmp_path):
                 ["g++", "-std=c++11", "-Wall", "-Werror", "-fsyntax-only", "-x", "c++", "-I", inc, str(src)]):
         out = subprocess.run(cmd, capture_output=True, text=True)
         assert out.returncode == 0, out.stderr
+
+
+def test_plain_c_program_links_and_calls_the_library(J, tmp_path):
+    """A C99 program linked against libjetsci.so calls the host-only entry points without a GPU:
+    the version string, destroy(NULL) as a no-op, and argument validation of mesh creation
+    (JETSCI_ERR_ARG with a message), so the boundary needs neither Python nor torch."""
+    src = tmp_path / "use_lib.c"
+    src.write_text(r'''#include <stdio.h>
+#include <string.h>
+#include "jetsci.h"
+int main(void) {
+    const char *v = jetsci_version();
+    if (!v || !strstr(v, "sm_103a")) return 1;
+    if (jetsci_mesh_destroy(NULL) != JETSCI_OK) return 2;
+    double xyz[3] = {0, 0, 0};
+    if (jetsci_mesh_create(xyz, 1, NULL, 0, NULL, NULL, 0, NULL, NULL) != JETSCI_ERR_ARG) return 3;
+    if (strlen(jetsci_last_error()) == 0) return 4;
+    return 0;
+}
+''')
+    libdir = os.path.dirname(J.LIB_PATH)
+    exe = tmp_path / "use_lib"
+    cuda_lib = "/usr/local/cuda/lib64"
+    out = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                          "-L" + libdir, "-ljetsci", "-Wl,-rpath," + libdir, "-L" + cuda_lib, "-Wl,-rpath," + cuda_lib,
+                          "-o", str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, (run.returncode, run.stderr)
