@@ -1,12 +1,21 @@
 """MLP surrogate on the GPU (tensor-core BF16 kernels) against the FP64 MLP oracle.
 
-Tolerance for network outputs (derived from the arithmetic, not fitted): the kernels round
-inputs, weights and every stored activation / tangent tile to BF16 (unit roundoff
-u = 2^-9) and accumulate in FP32 (error negligible against u).  A first-order
-absolute-value propagation of those roundings through the network, evaluated in FP64 from
-the oracle's own forward pass, bounds |y_gpu - y_exact| per sample and output; the tests
-assert the GPU result lies within twice that bound (factor 2 for second-order terms and
-SiLU evaluated with the hardware exponential).
+Tolerance for network outputs (derived from the arithmetic, not fitted).  The kernels round
+the inputs, the weights and every stored activation / tangent tile to BF16 (8 significant
+bits: unit roundoff u = 2^-8) and accumulate in FP32 (error negligible against u); biases,
+the SiLU evaluation and the first tangent seed W1 are FP32.  Two first-order propagations of
+those roundings through the network are evaluated in FP64 from the oracle's own forward pass:
+
+* worst case: every rounding at its bound u|t| with the signs aligned (absolute values);
+* probabilistic: every rounding an independent zero-mean error of variance at most u^2 t^2 / 3
+  (round to nearest errs by at most half an ulp, <= u|t|, modelled as uniform), variances
+  added through the layers (the sqrt(n) growth of probabilistic rounding-error analysis, as
+  opposed to the n growth of the worst case; where two error terms share sources their
+  variances are added with a factor 2, the bound for correlated terms).
+
+The tests allow min(6 sigma, worst case) per sample and entry.  For networks of 64-wide layers
+the worst case grows like (sum |W|)^layers and exceeds the outputs themselves; the 6-sigma
+bound is the informative one.
 """
 import numpy as np
 import pytest
@@ -17,7 +26,8 @@ from oracle import mlp
 from paper_2604_22087_b300 import inputs as I
 
 pytestmark = pytest.mark.gpu
-U = 2.0 ** -9
+U = 2.0 ** -8  # BF16 unit roundoff (8 significant bits)
+K_SIGMA = 6.0
 
 
 def J():
@@ -31,45 +41,97 @@ def config(range_=0.05):
     return dict(in_scale=range_, range_=range_, out_scale=sc, out_shift=np.zeros((2, 6)))
 
 
-def silu_pp_bound():
-    return 0.5  # |silu''| <= 0.5 everywhere
+def silu_pp(z):
+    """silu''(z) = s (1 - s) (2 + z (1 - 2 s)), s = sigmoid(z); |silu''| <= 0.5."""
+    s = mlp.sigmoid(z)
+    return s * (1.0 - s) * (2.0 + z * (1.0 - 2.0 * s))
 
 
 def forward_bound(layers, x):
-    """First-order bound on |y_bf16 - y| (and on the tangent rows) from BF16 roundings."""
+    """Worst-case first-order bound on |y_bf16 - y| per sample and output."""
     _, zs, acts = mlp.forward(layers, x, keep=True)
     absW = [np.abs(W) for W, _ in layers]
     da = U * np.abs(x)
     for li in range(3):
-        dz = da @ absW[li].T + 2 * U * (np.abs(acts[li]) @ absW[li].T)
-        da = 1.1 * dz + U * np.abs(acts[li + 1])
-    dy = da @ absW[3].T + 2 * U * (np.abs(acts[3]) @ absW[3].T)
-    return dy
+        dz = da @ absW[li].T + U * (np.abs(acts[li]) @ absW[li].T)
+        da = np.abs(mlp.silu_prime(zs[li])) * dz + U * np.abs(acts[li + 1])
+    return da @ absW[3].T + U * (np.abs(acts[3]) @ absW[3].T)
+
+
+def forward_sigma(layers, x):
+    """Standard deviation of y_bf16 - y per sample and output under independent roundings."""
+    _, zs, acts = mlp.forward(layers, x, keep=True)
+    W2 = [W * W for W, _ in layers]
+    r = U * U / 3.0
+    va = r * x * x
+    for li in range(3):
+        vz = va @ W2[li].T + r * ((acts[li] ** 2) @ W2[li].T)
+        va = mlp.silu_prime(zs[li]) ** 2 * vz + r * acts[li + 1] ** 2
+    return np.sqrt(va @ W2[3].T + r * ((acts[3] ** 2) @ W2[3].T))
+
+
+def _zsigma(layers, x):
+    """Variances of the errors of z_1..z_3 (for the silu' factors of the tangent pass)."""
+    _, zs, acts = mlp.forward(layers, x, keep=True)
+    W2 = [W * W for W, _ in layers]
+    r = U * U / 3.0
+    va = r * x * x
+    out = []
+    for li in range(3):
+        vz = va @ W2[li].T + r * ((acts[li] ** 2) @ W2[li].T)
+        out.append(vz)
+        va = mlp.silu_prime(zs[li]) ** 2 * vz + r * acts[li + 1] ** 2
+    return zs, out
 
 
 def jacobian_bound(layers, x):
-    """First-order bound on the input-Jacobian rows (per sample, output, direction)."""
+    """Worst-case first-order bound on the input-Jacobian rows (per sample, output, direction)."""
     _, zs, acts = mlp.forward(layers, x, keep=True)
     absW = [np.abs(W) for W, _ in layers]
-    n = x.shape[0]
-    # forward-pass errors of z_l (for the silu' factor)
     da = U * np.abs(x)
     dzs = []
     for li in range(3):
-        dz = da @ absW[li].T + 2 * U * (np.abs(acts[li]) @ absW[li].T)
+        dz = da @ absW[li].T + U * (np.abs(acts[li]) @ absW[li].T)
         dzs.append(dz)
-        da = 1.1 * dz + U * np.abs(acts[li + 1])
+        da = np.abs(mlp.silu_prime(zs[li])) * dz + U * np.abs(acts[li + 1])
     W1 = layers[0][0][:, :6]
     T = mlp.silu_prime(zs[0])[:, :, None] * W1[None]            # [n, 64, 6]
-    dT = (silu_pp_bound() * dzs[0])[:, :, None] * np.abs(W1)[None] + 2 * U * np.abs(T)
+    dT = (np.abs(silu_pp(zs[0])) * dzs[0])[:, :, None] * np.abs(W1)[None] + U * np.abs(T)
     for li in (1, 2):
         W = layers[li][0]
         V = np.einsum("oh,nhd->nod", W, T)
-        dV = np.einsum("oh,nhd->nod", absW[li], dT) + 2 * U * np.einsum("oh,nhd->nod", absW[li], np.abs(T))
+        dV = np.einsum("oh,nhd->nod", absW[li], dT) + U * np.einsum("oh,nhd->nod", absW[li], np.abs(T))
         sp = mlp.silu_prime(zs[li])[:, :, None]
         T = sp * V
-        dT = np.abs(sp) * dV + (silu_pp_bound() * dzs[li])[:, :, None] * np.abs(V) + U * np.abs(T)
-    return np.einsum("oh,nhd->nod", absW[3], dT) + 2 * U * np.einsum("oh,nhd->nod", absW[3], np.abs(T))
+        dT = np.abs(sp) * dV + (np.abs(silu_pp(zs[li])) * dzs[li])[:, :, None] * np.abs(V) + U * np.abs(T)
+    return np.einsum("oh,nhd->nod", absW[3], dT) + U * np.einsum("oh,nhd->nod", absW[3], np.abs(T))
+
+
+def jacobian_sigma(layers, x):
+    """Standard deviation of the input-Jacobian error under independent roundings."""
+    zs, vzs = _zsigma(layers, x)
+    W2 = [W * W for W, _ in layers]
+    r = U * U / 3.0
+    W1 = layers[0][0][:, :6]
+    T = mlp.silu_prime(zs[0])[:, :, None] * W1[None]
+    # T1 = silu'(z1) W1 (FP32 seed), rounded to BF16; silu'(z1) carries z1's error
+    vT = (silu_pp(zs[0]) ** 2 * vzs[0])[:, :, None] * (W1 * W1)[None] + r * T * T
+    for li in (1, 2):
+        W = layers[li][0]
+        V = np.einsum("oh,nhd->nod", W, T)
+        vV = np.einsum("oh,nhd->nod", W2[li], vT) + r * np.einsum("oh,nhd->nod", W2[li], T * T)
+        sp = mlp.silu_prime(zs[li])[:, :, None]
+        T = sp * V
+        # the two terms share error sources: variances added with a factor 2
+        vT = 2.0 * (sp * sp * vV + (silu_pp(zs[li]) ** 2 * vzs[li])[:, :, None] * V * V) + r * T * T
+    return np.sqrt(np.einsum("oh,nhd->nod", W2[3], vT) + r * np.einsum("oh,nhd->nod", W2[3], T * T))
+
+
+def output_bounds(layers, x):
+    """(|dy| bound [n, 6], |dJ| bound [n, 6, 6]): min(6 sigma, worst case) per entry."""
+    by = np.minimum(K_SIGMA * forward_sigma(layers, x), forward_bound(layers, x))
+    bJ = np.minimum(K_SIGMA * jacobian_sigma(layers, x), jacobian_bound(layers, x))
+    return by, bJ
 
 
 def nh_stress_oracle(E6, phase):
@@ -114,15 +176,17 @@ def test_eval_and_input_jacobian_within_bf16_bound(data):
     y_ref = mlp.forward(layers, x)
     sc = cfg["out_scale"][ph]
     y_gpu = S / sc
-    bound = forward_bound(layers, x)
-    assert np.all(np.abs(y_gpu - y_ref) <= 2 * bound + 1e-6)
+    bound, jb = output_bounds(layers, x)
+    # the bounds are informative: well below the outputs they bound
+    assert np.max(bound) <= 0.05 * np.max(np.abs(y_ref))
+    assert np.all(np.abs(y_gpu - y_ref) <= bound + 1e-6)
     Jm_ref = mlp.input_jacobian(layers, x)
     Jm_gpu = D * cfg["in_scale"] / sc[:, :, None]
-    jb = jacobian_bound(layers, x)
-    assert np.all(np.abs(Jm_gpu - Jm_ref) <= 2 * jb + 1e-6)
+    assert np.max(jb) <= 0.05 * np.max(np.abs(Jm_ref))
+    assert np.all(np.abs(Jm_gpu - Jm_ref) <= jb + 1e-6)
     # and the oracle's own surrogate map agrees on S and D up to the same bounds
     S_o, D_o = mlp.surrogate_stress(layers, E6, ph, cfg["in_scale"], cfg["out_scale"], cfg["out_shift"])
-    assert np.all(np.abs(S - S_o) <= (2 * bound + 1e-6) * sc)
+    assert np.all(np.abs(S - S_o) <= (bound + 1e-6) * sc)
 
 
 def test_minibatch_gradient_matches_oracle_reverse_mode(data):

@@ -1,12 +1,16 @@
 """Residual and tangent with the MLP surrogate fused into the element kernel, against the
 FP64 oracle (FP64 network and element arithmetic, same weights).
 
-Tolerances: the network's BF16 error bound (first-order propagation of the u = 2^-9
-roundings, computed from the oracle's forward pass as in test_gpu_surrogate.py) relative to
-the largest stress / tangent entry, times 4 for the assembly sums, plus the FP32 element
-arithmetic bound 2e-4 used for the FP32 path.  Gauss points whose strain lies within 1e-5
-of the range boundary could be decided differently in FP32 and FP64; the test inputs keep
-every point away from that band and the test asserts it.
+Tolerances, entry by entry, derived from the arithmetic: at every Gauss point inside the
+training range the network's stress and tangent carry the BF16 rounding bound of
+test_gpu_surrogate.py (min(6 sigma, worst case) of the propagated roundings, per output and
+direction); R and K are linear in S and in the elasticity tensor built from dS/dE, so the
+point bounds propagate exactly through R_e(a,i) = sum_q w detJ (F S)_iJ G_aJ and
+K_e = sum_q w detJ G (1 x S + F CC F) G with absolute values, and are summed over the points and
+elements of each entry.  To that the FP32 element arithmetic adds its normwise bound 2e-4
+(as for the FP32 path).  Gauss points whose strain lies within 1e-5 of the range boundary
+could be decided differently in FP32 and FP64; the test inputs keep every point away from
+that band and the tests assert it.
 """
 import numpy as np
 import pytest
@@ -16,7 +20,7 @@ import oracle
 from oracle import mlp, surrogate_fem
 from paper_2604_22087_b300 import inputs as I
 
-from test_gpu_surrogate import config, forward_bound, jacobian_bound
+from test_gpu_surrogate import config, output_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +69,71 @@ def _run(prob, layers_seed, rng):
                 layers=layers, cfg=cfg)
 
 
+def _element_bounds(om, e, u, layers, cfg, rng):
+    """Absolute bounds (R_e [24], K_e [24, 24], rows and columns (a, i)) on the network part of
+    the error of element e: the per-point bounds on S and dS/dE of its in-range Gauss points
+    pushed through the residual and tangent definitions with absolute values."""
+    en = om.conn[e].astype(np.int64)
+    ue = u[(3 * en[:, None] + np.arange(3))].reshape(8, 3)
+    geo = surrogate_fem._geometry(om.coords[en])
+    Fs = [np.eye(3) + ue.T @ G for G, _ in geo]
+    E6 = np.array([[(0.5 * (F.T @ F - np.eye(3)))[i, j] for i, j in surrogate_fem.VOIGT] for F in Fs])
+    inside = np.all(np.abs(E6) <= rng, axis=1)
+    bR, bK = np.zeros(24), np.zeros((24, 24))
+    if not inside.any():
+        return bR, bK
+    ph = np.full(8, int(om.phase[e]))
+    by, bJ = output_bounds(layers, mlp.surrogate_inputs(E6, ph, cfg["in_scale"]))
+    sc = cfg["out_scale"][ph]
+    dS, dD = by * sc, bJ * sc[:, :, None] / cfg["in_scale"]
+    for q, ((G, detJ), F) in enumerate(zip(geo, Fs)):
+        if not inside[q]:
+            continue
+        aS = np.abs(surrogate_fem._tensor(dS[q]))
+        aC = np.zeros((3, 3, 3, 3))
+        for a, (I_, J_) in enumerate(surrogate_fem.VOIGT):
+            for b, (K_, L_) in enumerate(surrogate_fem.VOIGT):
+                v = dD[q, a, b] if K_ == L_ else 0.5 * dD[q, a, b]
+                for (i1, j1) in {(I_, J_), (J_, I_)}:
+                    for (k1, l1) in {(K_, L_), (L_, K_)}:
+                        aC[i1, j1, k1, l1] = v
+        aF, aG = np.abs(F), np.abs(G)
+        bR += detJ * ((aF @ aS) @ aG.T).T.ravel()
+        A = np.einsum("ik,JL->iJkL", np.eye(3), aS) + np.einsum("iI,IJKL,kK->iJkL", aF, aC, aF)
+        bK += detJ * np.einsum("aJ,iJkL,bL->aibk", aG, A, aG).reshape(24, 24)
+    return bR, bK
+
+
+def _assembled_bounds(om, u, layers, cfg, rng):
+    """The element bounds summed into the global residual and the dense matrix."""
+    bR, bK = np.zeros(om.n_dof), np.zeros((om.n_dof, om.n_dof))
+    for e in range(om.n_elem):
+        r, k = _element_bounds(om, e, u, layers, cfg, rng)
+        d = (3 * om.conn[e].astype(np.int64)[:, None] + np.arange(3)).ravel()
+        bR[d] += r
+        bK[np.ix_(d, d)] += k
+    return bR, bK
+
+
+def _check_within(r, prob, rng):
+    """Entry-wise: |GPU - oracle| <= network bound + FP32 bound; returns the bounds' largest
+    share of the largest entry (to show they are informative)."""
+    om = oracle.Mesh.of(prob)
+    bR, bK = _assembled_bounds(om, prob.u, r["layers"], r["cfg"], rng)
+    sR, sK = np.max(np.abs(r["R"])), np.max(np.abs(r["K"]))
+    eR, eK = np.abs(r["Rg"] - r["R"]), np.abs(r["Kg"] - r["K"])
+    assert np.all(eR <= bR + 2e-4 * sR), float(np.max(eR / (bR + 2e-4 * sR)))
+    assert np.all(eK <= bK + 2e-4 * sK), float(np.max(eK / (bK + 2e-4 * sK)))
+    return float(np.max(bR) / sR), float(np.max(bK) / sK)
+
+
+# Regression guards, normwise, at about ten times the errors measured on B300 for these cases
+# (all points in range: R 4.6e-3, K 2.3e-3; half the points falling back: R 8.3e-4, K 1.0e-4;
+# all falling back: R 2.6e-6, K 1.6e-7).  The entry-wise bounds above hold with room; these catch
+# a regression inside them.
+GUARD = {"inrange": (5e-2, 2.5e-2), "mixed": (1e-2, 1e-3), "fallback": (3e-5, 2e-6)}
+
+
 def rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
@@ -75,17 +144,10 @@ def test_surrogate_tangent_and_residual_vs_oracle():
     # every point inside the range and away from its boundary
     assert np.max(np.abs(r["E6"])) < 0.05 - 1e-5
     assert r["nfb"] == 0 and r["fb"] == 0
-    cfg = r["cfg"]
-    ph = np.repeat(prob.phase, 8)
-    x = mlp.surrogate_inputs(r["E6"], ph, cfg["in_scale"])
-    sc = cfg["out_scale"][ph]
-    y = mlp.forward(r["layers"], x)
-    tol_S = 4 * np.max(2 * forward_bound(r["layers"], x) * sc) / np.max(np.abs(y * sc)) + 2e-4
-    Jm = mlp.input_jacobian(r["layers"], x)
-    tol_D = 4 * np.max(2 * jacobian_bound(r["layers"], x) * sc[:, :, None]) / np.max(np.abs(Jm * sc[:, :, None])) + 2e-4
-    assert rel(r["Rg"], r["R"]) <= tol_S, (rel(r["Rg"], r["R"]), tol_S)
+    share_R, share_K = _check_within(r, prob, 0.05)
+    assert share_R <= 0.25 and share_K <= 0.25  # the bounds say something
+    assert rel(r["Rg"], r["R"]) <= GUARD["inrange"][0] and rel(r["Kg"], r["K"]) <= GUARD["inrange"][1]
     assert np.array_equal(r["Rg"], r["R2"])
-    assert rel(r["Kg"], r["K"]) <= tol_D, (rel(r["Kg"], r["K"]), tol_D)
     # the surrogate tangent is not symmetric in general, and the kernel keeps that
     assert np.max(np.abs(r["Kg"] - r["Kg"].T)) > 0
 
@@ -96,8 +158,8 @@ def test_surrogate_fallback_equals_plain_law():
     r = _run(prob, 7, 1e-9)
     n_q = 8 * prob.n_elem
     assert r["nfb"] == n_q and r["fb"] == n_q
-    assert rel(r["Rg"], r["R"]) <= 2e-4
-    assert rel(r["Kg"], r["K"]) <= 5e-5 * 4
+    assert rel(r["Rg"], r["R"]) <= min(2e-4, GUARD["fallback"][0])
+    assert rel(r["Kg"], r["K"]) <= min(5e-5 * 4, GUARD["fallback"][1])
     om = oracle.Mesh.of(prob)
     assert rel(r["R"], oracle.residual(om, prob.u)) <= 1e-13
 
@@ -126,24 +188,79 @@ def test_full_size_surrogate_sampled_rows():
     rows, E6, ph = surrogate_fem.sampled_rows(om, prob.u, nodes, layers, cfg["in_scale"], cfg["range_"],
                                               cfg["out_scale"], cfg["out_shift"])
     assert np.max(np.abs(E6)) < cfg["range_"] - 1e-5
-    x = mlp.surrogate_inputs(E6, ph, cfg["in_scale"])
-    sc = cfg["out_scale"][ph]
-    y = mlp.forward(layers, x)
-    tol_S = 4 * np.max(2 * forward_bound(layers, x) * sc) / np.max(np.abs(y * sc)) + 2e-4
-    Jm = mlp.input_jacobian(layers, x)
-    tol_D = 4 * np.max(2 * jacobian_bound(layers, x) * sc[:, :, None]) / np.max(np.abs(Jm * sc[:, :, None])) + 2e-4
-    eR = sR = eK = sK = 0.0
+    ptr, eidx = oracle.node_elements(prob.conn, prob.n_nodes)
+    eb = {}
+    sR = max(np.max(np.abs(rows[int(n)][0])) for n in nodes)
+    sK = max(np.max(np.abs(list(rows[int(n)][1].values()))) for n in nodes)
     for n in nodes:
         n = int(n)
         Rn, krow = rows[n]
-        eR, sR = max(eR, np.max(np.abs(Rg[3 * n:3 * n + 3] - Rn))), max(sR, np.max(np.abs(Rn)))
+        bRn, bkrow = np.zeros(3), {}
+        for e in eidx[ptr[n]:ptr[n + 1]]:
+            e = int(e)
+            if e not in eb:
+                eb[e] = _element_bounds(om, e, prob.u, layers, cfg, cfg["range_"])
+            en = prob.conn[e].astype(np.int64)
+            a = int(np.where(en == n)[0][0])
+            bRn += eb[e][0][3 * a:3 * a + 3]
+            for b in range(8):
+                for k in range(3):
+                    c = 3 * int(en[b]) + k
+                    bkrow[c] = bkrow.get(c, np.zeros(3)) + eb[e][1][3 * a:3 * a + 3, 3 * b + k]
+        assert np.all(np.abs(Rg[3 * n:3 * n + 3] - Rn) <= bRn + 2e-4 * sR)
         for i in range(3):
             r = 3 * n + i
             cs = col[rp[r]:rp[r + 1]]
             kref = np.array([krow[c][i] for c in cs])
-            eK, sK = max(eK, np.max(np.abs(vg[rp[r]:rp[r + 1]] - kref))), max(sK, np.max(np.abs(kref)))
-    assert eR / sR <= tol_S, (eR / sR, tol_S)
-    assert eK / sK <= tol_D, (eK / sK, tol_D)
+            kb = np.array([bkrow[c][i] for c in cs])
+            assert np.all(np.abs(vg[rp[r]:rp[r + 1]] - kref) <= kb + 2e-4 * sK)
     J().attach_surrogate(mesh, None)
     mesh.close()
     s.close()
+
+
+def _split_range(E6, band=1e-5):
+    """A strain range that splits the Gauss points near the median of max_ij |E_ij|, at the
+    midpoint of a gap of at least 2 * band between consecutive point maxima, so that no point
+    lies within `band` of it (FP32 and FP64 then take the same in/out decision)."""
+    m = np.sort(np.max(np.abs(E6), axis=1))
+    n = len(m)
+    for d in range(n // 2):
+        for k in (n // 2 - d, n // 2 + d):
+            if 0 < k < n and m[k] - m[k - 1] >= 2 * band:
+                return 0.5 * (m[k] + m[k - 1])
+    raise AssertionError("no gap in the strain maxima")
+
+
+def test_surrogate_mixed_in_range_and_fallback_points():
+    """Gauss points inside and outside the training range in the same elements and in the same
+    128-point tensor-core tiles: the in-range points take S and dS/dE from the network, the
+    others from the plain neo-Hookean law, point by point (the fallback of the surrogate
+    model, Section III-B's remark on learned material laws).  The range is set at a gap in
+    the points' strain maxima near their median, so about half the points fall back, none
+    within 1e-5 of the boundary.  R and K against the oracle's surrogate element routine
+    (the same per-point choice in FP64), and the fallback count equal to the oracle's."""
+    prob = _problem(11)
+    om = oracle.Mesh.of(prob)
+    cfg0 = config()
+    E6 = np.concatenate([surrogate_fem.element(om, e, prob.u, [(W, b) for W, b in I.mlp_init(4)], cfg0["in_scale"],
+                                               1.0, cfg0["out_scale"], cfg0["out_shift"])[3]
+                         for e in range(prob.n_elem)])
+    rng = _split_range(E6)
+    r = _run(prob, 4, rng)
+    n_q = 8 * prob.n_elem
+    inside = np.all(np.abs(r["E6"]) <= rng, axis=1)
+    assert np.min(np.abs(np.max(np.abs(r["E6"]), axis=1) - rng)) >= 1e-5
+    assert 0 < r["nfb"] < n_q and r["nfb"] == r["fb"] == int(np.sum(~inside))
+    per_elem = inside.reshape(prob.n_elem, 8).sum(axis=1)
+    assert np.sum((per_elem > 0) & (per_elem < 8)) >= prob.n_elem // 4  # mixed elements
+    # the 128-point tiles (16 elements each) hold both kinds
+    for t0 in range(0, n_q - 127, 128):
+        assert 0 < np.sum(inside[t0:t0 + 128]) < 128
+    share_R, share_K = _check_within(r, prob, rng)
+    assert share_R <= 0.25 and share_K <= 0.25
+    assert rel(r["Rg"], r["R"]) <= GUARD["mixed"][0] and rel(r["Kg"], r["K"]) <= GUARD["mixed"][1]
+    assert np.array_equal(r["Rg"], r["R2"])
+    # the plain law alone at the same state is far from the mixed result (both kinds matter)
+    om_R = oracle.residual(om, prob.u)
+    assert rel(r["R"], om_R) > 10 * (share_R + 2e-4)
