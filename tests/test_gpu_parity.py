@@ -21,6 +21,15 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 
+# Regression guards at about ten times the errors measured on B300 (largest over the 16^3 sphere
+# RVE linear and stretched, the ragged box and the high-valence mesh): FP32 CSR values 2.0e-7,
+# R 5.5e-6, matrix-free K.v 8.9e-8, CSR K.v 2.0e-7; TF32 CSR values 1.15e-4, K.v 8.4e-5.  The
+# derived bounds are worst cases two orders above these; the guards catch a regression that
+# would stay inside them.  At 128^3 the measured errors are lower still (FP32 R 1.5e-6, values
+# 1.2e-7, K.v 5.2e-8; TF32 values 4.1e-5, K.v 6.9e-5).
+GUARD = {"FP32": dict(vals=2e-6, R=6e-5, ymf=1e-6, ycsr=2e-6),
+         "TF32": dict(vals=1.2e-3, R=6e-5, ymf=1e-3, ycsr=1e-3)}
+
 
 def jetsci():
     from paper_2604_22087_b300 import jetsci as J
@@ -200,17 +209,18 @@ def test_fp32_bounds(case):
     prob, mesh, _, ref = case
     J = jetsci()
     u = cuda(prob.u)
+    g = GUARD["FP32"]
     R = mesh.residual(u, precision=J.FP32)
-    assert relerr(R.cpu().numpy(), ref["R"]) <= 2e-4
+    assert relerr(R.cpu().numpy(), ref["R"]) <= min(2e-4, g["R"])
     R2 = mesh.new_vector()
     vals = mesh.tangent_csr(u, R=R2, precision=J.FP32)
     assert vals.dtype == torch.float32
-    assert relerr(vals.cpu().numpy(), ref["vals"]) <= 5e-5
-    assert relerr(R2.cpu().numpy(), ref["R"]) <= 2e-4
+    assert relerr(vals.cpu().numpy(), ref["vals"]) <= min(5e-5, g["vals"])
+    assert relerr(R2.cpu().numpy(), ref["R"]) <= min(2e-4, g["R"])
     y = mesh.apply_tangent(u, cuda(prob.v), precision=J.FP32)
-    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= 2e-4
+    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= min(2e-4, g["ymf"])
     yc = mesh.apply_tangent(None, cuda(prob.v), mode=J.CSR, vals=vals, precision=J.FP32)
-    assert relerr(yc.cpu().numpy(), ref["y_csr"]) <= 2e-4
+    assert relerr(yc.cpu().numpy(), ref["y_csr"]) <= min(2e-4, g["ycsr"])
 
 
 def test_bitwise_determinism(case):
@@ -389,7 +399,8 @@ def test_high_valence_node_and_isolated_node(name):
     vals = mesh.new_values(p)
     vals.fill_(float("nan"))
     mesh.tangent_csr(u, vals=vals, R=R, precision=p)
-    tol_v, tol_r = {"FP64": (FP64_TOL, FP64_TOL), "FP32": (5e-5, 2e-4), "TF32": (3e-3, 2e-4)}[name]
+    tol_v, tol_r = {"FP64": (FP64_TOL, FP64_TOL), "FP32": (GUARD["FP32"]["vals"], GUARD["FP32"]["R"]),
+                    "TF32": (GUARD["TF32"]["vals"], GUARD["TF32"]["R"])}[name]
     assert relerr(vals.cpu().numpy(), vals_ref) <= tol_v
     assert relerr(R.cpu().numpy(), R_ref) <= tol_r
     assert torch.count_nonzero(R[-3:]).item() == 0
@@ -513,10 +524,11 @@ def full_size():
     mesh.close()
 
 
-# (precision name, tolerance of R, of CSR values, of K.v), normwise over the sampled rows; the
-# FP32/TF32 bounds are those of the small-case tests (derivations there).
+# (precision name, tolerance of R, of CSR values, of K.v), normwise over the sampled rows; FP32
+# and TF32 at the regression guards of the small cases (tighter than their derived bounds).
 FULL_SIZE_FORMS = [("FP64", FP64_TOL, FP64_TOL, FP64_TOL), ("DF64", FP64_TOL, FP64_TOL, FP64_TOL),
-                   ("FP32", 2e-4, 5e-5, 2e-4), ("TF32", 2e-4, 3e-3, 1e-2)]
+                   ("FP32", GUARD["FP32"]["R"], GUARD["FP32"]["vals"], GUARD["FP32"]["ycsr"]),
+                   ("TF32", GUARD["TF32"]["R"], GUARD["TF32"]["vals"], GUARD["TF32"]["ycsr"])]
 
 
 def test_full_size_adjoint_sampled_elements():
@@ -600,11 +612,14 @@ def test_tf32_tensor_core_bounds(case):
     J = jetsci()
     u = cuda(prob.u)
     R = mesh.new_vector()
+    g = GUARD["TF32"]
     vals = mesh.tangent_csr(u, R=R, precision=J.TF32)
-    assert relerr(vals.cpu().numpy(), ref["vals"]) <= 3e-3
-    assert relerr(R.cpu().numpy(), ref["R"]) <= 2e-4
+    assert relerr(vals.cpu().numpy(), ref["vals"]) <= min(3e-3, g["vals"])
+    assert relerr(R.cpu().numpy(), ref["R"]) <= min(2e-4, g["R"])
     y = mesh.apply_tangent(u, cuda(prob.v), precision=J.TF32)
-    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= 1e-2
+    assert relerr(y.cpu().numpy(), ref["y_mf"]) <= min(1e-2, g["ymf"])
+    yc = mesh.apply_tangent(None, cuda(prob.v), mode=J.CSR, vals=vals, precision=J.TF32)
+    assert relerr(yc.cpu().numpy(), ref["y_csr"]) <= min(1e-2, g["ycsr"])
     assert mesh.check() == 0
 
 
@@ -680,3 +695,41 @@ def test_df64_material_gradient():
     assert relerr(R.cpu().numpy(), R_ref) <= FP64_TOL
     g = mesh.material_grad(u, R, E_elem=E, precision=J.DF64)
     assert relerr(g.cpu().numpy(), oracle.material_grad(om, prob.u, R_ref)) <= FP64_TOL
+
+
+def test_full_size_adjoint_central_differences():
+    """dL/dE on the 64^3 lognormal workload against central differences of L = 1/2 ||R(u; E)||^2
+    taken through the library's own residual and norm (the calibration gradient of the
+    Introduction, checked as the adjoint-exactness pin states).  R is linear in each E_e, so L
+    is exactly quadratic in E_e and the central difference has no truncation error for any
+    step: h = 1e-2 E_e keeps the change of L (about 1e-7 of L) far above the rounding of the
+    fixed-order norm (about 1e-15 of L), so the difference is accurate to about 1e-8.  FP64
+    gradient (kept-vector and recomputing passes): 1e-6 relative to the largest sampled
+    gradient, on 32 seeded elements.  The FP32 gradient against the same FP64 differences:
+    the FP32 residual bound 2e-4 (its R and R_e carry that relative error)."""
+    J = jetsci()
+    prob = I.lognormal_problem(64, seed=4)
+    mesh = J.Mesh.of(prob)
+    u, E = cuda(prob.u), cuda(prob.E_elem)
+    sample = np.random.default_rng(17).choice(prob.n_elem, 32, replace=False)
+    R = mesh.residual(u, E_elem=E)
+    g_kept = mesh.material_grad(None, R, E_elem=E).cpu().numpy()[sample]
+    g_rec = mesh.material_grad(u, R, E_elem=E).cpu().numpy()[sample]
+    R32 = mesh.residual(u, E_elem=E, precision=J.FP32)
+    g32 = mesh.material_grad(None, R32, E_elem=E, precision=J.FP32).cpu().numpy()[sample]
+    fd = []
+    Ep = E.clone()
+    for e in sample:
+        h = 1e-2 * float(prob.E_elem[e])
+        L = []
+        for sgn in (1.0, -1.0):
+            Ep[e] = float(prob.E_elem[e]) + sgn * h
+            L.append(0.5 * mesh.norm2(mesh.residual(u, E_elem=Ep)).item() ** 2)
+        Ep[e] = float(prob.E_elem[e])
+        fd.append((L[0] - L[1]) / (2 * h))
+    fd = np.array(fd)
+    assert relerr(g_kept, fd) <= 1e-6, relerr(g_kept, fd)
+    assert relerr(g_rec, fd) <= 1e-6, relerr(g_rec, fd)
+    assert relerr(g32, fd) <= 2e-4, relerr(g32, fd)
+    assert mesh.check() == 0
+    mesh.close()
