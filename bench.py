@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip surrogate training and the adjoint workload")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton iteration counts")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--partition", default="replicas", choices=["replicas", "slab"],
+                    help="N > 1: one replica of the workload per rank (weak scaling, default), or one mesh "
+                         "split into z-slabs over the ranks with a halo exchange (strong scaling)")
     return ap.parse_args()
 
 
@@ -196,16 +199,106 @@ def calibrated_slab(prob, target_seconds):
     return small, (OracleSlab(prob, m) if m > 512 else small)
 
 
+def host_cores():
+    """Cores this process may run on (its affinity set), else the machine's count."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def baseline_line(slab, dt):
     return {"value": slab.m / dt, "unit": "elem/s", "cores": 1, "kind": "oracle",
             "sample": f"first {slab.m} elements (a contiguous slab) of the same workload, FP64, one step "
-                      f"(tangent CSR + residual + element K.v + CSR K.v + norm) in {dt:.1f} s"}
+                      f"(tangent CSR + residual + element K.v + CSR K.v + norm) in {dt:.1f} s, one thread",
+            "host_cores": host_cores()}
+
+
+class _SlabArrays:
+    """Elements [e0, e0 + m) of the workload as plain arrays (picklable for a worker process)."""
+
+    def __init__(self, prob, e0, m):
+        conn = prob.conn[e0:e0 + m]
+        used = np.unique(conn)
+        remap = -np.ones(prob.n_nodes, dtype=np.int64)
+        remap[used] = np.arange(len(used))
+        dofs = (3 * used[:, None] + np.arange(3)).ravel()
+        self.m = m
+        self.coords, self.conn = prob.coords[used], remap[conn].astype(np.int32)
+        self.phase, self.materials = prob.phase[e0:e0 + m], prob.materials
+        self.u, self.v = prob.u[dofs], prob.v[dofs]
+
+
+def _oracle_worker(arrays, pipe):
+    """One process of the all-core leg: sets up its slab (not timed), waits for the start
+    message, runs one oracle step (single-threaded, as it stands) and sends its time back."""
+    import oracle
+    om = oracle.Mesh(arrays.coords, arrays.conn, arrays.phase, arrays.materials)
+    rp, col = oracle.csr_pattern(arrays.conn, len(arrays.coords))
+    pipe.send("ready")
+    pipe.recv()
+    t0 = time.perf_counter()
+    vals, R = oracle.tangent_csr(om, arrays.u, rp, col)
+    oracle.apply_tangent(om, arrays.u, arrays.v)
+    oracle.spmv(rp, col, vals, arrays.v)
+    oracle.norm2(R)
+    pipe.send(time.perf_counter() - t0)
+
+
+def cpu_baseline_all_cores(prob, per_worker_elems, max_workers=64):
+    """The same oracle step on every host core at once: one spawned process per core (at most
+    max_workers), each on its own slab of per_worker_elems elements spread over the workload.
+    value = all processes' elements / wall time from the common start to the last finish."""
+    import multiprocessing as mp
+    P = max(1, min(host_cores(), max_workers))
+    m = int(max(512, min(per_worker_elems, prob.n_elem // P)))
+    starts = [int(k * (prob.n_elem - m) / max(1, P - 1)) for k in range(P)] if P > 1 else [0]
+    ctx = mp.get_context("spawn")
+    procs, pipes = [], []
+    for e0 in starts:
+        a, b = ctx.Pipe()
+        pr = ctx.Process(target=_oracle_worker, args=(_SlabArrays(prob, e0, m), b), daemon=True)
+        pr.start()
+        procs.append(pr)
+        pipes.append(a)
+    def receive(a, pr, deadline):
+        # a worker that died (or never answers) must not block the bench
+        while not a.poll(0.2):
+            if not pr.is_alive() or time.perf_counter() > deadline:
+                raise RuntimeError(f"oracle worker exited or timed out (exit code {pr.exitcode})")
+        return a.recv()
+
+    try:
+        deadline = time.perf_counter() + 600.0
+        for a, pr in zip(pipes, procs):
+            if receive(a, pr, deadline) != "ready":
+                raise RuntimeError("oracle worker failed")
+        t0 = time.perf_counter()
+        for a in pipes:
+            a.send("go")
+        dts = [receive(a, pr, t0 + 600.0) for a, pr in zip(pipes, procs)]
+        wall = time.perf_counter() - t0
+    finally:
+        for pr in procs:
+            pr.join(timeout=30)
+            if pr.is_alive():
+                pr.terminate()
+    return {"value": P * m / wall, "unit": "elem/s", "cores": P, "kind": "oracle", "host_cores": host_cores(),
+            "sample": f"{P} processes at once, one per core, each the single-threaded oracle step on its own "
+                      f"{m}-element slab of the same workload ({P * m} elements), wall {wall:.1f} s "
+                      f"(per-process {min(dts):.1f}-{max(dts):.1f} s)"}
 
 
 def cpu_baseline(prob, target_seconds):
-    """The FP64 oracle on a bounded sample of the same workload; slab set-up is not timed."""
+    """The FP64 oracle on a bounded sample of the same workload, single-threaded and on every
+    host core; slab set-up is not timed."""
     _, slab = calibrated_slab(prob, target_seconds)
-    return baseline_line(slab, slab.step())
+    line = baseline_line(slab, slab.step())
+    try:
+        line["all_cores"] = cpu_baseline_all_cores(prob, max(512, slab.m // 2))
+    except Exception as ex:  # report, do not hide
+        line["all_cores"] = {"error": repr(ex)}
+    return line
 
 
 def run_reference(args, rank):
@@ -221,8 +314,13 @@ def run_reference(args, rank):
     dt = statistics.median(times)
     v = slab.m / dt
     cb = baseline_line(slab, dt)
+    # ms_per_step is the measured time of one step over the slab (the work each timed step did);
+    # the full mesh at this rate would take n_elem / value seconds per step.
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elem/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * prob.n_elem / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
+            "ms_per_step_note": f"one oracle step over a {slab.m}-element slab of the workload (warm-up steps "
+                                f"on a 512-element slab); the full {prob.n_elem}-element mesh at this rate "
+                                f"would take {prob.n_elem / v:.0f} s per step (extrapolated, not run)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(prob, args.n), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "elem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -416,6 +514,113 @@ def newton_counts(J, torch, I, prob, mesh, stretch=0.01):
     return out
 
 
+
+# ------------------------------------------------------------------------------ slab arm
+def main_slab(args, rank, world, local):
+    """One 128^3 mesh split over the ranks into z-slabs of owned nodes (each rank holds every
+    element touching its nodes: a one-element ghost layer).  A step is the headline step on
+    every rank's sub-mesh, preceded by the halo exchange of u and v (NCCL point-to-point), with
+    the norm from the ranks' owned sums of squares (all-gather, fixed-order sum).  Strong
+    scaling: value = the mesh's elements / the slowest rank's step time."""
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_22087_b300 import jetsci as J
+    from paper_2604_22087_b300 import slab as S
+
+    prob = make_problem(args.n)
+    s = S.decompose(prob.coords, prob.conn, world)[rank]
+    part = S.SlabMesh(s, prob.coords, prob.phase, prob.materials)
+    mesh = part.mesh
+    stream = torch.cuda.Stream()
+    u = torch.as_tensor(s.scatter_owned(prob.u)).cuda()
+    v = torch.as_tensor(s.scatter_owned(prob.v)).cuda()
+    R, y, y2 = mesh.new_vector(), mesh.new_vector(), mesh.new_vector()
+    vals = mesh.new_values(J.FP64)
+    own = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = {}
+    torch.cuda.synchronize()
+
+    def step():
+        with torch.cuda.stream(stream):
+            if world > 1:
+                S.exchange(s, u)
+                S.exchange(s, v)
+            mesh.tangent_csr(u, vals=vals, R=R, stream=stream)
+            mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals, stream=stream)
+            mesh.apply_tangent(None, v, y=y, stream=stream)
+            part.mesh.norm2(part.owned(R), out=own, stream=stream)
+            out["norm"] = S.norm2_device(s, own) if world > 1 else own
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        t1.synchronize()
+    barrier()
+    ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, world, "cuda")
+    norm = float(out["norm"].item())
+
+    # end to end: the owned part of u and v from pinned host memory, the owned rows of the CSR
+    # product and the norm back, every step
+    n_own = s.n_owned_dof
+    u_h = torch.as_tensor(prob.u[s.dofs()[:n_own]]).pin_memory()
+    v_h = torch.as_tensor(prob.v[s.dofs()[:n_own]]).pin_memory()
+    y_h = torch.empty(n_own, dtype=torch.float64).pin_memory()
+    n_h = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            u[:n_own].copy_(u_h, non_blocking=True)
+            v[:n_own].copy_(v_h, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            y_h.copy_(y2[:n_own], non_blocking=True)
+            n_h.copy_(out["norm"], non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    if rank == 0:
+        halo = sum(len(x) for x in s.recv.values())
+        line = {"metric": METRIC, "value": prob.n_elem / (ms_step * 1e-3), "unit": "elem/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(config_dict(prob, args.n), partition=f"z-slabs over {world} ranks, owner computes, "
+                               f"one-element ghost layer; rank 0: {len(s.elems)} elements, {s.n_owned} owned "
+                               f"nodes, {halo} halo DOFs received per exchange"),
+                "e2e": {"value": prob.n_elem / (e2e_ms * 1e-3), "unit": "elem/s",
+                        "h2d_bytes_per_step": 16 * n_own, "d2h_bytes_per_step": 8 * n_own + 8,
+                        "note": "rank 0's owned u, v in and owned CSR product rows and the norm out"},
+                "gpu_launches": args.steps * (2 * mesh.n_colours + 3), "clocks": clk.summary(),
+                "residual_norm": norm, "device_flags": mesh.check()}
+        print(json.dumps(line), flush=True)
+    part.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------------------ main arm
 def main():
     args = parse()
@@ -424,6 +629,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.partition == "slab":
+        main_slab(args, rank, world, local)
         return
     import torch
     import torch.distributed as dist
@@ -569,7 +777,10 @@ def main():
                          "ms_per_launch_group": ms_tangent, "hbm_achieved_gbs": hbm,
                          "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind},
             "e2e": {"value": world * prob.n_elem / (e2e_ms * 1e-3), "unit": "elem/s",
-                    "h2d_bytes_per_step": 2 * prob.n_dof * 8, "d2h_bytes_per_step": prob.n_dof * 8 + 8},
+                    "h2d_bytes_per_step": 2 * prob.n_dof * 8, "d2h_bytes_per_step": prob.n_dof * 8 + 8,
+                    "note": "in: u and v from pinned host memory; out: the CSR product y and ||R||. The "
+                            "residual R, the CSR values and the matrix-free product stay on the device "
+                            "(a device-resident Newton driver reads only the norm)"},
             # per step: k_tangent and k_apply_mf once per colour, k_spmv, two norm passes
             "gpu_launches": args.steps * (2 * mesh.n_colours + 3),
             "clocks": clocks, "device_flags": flags,
@@ -656,6 +867,15 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
         mesh.norm2(R, out=nrm, stream=stream)
 
     rec("step_fp32", timeit(fp32_step, stream))
+
+    # The surrogate step's calls (tangent CSR + R, CSR K.v, norm) with the plain law in FP32: the
+    # like-for-like comparison for the surrogate, which also runs FP32 element arithmetic.
+    def fp32_csr_step():
+        mesh.tangent_csr(u, vals=vals32, R=R, precision=J.FP32, stream=stream)
+        mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals32, precision=J.FP32, stream=stream)
+        mesh.norm2(R, out=nrm, stream=stream)
+
+    rec("step_fp32_csr_only", timeit(fp32_csr_step, stream))
     del vals32
     torch.cuda.empty_cache()
 
@@ -686,7 +906,8 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
             mesh.norm2(R, out=nrm, stream=stream)
 
         ms = timeit(surrogate_step, stream)
-        rec("step_surrogate", ms, {"vs_step_fp64_csr_only": out["step_fp64_csr_only"]["ms"] / ms})
+        rec("step_surrogate", ms, {"vs_step_fp64_csr_only": out["step_fp64_csr_only"]["ms"] / ms,
+                                   "vs_step_fp32_csr_only": out["step_fp32_csr_only"]["ms"] / ms})
         J.attach_surrogate(mesh, None)
         del vv
         torch.cuda.empty_cache()
