@@ -359,9 +359,11 @@ jetsci_status jetsci_assemble_element_blocks(jetsci_mesh mesh, const void *Ke_de
  * bitwise equal.  Scratch: a fixed file-scope device array of 4096 doubles (32 KiB) that
  * every GPU which loads the library holds until the process exits; the call allocates
  * nothing and frees nothing.  n is limited to 4096 * 8192 = 33,554,432 entries; larger
- * n returns JETSCI_ERR_ARG with a message.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current, so make that
- * first call before any stream capture.  All calls on one device share the array: calls
+ * n returns JETSCI_ERR_ARG with a message.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) in the current device's context; the first call on a device may
+ * load the library's device code, so make that first call before any stream capture.  The
+ * address is not cached, so a cudaDeviceReset in between leaves no stale pointer.  All
+ * calls on one device share the array: calls
  * that overlap on the GPU (e.g. on two streams at once) race; the array keeps the last
  * call's partial sums, which the next call overwrites before reading.
  * x_dev [n] FP64 device, out_dev[0] FP64 device.

@@ -10,7 +10,6 @@
 // the process exits, so a call allocates nothing.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "jetsci_internal.h"
@@ -18,12 +17,8 @@
 namespace {
 
 constexpr int64_t kStaticPartials = 4096;  // first-pass partials; n <= 4096 * 8192
-constexpr int kMaxDevices = 128;
 
 static __device__ __align__(256) double g_norm_scratch[kStaticPartials];
-
-double *g_scratch_addr[kMaxDevices] = {};  // device address of g_norm_scratch, per device
-std::mutex g_scratch_mu;
 
 }  // namespace
 
@@ -36,21 +31,13 @@ extern "C" jetsci_status jetsci_norm2_static(const double *x_dev, int64_t n, dou
         return fail(JETSCI_ERR_ARG, "jetsci_norm2_static: n = " + std::to_string(n) +
                                         " exceeds the static scratch limit of " + std::to_string(max_n) +
                                         " entries; use jetsci_norm2");
-    int dev = -1;
-    JETSCI_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(JETSCI_ERR_ARG, "device ordinal out of range");
-    double *scratch = nullptr;
-    {
-        // Set-up, once per device with that device current: in host code the symbol's name
-        // is only a host-side stand-in, so the kernels get its device address.
-        std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_addr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_norm_scratch);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_norm_scratch)");
-            g_scratch_addr[dev] = static_cast<double *>(p);
-        }
-        scratch = g_scratch_addr[dev];
-    }
-    return launch_norm2(x_dev, n, scratch, kStaticPartials, out_dev, (cudaStream_t)stream);
+    // In host code the symbol's name is only a host-side stand-in: the kernels get its device
+    // address in the current device's context.  It is looked up on every call (after the first
+    // call on a device, which may load this library's device code, the lookup is a table
+    // search), not cached, so that a cudaDeviceReset, which reloads the module possibly at
+    // another address, leaves no stale pointer behind.
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_norm_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_norm_scratch)");
+    return launch_norm2(x_dev, n, static_cast<double *>(p), kStaticPartials, out_dev, (cudaStream_t)stream);
 }
