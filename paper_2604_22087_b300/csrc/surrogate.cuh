@@ -169,83 +169,86 @@ __device__ inline bool mlp_forward(MlpTileSmem &sm, uint32_t &phase, float y[6])
     return ok;
 }
 
+// One round of the forward and input-Jacobian pass: directions 3 ROUND .. 3 ROUND + 2.  The
+// round is a template parameter, so the columns of Jm that the round fills are fixed at
+// compile time (a single copy of this code with the round chosen at run time returned the
+// second round's middle direction in both rounds' middle column from the evaluation kernel).
+template <int ROUND>
+__device__ __forceinline__ bool mlp_jacobian_round(MlpTileSmem &sm, uint32_t &phase, float y[6], float Jm[6][6]) {
+    const int t = threadIdx.x;
+    const uint32_t tm = sm.tmem_base;
+    constexpr int round = ROUND;
+    bool ok = true;
+    smem_to_tensor_sync();
+    // layer 1: z1 = x W1^T (K = 16, zero-padded)
+    if (t == 0) tc::gemm_bf16_128xN(tm, sm.x, sm.w + kImgW1, 64, 16);
+    ok = mma_sync_bounded(&sm.mbar, phase) && ok;
+#pragma unroll 1
+    for (int layer = 0; layer < 3; layer++) {
+        // epilogue of layer `layer`: activation, silu' and the three tangent rows
+        float s[64];
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float z[16], a[16], bias[16];
+            tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
+            ld_f32x16(&sm.b[layer][c0], bias);
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                silu_and_prime(z[j] + bias[j], a[j], s[c0 + j]);
+            }
+            st_bf16x8(sm.act, t, c0 / 8, 64, a);
+            st_bf16x8(sm.act, t, c0 / 8 + 1, 64, a + 8);
+        }
+#pragma unroll
+        for (int dl = 0; dl < 3; dl++) {
+            const int d = 3 * round + dl;
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float u[16];
+                if (layer == 0) {
+                    ld_f32x16(&sm.w1t[d][c0], u);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) u[j] *= s[c0 + j];
+                } else {
+                    tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (dl + 1) + c0), u);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) u[j] *= s[c0 + j];
+                }
+                st_bf16x8(sm.tan[dl], t, c0 / 8, 64, u);
+                st_bf16x8(sm.tan[dl], t, c0 / 8 + 1, 64, u + 8);
+            }
+        }
+        smem_to_tensor_sync();
+        if (t == 0) {
+            const unsigned char *W = sm.w + (layer == 0 ? kImgW2 : layer == 1 ? kImgW3 : kImgW4);
+            const int N = layer < 2 ? 64 : 16;
+            tc::gemm_bf16_128xN(tm, sm.act, W, N, 64);
+            for (int dl = 0; dl < 3; dl++) tc::gemm_bf16_128xN(tm + 64 * (dl + 1), sm.tan[dl], W, N, 64);
+        }
+        ok = mma_sync_bounded(&sm.mbar, phase) && ok;
+    }
+    float v[16];
+    if (ROUND == 0) {
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 0), v);
+#pragma unroll
+        for (int c = 0; c < 6; c++) y[c] = v[c] + sm.b4[c];
+    }
+#pragma unroll
+    for (int dl = 0; dl < 3; dl++) {
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (dl + 1)), v);
+#pragma unroll
+        for (int c = 0; c < 6; c++) Jm[c][3 * ROUND + dl] = v[c];
+    }
+    return ok;
+}
+
 // Runs the forward and input-Jacobian pass for the tile whose inputs are already in sm.x
 // (row t = point t).  On return thread t holds y[6] (normalised outputs) and Jm[6][6]
 // (dy/dx, column d = input direction d).  Returns false if a tensor-core wait timed out.
 __device__ inline bool mlp_forward_jacobian(MlpTileSmem &sm, uint32_t &phase, float y[6], float Jm[6][6]) {
-    const int t = threadIdx.x;
-    const uint32_t tm = sm.tmem_base;
-    bool ok = true;
-#pragma unroll 1
-    for (int round = 0; round < 2; round++) {
-        smem_to_tensor_sync();
-        // layer 1: z1 = x W1^T (K = 16, zero-padded)
-        if (t == 0) tc::gemm_bf16_128xN(tm, sm.x, sm.w + kImgW1, 64, 16);
-        ok = mma_sync_bounded(&sm.mbar, phase) && ok;
-#pragma unroll 1
-        for (int layer = 0; layer < 3; layer++) {
-            // epilogue of layer `layer`: activation, silu' and the three tangent rows
-            float s[64];
-#pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 16) {
-                float z[16], a[16], bias[16];
-                tc::tmem_ld16(tc::tmem_lane_addr(tm, c0), z);
-                ld_f32x16(&sm.b[layer][c0], bias);
-#pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    silu_and_prime(z[j] + bias[j], a[j], s[c0 + j]);
-                }
-                st_bf16x8(sm.act, t, c0 / 8, 64, a);
-                st_bf16x8(sm.act, t, c0 / 8 + 1, 64, a + 8);
-            }
-#pragma unroll
-            for (int dl = 0; dl < 3; dl++) {
-                const int d = 3 * round + dl;
-#pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 16) {
-                    float u[16];
-                    if (layer == 0) {
-                        ld_f32x16(&sm.w1t[d][c0], u);
-#pragma unroll
-                        for (int j = 0; j < 16; j++) u[j] *= s[c0 + j];
-                    } else {
-                        tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (dl + 1) + c0), u);
-#pragma unroll
-                        for (int j = 0; j < 16; j++) u[j] *= s[c0 + j];
-                    }
-                    st_bf16x8(sm.tan[dl], t, c0 / 8, 64, u);
-                    st_bf16x8(sm.tan[dl], t, c0 / 8 + 1, 64, u + 8);
-                }
-            }
-            smem_to_tensor_sync();
-            if (t == 0) {
-                const unsigned char *W = sm.w + (layer == 0 ? kImgW2 : layer == 1 ? kImgW3 : kImgW4);
-                const int N = layer < 2 ? 64 : 16;
-                tc::gemm_bf16_128xN(tm, sm.act, W, N, 64);
-                for (int dl = 0; dl < 3; dl++) tc::gemm_bf16_128xN(tm + 64 * (dl + 1), sm.tan[dl], W, N, 64);
-            }
-            ok = mma_sync_bounded(&sm.mbar, phase) && ok;
-        }
-        float v[16];
-        if (round == 0) {
-            tc::tmem_ld16(tc::tmem_lane_addr(tm, 0), v);
-#pragma unroll
-            for (int c = 0; c < 6; c++) y[c] = v[c] + sm.b4[c];
-        }
-#pragma unroll
-        for (int dl = 0; dl < 3; dl++) {
-            tc::tmem_ld16(tc::tmem_lane_addr(tm, 64 * (dl + 1)), v);
-            // compile-time column indices keep Jm in registers
-            if (round == 0) {
-#pragma unroll
-                for (int c = 0; c < 6; c++) Jm[c][dl] = v[c];
-            } else {
-#pragma unroll
-                for (int c = 0; c < 6; c++) Jm[c][3 + dl] = v[c];
-            }
-        }
-    }
-    return ok;
+    const bool ok0 = mlp_jacobian_round<0>(sm, phase, y, Jm);
+    const bool ok1 = mlp_jacobian_round<1>(sm, phase, y, Jm);
+    return ok0 && ok1;
 }
 
 }  // namespace jetsci

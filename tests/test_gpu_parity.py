@@ -733,3 +733,32 @@ def test_full_size_adjoint_central_differences():
     assert relerr(g32, fd) <= 2e-4, relerr(g32, fd)
     assert mesh.check() == 0
     mesh.close()
+
+
+def test_medium_box_row_gather_fp32_tf32():
+    """A distorted 40 x 40 x 24 box (38,400 elements, 2,400 element-pass blocks): the FP32 and TF32
+    row-gather assembly against the oracle within their guards, every value written
+    (NaN-prefilled outputs), and bitwise repeatable."""
+    J = jetsci()
+    coords, conn = I.box_mesh(40, 40, 24, distort=0.2, seed=12)
+    g = np.random.default_rng(12)
+    phase = (g.uniform(size=len(conn)) < 0.4).astype(np.int32)
+    prob = I.Problem("medium_box", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                     g.uniform(-3e-3, 3e-3, coords.size), g.uniform(-1, 1, coords.size))
+    mesh = J.Mesh.of(prob)
+    om = oracle.Mesh.of(prob)
+    rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
+    u = cuda(prob.u)
+    for name in ("FP32", "TF32"):
+        p = getattr(J, name)
+        R = torch.full((mesh.n_dof,), float("nan"), dtype=torch.float64, device="cuda")
+        vals = mesh.new_values(p)
+        vals.fill_(float("nan"))
+        mesh.tangent_csr(u, vals=vals, R=R, precision=p)
+        assert relerr(vals.cpu().numpy(), vals_ref) <= GUARD[name]["vals"], name
+        assert relerr(R.cpu().numpy(), R_ref) <= GUARD[name]["R"], name
+        vals2 = mesh.tangent_csr(u, precision=p)
+        assert torch.equal(vals, vals2)
+    assert mesh.check() == 0
+    mesh.close()
