@@ -68,7 +68,9 @@ typedef enum {
     JETSCI_FP32 = 1,      /* element arithmetic in FP32 (FP64 geometry differences);
                              CSR values float; R, K.v accumulated in FP64              */
     JETSCI_TF32 = 2,      /* as FP32, with the element stiffness contraction on
-                             tensor cores in TF32 with FP32 accumulation               */
+                             tensor cores in TF32 with FP32 accumulation (the
+                             residual and the matrix-free product, which form no
+                             element stiffness, run as FP32)                          */
     JETSCI_SURROGATE = 3, /* FP32 element arithmetic, stress and tangent from the
                              mesh's MLP surrogate (BF16 tensor cores, FP32 accumulate)
                              with the plain law as fallback out of range; CSR float    */

@@ -847,16 +847,20 @@ static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
 
 template <typename T>
 static void residual_colours(jetsci_mesh m, ElemArgs A, const double *u, double *R, cudaStream_t s) {
-    for (int c = 0; c < m->n_colours; c++) {
-        A.elems = m->d_colour_elems + m->colour_ptr[c];
-        A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
-        if (A.n == 0) continue;
+    // One launch per colour.  Running all colours of an element-id chunk before the next chunk
+    // (so that the nodal data the colours share stays in L2) was measured slower at every chunk
+    // size at 128^3 (FP32 residual 0.70 ms against 0.72 / 0.98 / 2.08 ms for chunks of 2^20 /
+    // 2^18 / 2^16 elements; matrix-free FP32 0.90 against 0.95 / 1.21 / 2.28 ms): the launches
+    // and their tails cost more than the DRAM re-reads of a colour-major order.
+    for_each_colour(m, [&](const int32_t *elems, int64_t n) {
+        A.elems = elems;
+        A.n = n;
         unsigned grid = (unsigned)((8 * A.n + 127) / 128);
         if (A.re)
             k_residual<T, true><<<grid, 128, 0, s>>>(A, u, R);
         else
             k_residual<T, false><<<grid, 128, 0, s>>>(A, u, R);
-    }
+    });
 }
 
 jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int precision,
@@ -916,6 +920,11 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
 
 // Row-gather assembly: the element pass writes every element's 24 x 24 rows and residual
 // vectors to the mesh's workspace in one launch, the row pass forms each CSR row and R entry once.
+// (Running both passes chunk by chunk, one slab of 16,384 elements at a time with the element
+// rows in a ring that L2 holds, was measured slower at 128^3: 5.93 ms against 4.19 ms for the FP32
+// tangent, 5.55 / 7.86 ms with chunks of 32,768 / 8,192 elements.  The row pass is bound by load
+// latency, not DRAM, so reading from L2 gains little, and 256 launches of one or two waves each
+// add their tails.)
 template <typename T, typename VT>
 static jetsci_status tangent_rows(jetsci_mesh m, ElemArgs A, const double *u, VT *vals, double *R,
                                   cudaStream_t s) {
@@ -953,7 +962,7 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
         return tangent_colours<df64, double>(m, A, u, (double *)vals, R, s);
     }
-    if (precision == JETSCI_TF32) return launch_tf32(m, u, nullptr, (float *)vals, R, nullptr, E_elem, s);
+    if (precision == JETSCI_TF32) return launch_tf32(m, u, (float *)vals, R, E_elem, s);
     if (precision == JETSCI_SURROGATE) return launch_surrogate(m, u, (float *)vals, R, s);
     return fail(JETSCI_ERR_UNSUPPORTED, "precision not implemented for the tangent");
 }
@@ -961,18 +970,21 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
 template <typename T, bool kReuse = false>
 static void apply_colours(jetsci_mesh m, ElemArgs A, const double *u, const double *v, double *y,
                           cudaStream_t s) {
-    for (int c = 0; c < m->n_colours; c++) {
-        A.elems = m->d_colour_elems + m->colour_ptr[c];
-        A.n = m->colour_ptr[c + 1] - m->colour_ptr[c];
-        if (A.n == 0) continue;
+    for_each_colour(m, [&](const int32_t *elems, int64_t n) {  // (one launch per colour: see residual_colours)
+        A.elems = elems;
+        A.n = n;
         unsigned grid = (unsigned)((8 * A.n + 127) / 128);
         k_apply_mf<T, kReuse><<<grid, 128, 0, s>>>(A, u, v, y);
-    }
+    });
 }
 
+// The matrix-free product forms no element stiffness: per Gauss point it is 3 x 3 algebra between
+// the sum-factorised gradient of v and the nodal forces, with no contraction for the tensor cores
+// to take.  TF32 therefore runs the FP32 product (as the TF32 residual runs the FP32 residual);
+// forming K_e on the tensor cores to multiply it by v_e was measured 5.8x slower at 128^3.
 jetsci_status launch_apply_mf(jetsci_mesh m, const double *u, const double *v, double *y, int precision,
                               const double *E_elem, cudaStream_t s) {
-    if (precision == JETSCI_TF32) return launch_tf32(m, u, v, nullptr, nullptr, y, E_elem, s);
+    if (precision == JETSCI_TF32) precision = JETSCI_FP32;
     JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     ElemArgs A = make_args(m, E_elem);
     if (!u) {  // at the stored FP64 linearisation (checked by the caller)

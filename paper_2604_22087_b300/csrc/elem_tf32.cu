@@ -1,5 +1,5 @@
 // Element stiffness on the tensor cores in TF32 (FP32 accumulate in TMEM): the element rows of
-// the row-gather tangent assembly, and the matrix-free product K.v.
+// the row-gather tangent assembly.
 //
 // The tangent in pair form, as the CUDA-core kernels use it:
 //   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi ] + delta_ik sum_q tg_a . g_b
@@ -14,11 +14,17 @@
 // TMEM columns.  The geometric term (36 dot products per element and point) is reduced over the
 // Gauss-point lanes on the CUDA cores.
 //
-// One CTA = four groups of four elements: warp w evaluates group w (lane = element x Gauss
-// point) and writes its operand columns; one thread issues the 16 MMAs; then every warp reads
-// its TMEM lane quarter of each group's accumulator.  T2 is transposed within node blocks
-// through shared memory.
+// Persistent CTAs (two per SM, as TMEM allows: 256 columns each) loop over batches of 16
+// elements = four groups of four; warp w evaluates group w (lane = element x Gauss point) and
+// writes its operand columns, one thread issues the 16 MMAs, then every warp reads its TMEM lane
+// quarter of each group's accumulator and T2 is transposed within node blocks through shared
+// memory.  Per CTA the zeros of the block-diagonal A tiles are written once (a lane only ever
+// writes its own element's rows), and the gathers of the next batch are issued before the
+// current batch's arithmetic: the connectivity two batches ahead, the coordinates and
+// displacements one batch ahead.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "blocks.cuh"
 #include "element.cuh"
@@ -44,17 +50,16 @@ constexpr int kTgT2Stride = 25;                   // floats per row of the T2 tr
 
 // The MMA reads 128 rows of A; rows 96..127 (row blocks 12..15) fall on the next tile or on the
 // B tiles and produce accumulator rows that are never read, so they need neither zeros nor room.
+constexpr int kTgT2Groups = 2;  // groups whose T2 rows the transposition buffer holds at once
 struct __align__(128) TgSmem {
-    unsigned char A[kTgGroups][kTgATile];  // after the MMAs: T2 rows, [group][96][kTgT2Stride] floats
+    unsigned char A[kTgGroups][kTgATile];
     unsigned char B[kTgGroups][kTgBTile];
-    float geo[kTgElems][36];      // sum_q tg_a . g_b, pairs a <= b row by row
-    float vnode[kTgElems][8][3];  // v at the element's nodes (matrix-free mode), FP32
-    int32_t node[kTgElems][8];
+    float t2[kTgT2Groups][96 * kTgT2Stride];  // T2 rows of two groups, [row][kTgT2Stride]
+    float geo[kTgElems][36];                  // sum_q tg_a . g_b, pairs a <= b row by row
     int32_t elem[kTgElems];
     uint64_t mbar;
     uint32_t tmem_base;
 };
-static_assert(kTgGroups * 96 * kTgT2Stride * 4 <= (int)sizeof(TgSmem::A), "T2 buffer fits in the A tiles");
 
 __device__ __forceinline__ uint32_t tg_offset(int r, int k) {
     return (uint32_t)((r >> 3) * kTgSBO + (k >> 2) * kTgLBO + (r & 7) * 16 + (k & 3) * 4);
@@ -75,249 +80,297 @@ struct Tf32Args {
     const int32_t *__restrict__ phase;
     const Material *__restrict__ mats;
     const double *__restrict__ E_elem;
-    const int32_t *__restrict__ elems;  // element list (one colour) or NULL = all elements in order
-    int64_t n;
+    int64_t n;         // elements 0 .. n - 1
     uint32_t *flags;
 };
 
-// MODE 0: element pass of the row-gather assembly -- the element's 24 x 24 stiffness rows go to
-// vals = the workspace [element][24][24] and, if R is given, its nodal forces to R = the
-// workspace's residual part [element][local node][3];
-// MODE 1: y += K_e v_e (matrix-free, one launch per colour).
-template <int MODE>
-__global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restrict__ u, const double *__restrict__ v,
-                                              float *__restrict__ vals, double *__restrict__ R, double *__restrict__ y) {
+// What a lane gathers for one batch: its element, its node, the node's coordinates and
+// displacement, the element's phase and modulus.
+struct Tf32Gather {
+    int64_t e;
+    int32_t node, ph;
+    double E;
+    double X[3], U[3];
+};
+
+// element of the lane in batch b (the last element for the slots past the end), and whether
+// the slot is one
+__device__ __forceinline__ int64_t tf32_elem(const Tf32Args &A, int64_t b, int es, bool &active) {
+    const int64_t slot = b * kTgElems + es;
+    active = slot < A.n;
+    return active ? slot : A.n - 1;
+}
+
+__device__ __forceinline__ void tf32_gather_conn(const Tf32Args &A, int64_t b, int es, int l, Tf32Gather &g) {
+    bool active;
+    g.e = tf32_elem(A, b, es, active);
+    g.node = __ldg(A.conn + 8 * g.e + hex_node_of_lane(l));
+    g.ph = __ldg(A.phase + g.e);
+    g.E = A.E_elem ? __ldg(A.E_elem + g.e) : 0.0;
+}
+
+__device__ __forceinline__ void tf32_gather_values(const Tf32Args &A, const double *__restrict__ u, Tf32Gather &g) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        g.X[i] = __ldg(A.coords + 3 * (int64_t)g.node + i);
+        g.U[i] = u ? __ldg(u + 3 * (int64_t)g.node + i) : 0.0;
+    }
+}
+
+// Element pass of the row-gather assembly: the element's 24 x 24 stiffness rows go to vals = the
+// workspace [element][24][24] and, if R is given, its nodal forces to R = the workspace's residual
+// part [element][local node][3].
+__global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restrict__ u, float *__restrict__ vals,
+                                              double *__restrict__ R) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TgSmem &sm = *reinterpret_cast<TgSmem *>(smem_raw);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int el = lane >> 3, l = lane & 7;  // element in the group, Gauss point
-    const int es = t >> 3;                   // element slot in the CTA (= 4 w + el)
+    const int es = t >> 3;                   // element slot in the batch (= 4 w + el)
     if (w == 0) tc::tmem_alloc(&sm.tmem_base, kTgTmemCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
         tc::fence_mbar_init();
     }
-    // ---------------- phase 1: thread = (element, Gauss point)
+    // zeros of the A tiles, once: every lane later writes only its own element's rows in its
+    // column, so the other elements' rows there stay zero
     {
-        const int64_t slot = (int64_t)blockIdx.x * kTgElems + es;
-        const bool active = slot < A.n;
-        const int64_t e = A.elems ? A.elems[active ? slot : A.n - 1] : (active ? slot : A.n - 1);
-        int32_t node;
-        GaussKinematics<float> K;
-        float cu[3];
-        gauss_kinematics_coords<float>(A.conn, A.coords, u, e, l, node, K, cu);
-        ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
-        const float lam = (float)mt.lam, mu = (float)mt.mu;
-        // W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau, m, and the residual moment Q
-        float W[3][3], tau[3][3], Q[3][3], m;
-        bool ok = true;
-        if (mt.law == JETSCI_LINEAR_ELASTIC) {
-            const float rdJ = 1.0f / K.dJ;
-#pragma unroll
-            for (int d = 0; d < 3; d++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) W[d][j] = K.aJ[d][j] * rdJ;
-            float H[3][3], sg[3][3];
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) H[i][j] = K.Du[i][0] * W[0][j] + K.Du[i][1] * W[1][j] + K.Du[i][2] * W[2][j];
-            const float ltr = lam * (H[0][0] + H[1][1] + H[2][2]);
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    sg[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : 0.0f);
-                    tau[i][j] = 0.0f;
-                }
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int d = 0; d < 3; d++) Q[i][d] = sg[i][0] * K.aJ[d][0] + sg[i][1] * K.aJ[d][1] + sg[i][2] * K.aJ[d][2];
-            m = mu;
-        } else {
-            NeoHookeanState<float> st;
-            neo_hookean_state(K, lam, mu, st);
-            ok = st.ok;
-            m = st.m;
-            const float sc = K.dJ * st.rdj;
-#pragma unroll
-            for (int d = 0; d < 3; d++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    W[d][j] = st.aj[d][j] * st.rdj;
-                    tau[d][j] = st.tau[d][j];
-                }
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int d = 0; d < 3; d++)
-                    Q[i][d] = sc * (st.tau[i][0] * st.aj[d][0] + st.tau[i][1] * st.aj[d][1] + st.tau[i][2] * st.aj[d][2]);
-        }
-        if (active) {
-            const uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE);
-            if (bits) atomicOr(A.flags, bits);
-        }
-        const float cw = K.dJ * (1.0f / 512.0f);
-        const float cl = cw * lam, cm = cw * m;
-        const float t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
-        const float t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
-        const float xp = 1.0f + K.xi, xm = 1.0f - K.xi, yp = 1.0f + K.eta, ym = 1.0f - K.eta;
-        const float zp = 1.0f + K.zeta, zm = 1.0f - K.zeta;
-        unsigned char *At = sm.A[w];
-        unsigned char *Bt = sm.B[w];
-        const int kc = 8 * el + l;  // this lane's column of A and B
-        float g[8][3], tg[8][3];
-#pragma unroll
-        for (int a = 0; a < 8; a++) {
-            const int bits = hex_bits_of_node(a);
-            const float fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
-            const float yz = fy * fz, xz = fx * fz, xy = fx * fy;
-            const float n0 = (bits & 1) ? yz : -yz, n1 = (bits & 2) ? xz : -xz, n2 = (bits & 4) ? xy : -xy;
-#pragma unroll
-            for (int j = 0; j < 3; j++) g[a][j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
-            tg[a][0] = t00 * g[a][0] + t01 * g[a][1] + t02 * g[a][2];
-            tg[a][1] = t01 * g[a][0] + t11 * g[a][1] + t12 * g[a][2];
-            tg[a][2] = t02 * g[a][0] + t12 * g[a][1] + t22 * g[a][2];
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                // A: the element's own row block gets g, the other three elements' rows a zero in
-                // this column
-#pragma unroll
-                for (int eo = 0; eo < 4; eo++)
-                    *reinterpret_cast<float *>(At + tg_offset(24 * eo + 3 * a + i, kc)) =
-                        eo == el ? to_tf32(g[a][i]) : 0.0f;
-                *reinterpret_cast<float *>(Bt + tg_offset(3 * a + i, kc)) = to_tf32(cl * g[a][i]);
-                *reinterpret_cast<float *>(Bt + tg_offset(24 + 3 * a + i, kc)) = to_tf32(cm * g[a][i]);
-            }
-        }
-        // geometric term: d_p = tg_a . g_b for the 36 pairs, summed over the 8 Gauss-point lanes
-        // by a reduce-scatter (halves exchanged across lanes 4, 2, 1 apart); lane l ends with
-        // the sums of pairs 18 (l>>2 & 1) + 9 (l>>1 & 1) + 5 (l & 1) + j, j < 5 (< 4 for odd l)
-        float d[36];
-#pragma unroll
-        for (int a = 0; a < 8; a++)
-#pragma unroll
-            for (int b = a; b < 8; b++)
-                d[tg_pair(a, b)] = tg[a][0] * g[b][0] + tg[a][1] * g[b][1] + tg[a][2] * g[b][2];
-        const bool h4 = (l >> 2) & 1, h2 = (l >> 1) & 1, h1 = l & 1;
-        float d18[18], d9[9], d5[5];
-#pragma unroll
-        for (int j = 0; j < 18; j++) {
-            const float keep = h4 ? d[18 + j] : d[j], give = h4 ? d[j] : d[18 + j];
-            d18[j] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
-        }
-#pragma unroll
-        for (int j = 0; j < 9; j++) {
-            const float keep = h2 ? d18[9 + j] : d18[j], give = h2 ? d18[j] : d18[9 + j];
-            d9[j] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
-        }
-#pragma unroll
-        for (int j = 0; j < 5; j++) {
-            const float lo = d9[j], hi = j + 5 < 9 ? d9[j + 5] : 0.0f;
-            const float keep = h1 ? hi : lo, give = h1 ? lo : hi;
-            d5[j] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
-        }
-        const int p0 = 18 * h4 + 9 * h2 + 5 * h1;
-#pragma unroll
-        for (int j = 0; j < 5; j++)
-            if (5 * h1 + j < 9) sm.geo[es][p0 + j] = d5[j];
-        // residual: nodal forces of the lane's node
-        float f[3];
-        nodal_force_of_moment(Q, K, l, f);
-        if (MODE == 0 && R && active)
-#pragma unroll
-            for (int i = 0; i < 3; i++) R[3 * (8 * e + hex_node_of_lane(l)) + i] = to_double(f[i]);
-        sm.node[es][hex_node_of_lane(l)] = node;
-        if (MODE == 1)
-#pragma unroll
-            for (int k = 0; k < 3; k++) sm.vnode[es][hex_node_of_lane(l)][k] = from_double<float>(v[3 * (int64_t)node + k]);
-        if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+        uint4 *z = reinterpret_cast<uint4 *>(&sm.A[0][0]);
+        for (int i = t; i < (int)(sizeof(sm.A) / 16); i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
     }
-    tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tm = sm.tmem_base;
-    if (t == 0) {
-        const uint32_t id = tc::idesc_tf32(128, kTgN);
-        for (int g = 0; g < kTgGroups; g++) {
-            const uint32_t a0 = tc::smem_addr(sm.A[g]), b0 = tc::smem_addr(sm.B[g]);
-            // one MMA of K = 8 covers two core matrices along K
-            for (int kk = 0; kk < kTgK / 8; kk++)
-                tc::mma_tf32(tm + kTgCols * g, tc::smem_desc(a0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO),
-                             tc::smem_desc(b0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO), id, kk > 0 ? 1u : 0u);
-        }
-        tc::mma_commit(&sm.mbar);
+    const int64_t n_batches = (A.n + kTgElems - 1) / kTgElems;
+    const int64_t G = gridDim.x;
+    int64_t b = blockIdx.x;
+    Tf32Gather cur, nxt;
+    if (b < n_batches) {
+        tf32_gather_conn(A, b, es, l, cur);
+        tf32_gather_values(A, u, cur);
     }
-    const bool ok = tc::mbar_wait_bounded(&sm.mbar, 0);
-    tc::fence_after_sync();
-    if (!ok && t == 0) atomicOr(A.flags, JETSCI_FLAG_NONFINITE);
-    // ---------------- epilogue: thread t owns accumulator row r = t of each group (TMEM lane t);
-    // rows 96..127 (warp 3) carry nothing.  First T2 of every group into the (now free) A tiles,
-    float *t2 = reinterpret_cast<float *>(sm.A[0]);
-    const int r = t, rel = r / 24, ra = (r % 24) / 3, ri = r % 3;
-    if (w < 3) {
-        for (int g = 0; g < kTgGroups; g++) {
-            float v16[16], v8[8];
-            tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * g + 24), v16);
-            tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * g + 40), v8);
-            float *dst = t2 + (96 * g + r) * kTgT2Stride;
+    if (b + G < n_batches) tf32_gather_conn(A, b + G, es, l, nxt);
+    uint32_t it = 0;
+    for (; b < n_batches; b += G, it++) {
+        // ---------------- phase 1: thread = (element, Gauss point)
+        bool active;
+        (void)tf32_elem(A, b, es, active);
+        const int64_t e = cur.e;
+        {
+            GaussKinematics<float> K;
+            float cu[3];
+            gauss_kinematics_of<float>(cur.X, cur.U, l, K, cu);
+            const Material &mat = A.mats[cur.ph];
+            const float lam = A.E_elem ? (float)(cur.E * mat.lam1) : (float)mat.lam;
+            const float mu = A.E_elem ? (float)(cur.E * mat.mu1) : (float)mat.mu;
+            // W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau, m, and the residual moment Q
+            float W[3][3], tau[3][3], Q[3][3], m;
+            bool ok = true;
+            if (mat.law == JETSCI_LINEAR_ELASTIC) {
+                const float rdJ = 1.0f / K.dJ;
 #pragma unroll
-            for (int c = 0; c < 16; c++) dst[c] = v16[c];
+                for (int d = 0; d < 3; d++)
 #pragma unroll
-            for (int c = 0; c < 8; c++) dst[16 + c] = v8[c];
-        }
-    }
-    __syncthreads();
-    // then each row: K[(a,i),(b,k)] = T1[(a,i),(b,k)] + T2[(b,i),(a,k)] + delta_ik geo(a,b)
-    // (T2 is symmetric: its entry ((a,k),(b,i)) is row (b,i), column (a,k))
-    if (w < 3) {
-        for (int g = 0; g < kTgGroups; g++) {
-            float rowv[24];
-            {
-                float v16[16], v8[8];
-                tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * g), v16);
-                tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * g + 16), v8);
+                    for (int j = 0; j < 3; j++) W[d][j] = K.aJ[d][j] * rdJ;
+                float H[3][3], sg[3][3];
 #pragma unroll
-                for (int c = 0; c < 16; c++) rowv[c] = v16[c];
+                for (int i = 0; i < 3; i++)
 #pragma unroll
-                for (int c = 0; c < 8; c++) rowv[16 + c] = v8[c];
-            }
-            const int ee = 4 * g + rel;
-            const int32_t eid = sm.elem[ee];
-            if (eid < 0) continue;
-            const float *t2e = t2 + (96 * g + 24 * rel) * kTgT2Stride;
+                    for (int j = 0; j < 3; j++) H[i][j] = K.Du[i][0] * W[0][j] + K.Du[i][1] * W[1][j] + K.Du[i][2] * W[2][j];
+                const float ltr = lam * (H[0][0] + H[1][1] + H[2][2]);
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const float geo = sm.geo[ee][ra <= b ? tg_pair(ra, b) : tg_pair(b, ra)];
+                for (int i = 0; i < 3; i++)
 #pragma unroll
-                for (int k = 0; k < 3; k++)
-                    rowv[3 * b + k] += t2e[(3 * b + ri) * kTgT2Stride + 3 * ra + k] + (k == ri ? geo : 0.0f);
-            }
-            if (MODE == 0) {
-                // row 3a + i of K_e: 96 contiguous bytes
-                float4 *dst = reinterpret_cast<float4 *>(vals + 576 * (int64_t)eid + 24 * (3 * ra + ri));
+                    for (int j = 0; j < 3; j++) {
+                        sg[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : 0.0f);
+                        tau[i][j] = 0.0f;
+                    }
 #pragma unroll
-                for (int c = 0; c < 6; c++)
-                    dst[c] = make_float4(rowv[4 * c], rowv[4 * c + 1], rowv[4 * c + 2], rowv[4 * c + 3]);
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        Q[i][d] = sg[i][0] * K.aJ[d][0] + sg[i][1] * K.aJ[d][1] + sg[i][2] * K.aJ[d][2];
+                m = mu;
             } else {
-                float s = 0.0f;
+                NeoHookeanState<float> st;
+                neo_hookean_state(K, lam, mu, st);
+                ok = st.ok;
+                m = st.m;
+                const float sc = K.dJ * st.rdj;
 #pragma unroll
-                for (int b = 0; b < 8; b++)
+                for (int d = 0; d < 3; d++)
 #pragma unroll
-                    for (int k = 0; k < 3; k++) s += rowv[3 * b + k] * sm.vnode[ee][b][k];
-                y[3 * (int64_t)sm.node[ee][ra] + ri] += to_double(s);
+                    for (int j = 0; j < 3; j++) {
+                        W[d][j] = st.aj[d][j] * st.rdj;
+                        tau[d][j] = st.tau[d][j];
+                    }
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        Q[i][d] = sc * (st.tau[i][0] * st.aj[d][0] + st.tau[i][1] * st.aj[d][1] + st.tau[i][2] * st.aj[d][2]);
             }
+            if (active) {
+                const uint32_t bits = (K.dJ > 0.0f ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE);
+                if (bits) atomicOr(A.flags, bits);
+            }
+            const float cw = K.dJ * (1.0f / 512.0f);
+            const float cl = cw * lam, cm = cw * m;
+            const float t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
+            const float t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
+            const float xp = 1.0f + K.xi, xm = 1.0f - K.xi, yp = 1.0f + K.eta, ym = 1.0f - K.eta;
+            const float zp = 1.0f + K.zeta, zm = 1.0f - K.zeta;
+            unsigned char *At = sm.A[w];
+            unsigned char *Bt = sm.B[w];
+            const int kc = 8 * el + l;  // this lane's column of A and B
+            float g[8][3], tg[8][3];
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const int bits = hex_bits_of_node(a);
+                const float fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
+                const float yz = fy * fz, xz = fx * fz, xy = fx * fy;
+                const float n0 = (bits & 1) ? yz : -yz, n1 = (bits & 2) ? xz : -xz, n2 = (bits & 4) ? xy : -xy;
+#pragma unroll
+                for (int j = 0; j < 3; j++) g[a][j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
+                tg[a][0] = t00 * g[a][0] + t01 * g[a][1] + t02 * g[a][2];
+                tg[a][1] = t01 * g[a][0] + t11 * g[a][1] + t12 * g[a][2];
+                tg[a][2] = t02 * g[a][0] + t12 * g[a][1] + t22 * g[a][2];
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    // A: the element's own row block (the other elements' rows of this column
+                    // hold the zeros written at the start)
+                    *reinterpret_cast<float *>(At + tg_offset(24 * el + 3 * a + i, kc)) = to_tf32(g[a][i]);
+                    *reinterpret_cast<float *>(Bt + tg_offset(3 * a + i, kc)) = to_tf32(cl * g[a][i]);
+                    *reinterpret_cast<float *>(Bt + tg_offset(24 + 3 * a + i, kc)) = to_tf32(cm * g[a][i]);
+                }
+            }
+            // geometric term: d_p = tg_a . g_b for the 36 pairs, summed over the 8 Gauss-point lanes
+            // by a reduce-scatter (halves exchanged across lanes 4, 2, 1 apart); lane l ends with
+            // the sums of pairs 18 (l>>2 & 1) + 9 (l>>1 & 1) + 5 (l & 1) + j, j < 5 (< 4 for odd l)
+            float d[36];
+#pragma unroll
+            for (int a = 0; a < 8; a++)
+#pragma unroll
+                for (int bb = a; bb < 8; bb++)
+                    d[tg_pair(a, bb)] = tg[a][0] * g[bb][0] + tg[a][1] * g[bb][1] + tg[a][2] * g[bb][2];
+            const bool h4 = (l >> 2) & 1, h2 = (l >> 1) & 1, h1 = l & 1;
+            float d18[18], d9[9], d5[5];
+#pragma unroll
+            for (int j = 0; j < 18; j++) {
+                const float keep = h4 ? d[18 + j] : d[j], give = h4 ? d[j] : d[18 + j];
+                d18[j] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+            }
+#pragma unroll
+            for (int j = 0; j < 9; j++) {
+                const float keep = h2 ? d18[9 + j] : d18[j], give = h2 ? d18[j] : d18[9 + j];
+                d9[j] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+            }
+#pragma unroll
+            for (int j = 0; j < 5; j++) {
+                const float lo = d9[j], hi = j + 5 < 9 ? d9[j + 5] : 0.0f;
+                const float keep = h1 ? hi : lo, give = h1 ? lo : hi;
+                d5[j] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
+            }
+            const int p0 = 18 * h4 + 9 * h2 + 5 * h1;
+#pragma unroll
+            for (int j = 0; j < 5; j++)
+                if (5 * h1 + j < 9) sm.geo[es][p0 + j] = d5[j];
+            // residual: nodal forces of the lane's node
+            float f[3];
+            nodal_force_of_moment(Q, K, l, f);
+            if (R && active)
+#pragma unroll
+                for (int i = 0; i < 3; i++) R[3 * (8 * e + hex_node_of_lane(l)) + i] = to_double(f[i]);
+            if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
         }
+        // the next batch's coordinates and displacements (its connectivity has arrived)
+        if (b + G < n_batches) tf32_gather_values(A, u, nxt);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (t == 0) {
+            const uint32_t id = tc::idesc_tf32(128, kTgN);
+            for (int g = 0; g < kTgGroups; g++) {
+                const uint32_t a0 = tc::smem_addr(sm.A[g]), b0 = tc::smem_addr(sm.B[g]);
+                // one MMA of K = 8 covers two core matrices along K
+                for (int kk = 0; kk < kTgK / 8; kk++)
+                    tc::mma_tf32(tm + kTgCols * g, tc::smem_desc(a0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO),
+                                 tc::smem_desc(b0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO), id, kk > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&sm.mbar);
+        }
+        const bool ok = tc::mbar_wait_bounded(&sm.mbar, it & 1);
+        tc::fence_after_sync();
+        if (!ok && t == 0) atomicOr(A.flags, JETSCI_FLAG_NONFINITE);
+        // ---------------- epilogue: thread t owns accumulator row r = t of each group (TMEM lane
+        // t); rows 96..127 (warp 3) carry nothing.  Two groups at a time: their T2 rows into the
+        // transposition buffer, then each row
+        //   K[(a,i),(b,k)] = T1[(a,i),(b,k)] + T2[(b,i),(a,k)] + delta_ik geo(a,b)
+        // (T2 is symmetric: its entry ((a,k),(b,i)) is row (b,i), column (a,k)).
+        const int r = t, rel = r / 24, ra = (r % 24) / 3, ri = r % 3;
+        for (int g0 = 0; g0 < kTgGroups; g0 += kTgT2Groups) {
+            if (w < 3) {
+#pragma unroll
+                for (int gg = 0; gg < kTgT2Groups; gg++) {
+                    float v16[16], v8[8];
+                    tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * (g0 + gg) + 24), v16);
+                    tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * (g0 + gg) + 40), v8);
+                    float *dst = sm.t2[gg] + r * kTgT2Stride;
+#pragma unroll
+                    for (int c = 0; c < 16; c++) dst[c] = v16[c];
+#pragma unroll
+                    for (int c = 0; c < 8; c++) dst[16 + c] = v8[c];
+                }
+            }
+            __syncthreads();
+            if (w < 3) {
+#pragma unroll 1
+                for (int gg = 0; gg < kTgT2Groups; gg++) {
+                    const int g = g0 + gg;
+                    float rowv[24];
+                    {
+                        float v16[16], v8[8];
+                        tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * g), v16);
+                        tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * g + 16), v8);
+#pragma unroll
+                        for (int c = 0; c < 16; c++) rowv[c] = v16[c];
+#pragma unroll
+                        for (int c = 0; c < 8; c++) rowv[16 + c] = v8[c];
+                    }
+                    const int ee = 4 * g + rel;
+                    const int32_t eid = sm.elem[ee];
+                    if (eid < 0) continue;
+                    const float *t2e = sm.t2[gg] + 24 * rel * kTgT2Stride;
+#pragma unroll
+                    for (int bb = 0; bb < 8; bb++) {
+                        const float geo = sm.geo[ee][ra <= bb ? tg_pair(ra, bb) : tg_pair(bb, ra)];
+#pragma unroll
+                        for (int k = 0; k < 3; k++)
+                            rowv[3 * bb + k] += t2e[(3 * bb + ri) * kTgT2Stride + 3 * ra + k] + (k == ri ? geo : 0.0f);
+                    }
+                    // row 3a + i of K_e: 96 contiguous bytes
+                    float4 *dst = reinterpret_cast<float4 *>(vals + 576 * (int64_t)eid + 24 * (3 * ra + ri));
+#pragma unroll
+                    for (int c = 0; c < 6; c++)
+                        dst[c] = make_float4(rowv[4 * c], rowv[4 * c + 1], rowv[4 * c + 2], rowv[4 * c + 3]);
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();  // the buffer, geo and elem are reused; the next MMA overwrites TMEM
+            tc::fence_after_sync();
+        }
+        cur = nxt;
+        if (b + 2 * G < n_batches) tf32_gather_conn(A, b + 2 * G, es, l, nxt);
     }
     tc::fence_before_sync();
     __syncthreads();
     if (w == 0) tc::tmem_dealloc(tm, kTgTmemCols);
 }
 
-jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float *vals, double *R, double *y,
-                          const double *E_elem, cudaStream_t s) {
+jetsci_status launch_tf32(jetsci_mesh m, const double *u, float *vals, double *R, const double *E_elem,
+                          cudaStream_t s) {
     Tf32Args A;
     A.conn = m->d_conn;
     A.coords = m->d_coords;
@@ -326,33 +379,24 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float
     A.E_elem = E_elem;
     A.flags = m->d_flags;
     const size_t smem = sizeof(TgSmem);
-    if (vals) {
-        // row-gather assembly: element rows (one launch, elements in order), then the row pass
-        void *ws = nullptr;
-        double *Re = nullptr;
-        if (jetsci_status st = ensure_block_workspace(m, blk_full_bytes(m->n_elem, sizeof(float)), s, &ws, &Re))
-            return st;
-        if (!R) Re = nullptr;
-        if (m->n_elem > 0) {
-            if (jetsci_status st = kernel_attrs_once<k_tf32<0>>(smem, false)) return st;
-            A.elems = nullptr;
-            A.n = m->n_elem;
-            const unsigned grid = (unsigned)((A.n + kTgElems - 1) / kTgElems);
-            k_tf32<0><<<grid, 128, smem, s>>>(A, u, nullptr, (float *)ws, Re, nullptr);
-            JETSCI_CUDA_TRY(cudaGetLastError());
-        }
-        return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);
+    // row-gather assembly: element rows (one persistent launch, elements in order), then the row pass
+    void *ws = nullptr;
+    double *Re = nullptr;
+    if (jetsci_status st = ensure_block_workspace(m, blk_full_bytes(m->n_elem, sizeof(float)), s, &ws, &Re))
+        return st;
+    if (!R) Re = nullptr;
+    if (m->n_elem > 0) {
+        if (jetsci_status st = kernel_attrs_once<k_tf32>(smem, false)) return st;
+        int sms = 0;
+        JETSCI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+        A.n = m->n_elem;
+        const int64_t n_batches = (A.n + kTgElems - 1) / kTgElems;
+        // two CTAs per SM: 256 TMEM columns and about 104 KB of shared memory each
+        const unsigned grid = (unsigned)std::min<int64_t>(n_batches, 2 * (int64_t)std::max(sms, 1));
+        k_tf32<<<grid, 128, smem, s>>>(A, u, (float *)ws, Re);
+        JETSCI_CUDA_TRY(cudaGetLastError());
     }
-    if (jetsci_status st = kernel_attrs_once<k_tf32<1>>(smem, false)) return st;
-    JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
-    for_each_colour(m, [&](const int32_t *elems, int64_t n) {
-        A.elems = elems;
-        A.n = n;
-        unsigned grid = (unsigned)((A.n + kTgElems - 1) / kTgElems);
-        k_tf32<1><<<grid, 128, smem, s>>>(A, u, v, nullptr, nullptr, y);
-    });
-    JETSCI_CUDA_TRY(cudaGetLastError());
-    return JETSCI_OK;
+    return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);
 }
 
 }  // namespace jetsci

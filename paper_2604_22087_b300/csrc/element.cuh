@@ -317,20 +317,12 @@ __device__ __forceinline__ void lin_load(const double *__restrict__ lin, int64_t
     rdj = f[kLinRdj];
 }
 
-// Gathers coordinates and one nodal field for element e, forms coefficients (FP64) and the
-// kinematics at the lane's Gauss point.  `node` receives the global node of the lane.
+// Kinematics at the lane's Gauss point from the lane's node's coordinates X and nodal field
+// values U (gathered by the caller): coefficients (FP64 differences, element.cuh header), Jp,
+// adj(Jp), det Jp and Du.
 template <typename T>
-__device__ __forceinline__ void gauss_kinematics_coords(const int32_t *__restrict__ conn,
-                                                        const double *__restrict__ coords,
-                                                        const double *__restrict__ u, int64_t e, int l,
-                                                        int32_t &node, GaussKinematics<T> &K, T cu[3]) {
-    node = conn[8 * e + hex_node_of_lane(l)];
-    double X[3], U[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        X[i] = coords[3 * (int64_t)node + i];
-        U[i] = u ? u[3 * (int64_t)node + i] : 0.0;
-    }
+__device__ __forceinline__ void gauss_kinematics_of(const double X[3], const double U[3], int l,
+                                                    GaussKinematics<T> &K, T cu[3]) {
     T cx[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) {
@@ -348,6 +340,23 @@ __device__ __forceinline__ void gauss_kinematics_coords(const int32_t *__restric
     }
     adj3(K.Jp, K.aJ);
     K.dJ = K.Jp[0][0] * K.aJ[0][0] + K.Jp[0][1] * K.aJ[1][0] + K.Jp[0][2] * K.aJ[2][0];
+}
+
+// Gathers coordinates and one nodal field for element e, forms coefficients (FP64) and the
+// kinematics at the lane's Gauss point.  `node` receives the global node of the lane.
+template <typename T>
+__device__ __forceinline__ void gauss_kinematics_coords(const int32_t *__restrict__ conn,
+                                                        const double *__restrict__ coords,
+                                                        const double *__restrict__ u, int64_t e, int l,
+                                                        int32_t &node, GaussKinematics<T> &K, T cu[3]) {
+    node = conn[8 * e + hex_node_of_lane(l)];
+    double X[3], U[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        X[i] = coords[3 * (int64_t)node + i];
+        U[i] = u ? u[3 * (int64_t)node + i] : 0.0;
+    }
+    gauss_kinematics_of<T>(X, U, l, K, cu);
 }
 
 // The kinematics of gauss_kinematics_coords.  FP64 and two-float elements read Jp, adj(Jp) and

@@ -127,8 +127,8 @@ jetsci_status launch_spmv(jetsci_mesh m, const void *vals, bool fp32, const doub
                           double *y, cudaStream_t s);
 jetsci_status launch_norm2(const double *x, int64_t n, double *partials, int64_t cap,
                            double *out, cudaStream_t s);
-jetsci_status launch_tf32(jetsci_mesh m, const double *u, const double *v, float *vals, double *R, double *y,
-                          const double *E_elem, cudaStream_t s);
+jetsci_status launch_tf32(jetsci_mesh m, const double *u, float *vals, double *R, const double *E_elem,
+                          cudaStream_t s);
 jetsci_status launch_surrogate(jetsci_mesh m, const double *u, float *vals, double *R, cudaStream_t s);
 jetsci_status launch_insert_blocks(jetsci_mesh m, const void *Ke, void *vals, bool fp32, cudaStream_t s);
 // The mesh's element-block workspace (blocks.cuh): values_bytes of blocks, then the residual
