@@ -41,6 +41,9 @@ METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % o
 # slot map and masks 96 + u, R and connectivity 82 + the reference-geometry cache 1,216 + the
 # stored linearisation 768).
 TANGENT_FP64_FLOP_PER_ELEM = 16_860.0
+# The same operations counted as FP64-pipe instructions (7,400 DFMA + 628 DADD + 1,432 DMUL): each
+# takes one slot of the pipe (2 per clock per SM), whatever its flop count.
+TANGENT_FP64_INSTR_PER_ELEM = 9_460.0
 TANGENT_BYTES_PER_ELEM_FP64 = 4_121.0
 # DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
@@ -782,7 +785,14 @@ def main():
                          "traffic_note": "bytes per tangent call (8 colour launches), ncu at 64^3 scaled by elements",
                          "kernel": "k_tangent<double,double>",
                          "peak_source": "FP64 pipe: 2 DFMA/clk/SM (measured FP64 FMA rate) x 2 flop x 148 SMs x the maximum SM clock",
-                         "ms_per_launch_group": ms_tangent, "hbm_achieved_gbs": hbm,
+                         "ms_per_launch_group": ms_tangent,
+                         "fp64_pipe_instr_frac": TANGENT_FP64_INSTR_PER_ELEM * prob.n_elem / (ms_tangent * 1e-3) /
+                                                 (2.0 * 148 * peaks.get("sm_max_mhz", 2032.0) * 1e6),
+                         "fp64_pipe_instr_note": "FP64-pipe instructions (DFMA, DADD, DMUL: 9,460 per element, ncu) "
+                                                 "per second over the pipe's 2 per clock per SM: the share of the "
+                                                 "pipe's issue slots the executed work fills (frac counts a DADD or "
+                                                 "DMUL as 1 flop against a peak of 2)",
+                         "hbm_achieved_gbs": hbm,
                          "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind},
             "e2e": {"value": world * prob.n_elem / (e2e_ms * 1e-3), "unit": "elem/s",
                     "h2d_bytes_per_step": 2 * prob.n_dof * 8, "d2h_bytes_per_step": prob.n_dof * 8 + 8,

@@ -264,3 +264,68 @@ def test_surrogate_mixed_in_range_and_fallback_points():
     # the plain law alone at the same state is far from the mixed result (both kinds matter)
     om_R = oracle.residual(om, prob.u)
     assert rel(r["R"], om_R) > 10 * (share_R + 2e-4)
+
+
+def test_trained_surrogate_in_the_element_kernel():
+    """The network trained on neo-Hookean labels by the library's own kernels (2^16 samples,
+    20 epochs), fused into the element kernel on the 16^3 sphere RVE at a 1% stretch: R and K
+    against the oracle's surrogate element routine with the trained weights (entry-wise
+    bounds as above), and against the plain neo-Hookean oracle within the error the training
+    left (its largest stress error on held-out strains, pushed through the residual definition
+    with absolute values): the learned law stands in for the plain one in the assembled system,
+    not only point by point."""
+    n = 1 << 16
+    E6s, phs = I.strain_samples(n, seed=5)
+    E6d, phd = torch.as_tensor(E6s).cuda(), torch.as_tensor(phs).cuda()
+    mats = I.composite_materials(I.LAW_NEO_HOOKEAN)
+    Sd = J().Surrogate.label(mats, E6d, phd)
+    cfg = config()
+    s = J().Surrogate(I.mlp_init(5), **cfg)
+    epochs, batch = 20, 2048
+    order = torch.as_tensor(I.minibatch_order(n, epochs, seed=5)).cuda()
+    s.train(E6d, phd, Sd, order, n_steps=epochs * (n // batch), batch=batch, lr_max=3e-3, lr_min=1e-5)
+    prob = I.sphere_composite(16, seed=1, law=I.LAW_NEO_HOOKEAN)
+    prob.u = I.uniform_field(prob.coords.size, 1e-3, 11) + np.repeat(prob.coords[:, :1] * 0.01, 3, 1).ravel() * \
+        np.tile([1.0, 0.0, 0.0], prob.n_nodes)
+    mesh = J().Mesh.of(prob)
+    J().attach_surrogate(mesh, s)
+    u = torch.as_tensor(prob.u).cuda()
+    R = mesh.new_vector()
+    vals = mesh.tangent_csr(u, R=R, precision=J().SURROGATE)
+    assert J().surrogate_fallbacks(mesh) == 0 and mesh.check() == 0
+    rp, col = mesh.pattern()
+    Kg = _csr_to_dense(rp.cpu().numpy(), col.cpu().numpy(), vals.cpu().numpy().astype(np.float64), mesh.n_dof)
+    layers = s.layers()
+    om = oracle.Mesh.of(prob)
+    K, Rref, fb, E6 = surrogate_fem.assemble(om, prob.u, layers, cfg["in_scale"], cfg["range_"], cfg["out_scale"],
+                                             cfg["out_shift"])
+    assert fb == 0 and np.max(np.abs(E6)) < cfg["range_"] - 1e-5
+    r = dict(Kg=Kg, Rg=R.cpu().numpy(), K=K, R=Rref, layers=layers, cfg=cfg)
+    share_R, share_K = _check_within(r, prob, cfg["range_"])
+    assert share_R <= 0.25 and share_K <= 0.25
+    # the trained network against the plain law: held-out stress error, then the assembled system
+    Et, pt = I.strain_samples(4096, seed=99)
+    S_true = J().Surrogate.label(mats, torch.as_tensor(Et).cuda(), torch.as_tensor(pt).cuda()).cpu().numpy()
+    S_net = s.eval(torch.as_tensor(Et).cuda(), torch.as_tensor(pt).cuda(), tangent=False).cpu().numpy()
+    # largest stress error of the trained network over held-out strains of the training box,
+    # per phase (absolute, Pa); twice that bounds it at the RVE's strains, which lie in the box
+    dS = [2.0 * float(np.max(np.abs(S_net - S_true)[pt == p])) for p in (0, 1)]
+    # pushed through R_e(a,i) = sum_q w detJ (F S)_iJ G_aJ with absolute values: |dR_ai| <= dS
+    # sum_q detJ sum_IJ |F_iI| |G_aJ|, summed over the elements of each DOF
+    bR = np.zeros(om.n_dof)
+    for e in range(om.n_elem):
+        en = om.conn[e].astype(np.int64)
+        ue = prob.u[(3 * en[:, None] + np.arange(3))].reshape(8, 3)
+        w = np.zeros(24)
+        for G, detJ in surrogate_fem._geometry(om.coords[en]):
+            F = np.eye(3) + ue.T @ G
+            w += detJ * (np.abs(F).sum(axis=1)[None, :] * np.abs(G).sum(axis=1)[:, None]).ravel()
+        bR[(3 * en[:, None] + np.arange(3)).ravel()] += dS[int(om.phase[e])] * w
+    R_nh = oracle.residual(om, prob.u)
+    err = np.abs(r["Rg"] - R_nh)
+    assert np.all(err <= bR + 2e-4 * np.max(np.abs(R_nh))), float(np.max(err / (bR + 1e-300)))
+    # and it is the network's error, not the bound's looseness, that separates the two
+    assert rel(r["Rg"], R_nh) > 10 * rel(r["Rg"], r["R"])
+    s.close()
+    J().attach_surrogate(mesh, None)
+    mesh.close()
