@@ -26,12 +26,12 @@ def problem():
 
 def _step(J, mesh, u, v, vals, R, y_mf, y_csr, nrm, precision):
     mesh.tangent_csr(u, vals=vals, R=R, precision=precision)
-    mesh.apply_tangent(u, v, y=y_mf, precision=J.FP64 if precision == J.FP64 else J.FP32)
+    mesh.apply_tangent(u, v, y=y_mf, precision=precision)
     mesh.apply_tangent(None, v, y=y_csr, mode=J.CSR, vals=vals, precision=precision)
     mesh.norm2(R, out=nrm)
 
 
-@pytest.mark.parametrize("name", ["FP64", "FP32"])
+@pytest.mark.parametrize("name", ["FP64", "FP32", "TF32", "DF64"])
 def test_captured_step_replays_bitwise(problem, name):
     J = jetsci()
     p = getattr(J, name)
