@@ -189,12 +189,12 @@ jetsci_status jetsci_tangent_csr(jetsci_mesh mesh, const double *u_dev, void *va
  * mode JETSCI_CSR: sparse product with the CSR values vals_dev of the same mesh
  * (double for FP64/DF64, float for FP32/TF32/SURROGATE); u_dev is ignored.
  * u_dev, v_dev, y_dev [n_dof] FP64; y overwritten.  y must not alias u or v.
- * Matrix-free FP64 with u_dev = NULL applies K at the linearisation stored by the mesh's last
- * FP64 jetsci_residual or jetsci_tangent_csr call (its u; the neo-Hookean state per Gauss point
- * is kept, 768 bytes per element, so the product skips u and that state): for repeated
- * products at one Newton iterate.  E_elem_dev must be the pointer that call used; the calls
- * must be ordered on the stream(s).  Otherwise (no such call, another precision, another
- * E_elem_dev) JETSCI_ERR_ARG.
+ * Matrix-free FP64 or DF64 with u_dev = NULL applies K at the linearisation stored by the mesh's
+ * last FP64 or DF64 jetsci_residual or jetsci_tangent_csr call (its u; the neo-Hookean state per
+ * Gauss point is kept in FP64, 768 bytes per element, so the product skips u and that state):
+ * for repeated products at one Newton iterate.  E_elem_dev must be the pointer that call used;
+ * the calls must be ordered on the stream(s).  Otherwise (no such call, FP32/TF32/SURROGATE,
+ * another E_elem_dev) JETSCI_ERR_ARG.
  */
 jetsci_status jetsci_apply_tangent(jetsci_mesh mesh, const double *u_dev, const double *v_dev,
                                    double *y_dev, int32_t mode, const void *vals_dev,

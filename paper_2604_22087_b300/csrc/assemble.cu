@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     T Q[3][3];
     NeoHookeanState<T> st;
     const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q, &st);
-    if constexpr (std::is_same<T, double>::value)
-        if (A.lin && active && mt.law != JETSCI_LINEAR_ELASTIC) lin_store(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
+    if constexpr (!std::is_same<T, float>::value)  // FP64 and two-float calls store the state
+        if (A.lin && active && mt.law != JETSCI_LINEAR_ELASTIC) lin_store_t<T>(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
     T f[3];
     nodal_force_of_moment(Q, K, l, f);
     if (active) {
@@ -318,8 +318,8 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             neo_hookean_state(K, lam, mu, st);
             ok = st.ok;
             m = st.m;
-            if constexpr (std::is_same<T, double>::value)
-                if (A.lin && active) lin_store(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
+            if constexpr (!std::is_same<T, float>::value)  // FP64 and two-float calls store the state
+                if (A.lin && active) lin_store_t<T>(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
 #pragma unroll
             for (int d = 0; d < 3; d++)
 #pragma unroll
@@ -608,8 +608,8 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 // Q = Y adj(Jp)^T directly:
 //   Q = (mu / det Jp) Dv adj(Jp) adj(Jp)^T + (det Jp / det j^2) M' adj(j)^T,
 //   M' = m h'^T + lam tr(h') I,  h' = Dv adj(j) = det j h.
-// kReuse (FP64 only): the neo-Hookean state comes from the mesh's linearisation store (the
-// last FP64 residual or tangent, at its u) instead of u; u is not read.
+// kReuse (FP64 and two-float): the neo-Hookean state comes from the mesh's linearisation store
+// (the last FP64 or two-float residual or tangent, at its u) instead of u; u is not read.
 template <typename T, bool kReuse>
 __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__restrict__ u,
                                                  const double *__restrict__ v, double *__restrict__ y) {
@@ -620,8 +620,8 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
     int32_t node;
     GaussKinematics<T> K;
     if constexpr (kReuse) {
-        static_assert(std::is_same<T, double>::value, "the linearisation store is FP64");
-        gauss_geometry(A.conn, A.geom, e, l, node, K);
+        static_assert(!std::is_same<T, float>::value, "the linearisation store serves FP64 and two-float products");
+        gauss_geometry<T>(A.conn, A.geom, e, l, node, K);
     } else {
         T cu[3];
         gauss_kinematics<T>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
@@ -652,7 +652,7 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
     } else {
         T m, rdj, rdJ, aj[3][3];
         if constexpr (kReuse) {
-            lin_load(A.lin, e, l, aj, m, rdJ, rdj);  // (states outside the law were flagged when stored)
+            lin_load_t<T>(A.lin, e, l, aj, m, rdJ, rdj);  // (states outside the law were flagged when stored)
         } else {
             NeoHookeanState<T> st;
             neo_hookean_state(K, lam, mu, st);
@@ -883,8 +883,12 @@ jetsci_status launch_residual(jetsci_mesh m, const double *u, double *R, int pre
     }
     else if (precision == JETSCI_FP32 || precision == JETSCI_TF32)
         residual_colours<float>(m, A, u, R, s);
-    else if (precision == JETSCI_DF64)
+    else if (precision == JETSCI_DF64) {
+        A.lin = m->d_lin;  // the linearisation at u (two-float values rounded to double)
+        m->lin_valid = true;
+        m->lin_E = E_elem;
         residual_colours<df64>(m, A, u, R, s);
+    }
     else if (precision == JETSCI_SURROGATE)
         return launch_surrogate(m, u, nullptr, R, s);
     else
@@ -960,6 +964,9 @@ jetsci_status launch_tangent(jetsci_mesh m, const double *u, void *vals, double 
     if (precision == JETSCI_DF64) {
         JETSCI_CUDA_TRY(cudaMemsetAsync(vals, 0, m->nnz * sizeof(double), s));
         if (R) JETSCI_CUDA_TRY(cudaMemsetAsync(R, 0, m->n_dof * sizeof(double), s));
+        A.lin = m->d_lin;  // the linearisation at u (two-float values rounded to double)
+        m->lin_valid = true;
+        m->lin_E = E_elem;
         return tangent_colours<df64, double>(m, A, u, (double *)vals, R, s);
     }
     if (precision == JETSCI_TF32) return launch_tf32(m, u, (float *)vals, R, E_elem, s);
@@ -987,9 +994,12 @@ jetsci_status launch_apply_mf(jetsci_mesh m, const double *u, const double *v, d
     if (precision == JETSCI_TF32) precision = JETSCI_FP32;
     JETSCI_CUDA_TRY(cudaMemsetAsync(y, 0, m->n_dof * sizeof(double), s));
     ElemArgs A = make_args(m, E_elem);
-    if (!u) {  // at the stored FP64 linearisation (checked by the caller)
+    if (!u) {  // at the stored linearisation (checked by the caller), in FP64 or two-float arithmetic
         A.lin = m->d_lin;
-        apply_colours<double, true>(m, A, nullptr, v, y, s);
+        if (precision == JETSCI_DF64)
+            apply_colours<df64, true>(m, A, nullptr, v, y, s);
+        else
+            apply_colours<double, true>(m, A, nullptr, v, y, s);
     } else if (precision == JETSCI_FP64)
         apply_colours<double>(m, A, u, v, y, s);
     else if (precision == JETSCI_FP32)

@@ -51,11 +51,12 @@ extern "C" jetsci_status jetsci_apply_tangent(jetsci_mesh m, const double *u, co
         return launch_spmv(m, vals, fp32, v, y, s);
     }
     if (!u) {
-        // K(u) v at the stored linearisation of the last FP64 residual or tangent call
-        if (precision != JETSCI_FP64)
-            return fail(JETSCI_ERR_ARG, "u is NULL: a stored linearisation exists for JETSCI_FP64 only");
+        // K(u) v at the stored linearisation of the last FP64 or two-float residual or tangent call
+        if (precision != JETSCI_FP64 && precision != JETSCI_DF64)
+            return fail(JETSCI_ERR_ARG, "u is NULL: a stored linearisation exists for JETSCI_FP64 and JETSCI_DF64 only");
         if (!m->lin_valid)
-            return fail(JETSCI_ERR_ARG, "u is NULL and no FP64 residual or tangent call has stored a linearisation");
+            return fail(JETSCI_ERR_ARG,
+                        "u is NULL and no FP64 or two-float residual or tangent call has stored a linearisation");
         if (E_elem != m->lin_E)
             return fail(JETSCI_ERR_ARG, "u is NULL: E_elem differs from the call that stored the linearisation");
     }

@@ -284,8 +284,8 @@ __device__ __forceinline__ double2 geom_pair(const double *__restrict__ p, int k
     return __ldg(reinterpret_cast<const double2 *>(p + 16 * k));
 }
 
-// Linearisation of the neo-Hookean state at the last FP64 residual or tangent call, kept per
-// mesh for matrix-free products at that state: adj(j) (0-8), m (9), 1 / det Jp (10) and
+// Linearisation of the neo-Hookean state at the last FP64 or two-float residual or tangent call,
+// kept per mesh for matrix-free products at that state: adj(j) (0-8), m (9), 1 / det Jp (10) and
 // 1 / det j (11) per element and Gauss point, in pairs as [element][6][Gauss point][2] doubles.
 constexpr int kLinAj = 0, kLinM = 9, kLinRdJ = 10, kLinRdj = 11, kLinPairs = 6;
 
@@ -296,6 +296,19 @@ __device__ __forceinline__ void lin_store(double *__restrict__ lin, int64_t e, i
     double2 *p = reinterpret_cast<double2 *>(lin + (int64_t)2 * kLinPairs * 8 * e + 2 * l);
 #pragma unroll
     for (int k = 0; k < kLinPairs; k++) p[8 * k] = make_double2(f[2 * k], f[2 * k + 1]);
+}
+
+// The state of a two-float (or FP64) neo-Hookean update, stored in FP64 (two-float values rounded
+// to the nearest double, about 48 significant bits either way).
+template <typename T>
+__device__ __forceinline__ void lin_store_t(double *__restrict__ lin, int64_t e, int l, const T aj[3][3], T m, T rdJ,
+                                            T rdj) {
+    double a[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) a[i][k] = to_double(aj[i][k]);
+    lin_store(lin, e, l, a, to_double(m), to_double(rdJ), to_double(rdj));
 }
 
 __device__ __forceinline__ void lin_load(const double *__restrict__ lin, int64_t e, int l, double aj[3][3], double &m,
@@ -315,6 +328,21 @@ __device__ __forceinline__ void lin_load(const double *__restrict__ lin, int64_t
     m = f[kLinM];
     rdJ = f[kLinRdJ];
     rdj = f[kLinRdj];
+}
+
+// The stored state in the element type T (FP64 as stored; two-float by splitting each double).
+template <typename T>
+__device__ __forceinline__ void lin_load_t(const double *__restrict__ lin, int64_t e, int l, T aj[3][3], T &m, T &rdJ,
+                                           T &rdj) {
+    double a[3][3], md, rJ, rj;
+    lin_load(lin, e, l, a, md, rJ, rj);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) aj[i][k] = from_double<T>(a[i][k]);
+    m = from_double<T>(md);
+    rdJ = from_double<T>(rJ);
+    rdj = from_double<T>(rj);
 }
 
 // Kinematics at the lane's Gauss point from the lane's node's coordinates X and nodal field
@@ -417,12 +445,13 @@ __device__ __forceinline__ void gauss_kinematics(const int32_t *__restrict__ con
     }
 }
 
-// The reference geometry of the lane's Gauss point alone (FP64, from the cache): node, xi,
-// eta, zeta, Jp, adj(Jp), det Jp; K.Du is not formed.
+// The reference geometry of the lane's Gauss point alone (from the FP64 cache, in the element
+// type): node, xi, eta, zeta, Jp, adj(Jp), det Jp; K.Du is not formed.
+template <typename T>
 __device__ __forceinline__ void gauss_geometry(const int32_t *__restrict__ conn, const double *__restrict__ geom,
-                                               int64_t e, int l, int32_t &node, GaussKinematics<double> &K) {
+                                               int64_t e, int l, int32_t &node, GaussKinematics<T> &K) {
     node = conn[8 * e + hex_node_of_lane(l)];
-    const double g = kGaussG;
+    const T g = (T)kGaussG;
     K.xi = (l & 1) ? g : -g;
     K.eta = (l & 2) ? g : -g;
     K.zeta = (l & 4) ? g : -g;
@@ -438,10 +467,10 @@ __device__ __forceinline__ void gauss_geometry(const int32_t *__restrict__ conn,
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            K.Jp[i][j] = gf[kGeomJp + 3 * i + j];
-            K.aJ[i][j] = gf[kGeomAJ + 3 * i + j];
+            K.Jp[i][j] = from_double<T>(gf[kGeomJp + 3 * i + j]);
+            K.aJ[i][j] = from_double<T>(gf[kGeomAJ + 3 * i + j]);
         }
-    K.dJ = gf[kGeomDJ];
+    K.dJ = from_double<T>(gf[kGeomDJ]);
 }
 
 // A0 = adj(Jp) adj(Jp)^T of the matrix-free neo-Hookean product (symmetric).

@@ -40,7 +40,7 @@ struct jetsci_mesh_s {
     int32_t *d_conn = nullptr;          // [n_elem*8]
     double *d_coords = nullptr;         // [n_nodes*3]
     double *d_lin = nullptr;            // [n_elem][6][8][2]: FP64 neo-Hookean linearisation (element.cuh)
-    bool lin_valid = false;             // d_lin holds the state of an FP64 residual/tangent call
+    bool lin_valid = false;             // d_lin holds the state of an FP64 or two-float residual/tangent call
     const double *lin_E = nullptr;      // ... made with this per-element modulus array (or NULL)
     double *d_re = nullptr;             // [n_elem][8][3]: element residual vectors R_e kept by the last
                                         // residual call given a per-element modulus field

@@ -119,9 +119,9 @@ def test_apply_tangent_csr_fp64(case):
 
 
 def test_matrix_free_at_stored_linearisation(case):
-    """An FP64 tangent (or residual) stores the neo-Hookean state at its u; a matrix-free
-    product with u = NULL applies K at that state.  It must equal the product that forms the
-    state from u (the same arithmetic on the same values) and the oracle."""
+    """An FP64 or two-float tangent (or residual) stores the neo-Hookean state at its u; a
+    matrix-free product with u = NULL applies K at that state.  It must equal the product that
+    forms the state from u (the same arithmetic on the same values) and the oracle."""
     prob, mesh, _, ref = case
     J = jetsci()
     u, v = cuda(prob.u), cuda(prob.v)
@@ -135,9 +135,16 @@ def test_matrix_free_at_stored_linearisation(case):
     mesh.residual(u2)
     y2 = mesh.apply_tangent(None, v)
     assert relerr(y2.cpu().numpy(), mesh.apply_tangent(u2, v).cpu().numpy()) <= 1e-14
-    # other precisions do not touch it
+    # FP32 calls do not touch it
     mesh.tangent_csr(u, precision=J.FP32)
     assert relerr(mesh.apply_tangent(None, v).cpu().numpy(), y2.cpu().numpy()) == 0.0
+    # a two-float tangent stores its state too (rounded to double); the two-float product at it
+    # matches the two-float product formed from u and the oracle
+    mesh.tangent_csr(u, precision=J.DF64)
+    y_df = mesh.apply_tangent(None, v, precision=J.DF64)
+    assert relerr(y_df.cpu().numpy(), mesh.apply_tangent(u, v, precision=J.DF64).cpu().numpy()) <= 1e-13
+    assert relerr(y_df.cpu().numpy(), ref["y_mf"]) <= FP64_TOL
+    assert relerr(mesh.apply_tangent(None, v).cpu().numpy(), ref["y_mf"]) <= FP64_TOL
 
 
 def test_matrix_free_linearisation_errors():
@@ -149,7 +156,7 @@ def test_matrix_free_linearisation_errors():
         mesh.apply_tangent(None, v)
     assert ei.value.status == 1
     mesh.residual(u)
-    with pytest.raises(J.JetsciError):  # stored in FP64 only
+    with pytest.raises(J.JetsciError):  # stored for FP64 and two-float products only
         mesh.apply_tangent(None, v, precision=J.FP32)
     E = torch.full((mesh.n_elem,), 1e9, dtype=torch.float64, device="cuda")
     with pytest.raises(J.JetsciError):  # the state belongs to the phase moduli, not to E

@@ -243,9 +243,13 @@ def test_checkpoint_round_trip(data, tmp_path):
     t.close()
 
 
-def test_training_reduces_error_and_beats_the_baselines():
-    """Train on NH labels with the library's kernels; the trained network is far closer to
-    the plain law than the untrained network and than small-strain Hooke."""
+def test_training_learns_the_neo_hookean_law():
+    """Train on NH labels with the library's kernels: the trained network is far closer to the
+    plain neo-Hookean law than the untrained network and than small-strain Hooke with the same
+    Lame constants (the cheaper law it could otherwise stand in for).  This is what training
+    gains; it is not a gain over the neo-Hookean update itself, which is exact by definition
+    and, evaluated in FP32 on this GPU, cheaper per Gauss point than the network's forward
+    pass."""
     n = 1 << 16
     E6, ph = I.strain_samples(n, seed=5)
     E6d, phd = torch.as_tensor(E6).cuda(), torch.as_tensor(ph).cuda()
