@@ -161,7 +161,15 @@ def config_dict(prob, n):
     return {"workload": f"fibre RVE {n}^3 hex8 neo-Hookean (50% fibres, E 3.5/70 GPa), 1% stretch + 1e-4 noise; "
                         f"step = tangent CSR with fused residual + K.v (CSR SpMV, and matrix-free at the linearisation the tangent stored) + ||R||, FP64",
             "n_elem": prob.n_elem, "n_dof": prob.n_dof, "fibre_fraction": prob.meta.get("fibre_fraction"),
-            "l2": "inputs larger than L2 (CSR values 4.1 GB written and read every step)"}
+            "l2": l2_note(n)}
+
+
+def l2_note(n):
+    # an n^3 grid of hex8 elements couples (3n+1)^3 node pairs, 9 values each
+    gb = 9 * (3 * n + 1) ** 3 * 8 / 1e9
+    if gb > 0.126:
+        return f"inputs larger than L2 (CSR values {gb:.1f} GB written and read every step)"
+    return f"inputs fit in L2 ({gb * 1e3:.1f} MB of CSR values): a parity-size case, not a timed workload"
 
 
 # ------------------------------------------------------------------------------ CPU oracle
@@ -194,11 +202,17 @@ class OracleSlab:
         return time.perf_counter() - t0
 
 
-def calibrated_slab(prob, target_seconds):
-    """A slab sized so that one oracle step takes about target_seconds, and a 512-element one."""
+def calibrated_m(prob, target_seconds):
+    """A 512-element slab, and the element count one oracle step covers in about target_seconds
+    (from the 512-element step's time)."""
     small = OracleSlab(prob, 512)
     dt = min(small.step() for _ in range(2))
-    m = int(min(prob.n_elem, max(512, 512 * target_seconds / max(dt, 1e-6))))
+    return small, int(min(prob.n_elem, max(512, 512 * target_seconds / max(dt, 1e-6))))
+
+
+def calibrated_slab(prob, target_seconds):
+    """A slab sized so that one oracle step takes about target_seconds, and a 512-element one."""
+    small, m = calibrated_m(prob, target_seconds)
     return small, (OracleSlab(prob, m) if m > 512 else small)
 
 
@@ -233,59 +247,86 @@ class _SlabArrays:
 
 
 def _oracle_worker(arrays, pipe):
-    """One process of the all-core leg: sets up its slab (not timed), waits for the start
-    message, runs one oracle step (single-threaded, as it stands) and sends its time back."""
+    """One process of the all-core legs: sets up its slab (not timed), then for every "go"
+    message runs one oracle step (single-threaded, as it stands) and sends its time back, until
+    it receives "stop"."""
     import oracle
     om = oracle.Mesh(arrays.coords, arrays.conn, arrays.phase, arrays.materials)
     rp, col = oracle.csr_pattern(arrays.conn, len(arrays.coords))
     pipe.send("ready")
-    pipe.recv()
-    t0 = time.perf_counter()
-    vals, R = oracle.tangent_csr(om, arrays.u, rp, col)
-    oracle.apply_tangent(om, arrays.u, arrays.v)
-    oracle.spmv(rp, col, vals, arrays.v)
-    oracle.norm2(R)
-    pipe.send(time.perf_counter() - t0)
+    while pipe.recv() == "go":
+        t0 = time.perf_counter()
+        vals, R = oracle.tangent_csr(om, arrays.u, rp, col)
+        oracle.apply_tangent(om, arrays.u, arrays.v)
+        oracle.spmv(rp, col, vals, arrays.v)
+        oracle.norm2(R)
+        pipe.send(time.perf_counter() - t0)
 
 
-def cpu_baseline_all_cores(prob, per_worker_elems, max_workers=64):
-    """The same oracle step on every host core at once: one spawned process per core (at most
-    max_workers), each on its own slab of per_worker_elems elements spread over the workload.
-    value = all processes' elements / wall time from the common start to the last finish."""
-    import multiprocessing as mp
-    P = max(1, min(host_cores(), max_workers))
-    m = int(max(512, min(per_worker_elems, prob.n_elem // P)))
-    starts = [int(k * (prob.n_elem - m) / max(1, P - 1)) for k in range(P)] if P > 1 else [0]
-    ctx = mp.get_context("spawn")
-    procs, pipes = [], []
-    for e0 in starts:
-        a, b = ctx.Pipe()
-        pr = ctx.Process(target=_oracle_worker, args=(_SlabArrays(prob, e0, m), b), daemon=True)
-        pr.start()
-        procs.append(pr)
-        pipes.append(a)
-    def receive(a, pr, deadline):
+class OraclePool:
+    """The oracle on every host core: one spawned process per core (at most max_workers), each
+    with its own slab of m elements spread over the workload.  step() runs one oracle step in
+    every process at once and returns (wall seconds from the common start to the last finish,
+    per-process seconds)."""
+
+    def __init__(self, prob, per_worker_elems, max_workers=64):
+        import multiprocessing as mp
+        self.P = max(1, min(host_cores(), max_workers))
+        self.m = int(max(512, min(per_worker_elems, prob.n_elem // self.P)))
+        starts = [int(k * (prob.n_elem - self.m) / max(1, self.P - 1)) for k in range(self.P)] if self.P > 1 else [0]
+        ctx = mp.get_context("spawn")
+        self.procs, self.pipes = [], []
+        try:
+            for e0 in starts:
+                a, b = ctx.Pipe()
+                pr = ctx.Process(target=_oracle_worker, args=(_SlabArrays(prob, e0, self.m), b), daemon=True)
+                pr.start()
+                self.procs.append(pr)
+                self.pipes.append(a)
+            deadline = time.perf_counter() + 600.0
+            for a, pr in zip(self.pipes, self.procs):
+                if self._receive(a, pr, deadline) != "ready":
+                    raise RuntimeError("oracle worker failed")
+        except BaseException:
+            self.close()
+            raise
+
+    @staticmethod
+    def _receive(a, pr, deadline):
         # a worker that died (or never answers) must not block the bench
         while not a.poll(0.2):
             if not pr.is_alive() or time.perf_counter() > deadline:
                 raise RuntimeError(f"oracle worker exited or timed out (exit code {pr.exitcode})")
         return a.recv()
 
-    try:
-        deadline = time.perf_counter() + 600.0
-        for a, pr in zip(pipes, procs):
-            if receive(a, pr, deadline) != "ready":
-                raise RuntimeError("oracle worker failed")
+    def step(self):
         t0 = time.perf_counter()
-        for a in pipes:
+        for a in self.pipes:
             a.send("go")
-        dts = [receive(a, pr, t0 + 600.0) for a, pr in zip(pipes, procs)]
-        wall = time.perf_counter() - t0
-    finally:
-        for pr in procs:
+        dts = [self._receive(a, pr, t0 + 600.0) for a, pr in zip(self.pipes, self.procs)]
+        return time.perf_counter() - t0, dts
+
+    def close(self):
+        for a in self.pipes:
+            try:
+                a.send("stop")
+            except (BrokenPipeError, OSError):
+                pass
+        for pr in self.procs:
             pr.join(timeout=30)
             if pr.is_alive():
                 pr.terminate()
+
+
+def cpu_baseline_all_cores(prob, per_worker_elems, max_workers=64):
+    """The same oracle step on every host core at once (OraclePool), one step.  value = all
+    processes' elements / wall time from the common start to the last finish."""
+    pool = OraclePool(prob, per_worker_elems, max_workers)
+    try:
+        wall, dts = pool.step()
+    finally:
+        pool.close()
+    P, m = pool.P, pool.m
     return {"value": P * m / wall, "unit": "elem/s", "cores": P, "kind": "oracle", "host_cores": host_cores(),
             "sample": f"{P} processes at once, one per core, each the single-threaded oracle step on its own "
                       f"{m}-element slab of the same workload ({P * m} elements), wall {wall:.1f} s "
@@ -305,25 +346,41 @@ def cpu_baseline(prob, target_seconds):
 
 
 def run_reference(args, rank):
+    """The oracle as it stands on the machine's host cores: every step runs one single-threaded oracle
+    step in each of one process per core, each on its own slab of the workload sized so that the
+    whole --warmup + --steps run takes a few minutes; value = the elements all processes stepped
+    over the step's wall time (median over the timed steps)."""
     if rank != 0:
         return
     prob = make_problem(args.n)
-    # each timed step is one oracle step over a slab sized to keep the run within minutes
     per = max(1.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
-    small, slab = calibrated_slab(prob, per)
-    for _ in range(args.warmup):
-        small.step()
-    times = [slab.step() for _ in range(args.steps)]
-    dt = statistics.median(times)
-    v = slab.m / dt
-    cb = baseline_line(slab, dt)
-    # ms_per_step is the measured time of one step over the slab (the work each timed step did);
-    # the full mesh at this rate would take n_elem / value seconds per step.
+    _, m = calibrated_m(prob, per)  # the elements one core steps in about `per` seconds
+    pool = OraclePool(prob, m)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        walls, per_proc = [], []
+        for _ in range(args.steps):
+            w, dts = pool.step()
+            walls.append(w)
+            per_proc += dts
+    finally:
+        pool.close()
+    wall = statistics.median(walls)
+    elems = pool.P * pool.m
+    v = elems / wall
+    cb = {"value": v, "unit": "elem/s", "cores": pool.P, "kind": "oracle", "host_cores": host_cores(),
+          "sample": f"{pool.P} processes at once, one per host core, each the single-threaded oracle step "
+                    f"(tangent CSR + residual + element K.v + CSR K.v + norm) on its own {pool.m}-element slab of "
+                    f"the same workload ({elems} elements per step); median wall {wall:.2f} s over {args.steps} "
+                    f"steps (per-process {min(per_proc):.2f}-{max(per_proc):.2f} s)"}
+    # ms_per_step is the measured wall time of one step (the work each timed step did); the full
+    # mesh at this rate would take n_elem / value seconds per step.
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elem/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
-            "ms_per_step_note": f"one oracle step over a {slab.m}-element slab of the workload (warm-up steps "
-                                f"on a 512-element slab); the full {prob.n_elem}-element mesh at this rate "
-                                f"would take {prob.n_elem / v:.0f} s per step (extrapolated, not run)",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall,
+            "ms_per_step_note": f"one step = the oracle on {pool.P} host cores over {elems} elements of the workload; "
+                                f"the full {prob.n_elem}-element mesh at this rate would take "
+                                f"{prob.n_elem / v:.1f} s per step (extrapolated, not run)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(prob, args.n), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "elem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -837,12 +894,12 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
         ms = timeit(lambda: mesh.apply_tangent(u, v, y=y, precision=p, stream=stream), stream)
         torch.cuda.synchronize()
         rec(f"apply_matrix_free_{name}", ms, {"err_vs_oracle": so.errors(None, None, gather_rows(y, so.nodes), rp_h, col_h)})
-        if p == J.FP64:
-            # at the linearisation stored by the FP64 tangent call above (u not read again)
+        if p in (J.FP64, J.DF64):
+            # at the linearisation stored by the tangent call above (u not read again)
             mesh.tangent_csr(u, vals=vv, R=R, precision=p, stream=stream)
             ms = timeit(lambda: mesh.apply_tangent(None, v, y=y, precision=p, stream=stream), stream)
             torch.cuda.synchronize()
-            rec("apply_matrix_free_fp64_stored_linearisation", ms,
+            rec(f"apply_matrix_free_{name}_stored_linearisation", ms,
                 {"err_vs_oracle": so.errors(None, None, gather_rows(y, so.nodes), rp_h, col_h)})
         if p in (J.FP64, J.FP32):
             # 100 back-to-back products on the assembled matrix (the paper's repeated-SpMV
@@ -857,16 +914,17 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
             del vv
             torch.cuda.empty_cache()
     # The same step with two-float (DF64) element arithmetic on the FP32 pipes: tangent CSR with
-    # fused R (FP64 values), CSR K.v, matrix-free DF64 K.v (formed from u: the stored
-    # linearisation is FP64-only) and the FP64 norm.  An FP64-accurate alternative reported
-    # beside the IEEE FP64 headline, never in its place.
+    # fused R (FP64 values), CSR K.v, matrix-free DF64 K.v at the linearisation the tangent stored,
+    # and the FP64 norm.  An FP64-accurate alternative reported beside the IEEE FP64 headline,
+    # never in its place.
     nrm = torch.empty(1, dtype=torch.float64, device="cuda")
     y2 = mesh.new_vector()
 
     def df64_step():
         mesh.tangent_csr(u, vals=vals64, R=R, precision=J.DF64, stream=stream)
         mesh.apply_tangent(None, v, y=y2, mode=J.CSR, vals=vals64, precision=J.DF64, stream=stream)
-        mesh.apply_tangent(u, v, y=y, precision=J.DF64, stream=stream)
+        # at the linearisation the two-float tangent stored, as in the FP64 step
+        mesh.apply_tangent(None, v, y=y, precision=J.DF64, stream=stream)
         mesh.norm2(R, out=nrm, stream=stream)
 
     ms = timeit(df64_step, stream)
