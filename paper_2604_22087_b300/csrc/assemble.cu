@@ -96,9 +96,14 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
 // the neo-Hookean CC (F CC F = lam I(x)I + 2 m Isym).  The diagonal-pair thread (a == b) also
 // forms the residual R_a = sum_q c Tg g_a (= sum_q w detJ P G_a).
 //
-// FP64 elements, bound by B300's FP64 pipe, also store c lam g_a and c m g_a, so that an
-// off-diagonal pair costs 21 multiply-adds per Gauss point instead of 27; FP32 and two-float
-// elements keep the smaller record, which leaves room for more resident blocks.
+// With h_a = (c lam + c m)/2 g_a and d_a = (c lam - c m)/2 g_a (so c lam g_a = h_a + d_a and
+// c m g_a = h_a - d_a), an off-diagonal block is K_ab = A + B + diag(A_ii + gs) with
+//   A_ik = sum_q h_ai g_bk + h_ak g_bi  (symmetric),   B_ik = sum_q d_ai g_bk - d_ak g_bi  (skew),
+// K_ab,ik = A_ik + B_ik for i != k and K_ab,ii = 2 sum_q h_ai g_bi + gs_ab, gs_ab = sum_q tg_a . g_b:
+// 18 multiply-adds per Gauss point instead of the 21 of accumulating c lam g_ai g_bk and
+// c m g_ak g_bi separately.  FP64 elements, bound by B300's FP64 pipe, store h_a and d_a; FP32
+// and two-float elements form them from g_a and two coefficients, keeping the smaller record,
+// which leaves room for more resident blocks.
 
 // Shared memory: one array per per-node vector (g, tg and, for FP64, c lam g and c m g), each
 // [element][Gauss point][node][3], nodes 3 entries apart, so that the eight nodes of an element
@@ -123,9 +128,9 @@ struct TangentLayout {
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
     static constexpr int kArr = kElems * kElem;
-    // per (element, Gauss point): c lam, c m, c Tg (00,11,22,12,02,01); odd stride
+    // per (element, Gauss point): (c lam + c m)/2, (c lam - c m)/2, c Tg (00,11,22,12,02,01); odd stride
     static constexpr int kCoef = 9;
-    enum { kG = 0, kTG = 1, kLG = 2, kMG = 3 };
+    enum { kG = 0, kTG = 1, kHG = 2, kDG = 3 };
     // FP64 values: each CSR block's first writer stores and no clearing pass is needed (saves
     // the 4 GB memset at 128^3).  The two-float kernel was measured slower that way (the
     // partial-sector first stores and the divergent store/accumulate paths cost more than the
@@ -149,12 +154,107 @@ struct TangentSmem {
 // predicated off, and an element's diagonal blocks follow its other blocks closely.
 constexpr int kGroup = 8, kGroupItems = kGroup * 36, kGroupOff = kGroup * 28;
 
-// Block K_ab of work item `it` (element slot ee, nodes a <= b) from the phase-1 records; for a
-// diagonal item with want_r also the residual R_a = sum_q c Tg g_a.
-template <typename T>
-__device__ __forceinline__ void tangent_item(const TangentSmem<T> &sm, int it, bool want_r, T Kab[3][3], T Ra[3],
-                                             int &ee, int &a, int &b, bool &off) {
+// Off-diagonal block K_ab (a < b) of element slot ee from the phase-1 records.
+template <typename T, int kUnrollQ>
+__device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, int a, int b, T Kab[3][3]) {
     using L = TangentLayout<T>;
+    const T *pa = sm.v + ee * L::kElem + 3 * a;
+    const T *pb = sm.v + ee * L::kElem + 3 * b;
+    const T *pc = sm.coef + ee * 8 * L::kCoef;
+    T A00 = T(0), A11 = T(0), A22 = T(0), A01 = T(0), A02 = T(0), A12 = T(0);
+    T B01 = T(0), B02 = T(0), B12 = T(0), gs = T(0);
+#pragma unroll kUnrollQ
+    for (int q = 0; q < 8; q++) {
+        const T *qa = pa + q * L::kPoint;
+        const T *qb = pb + q * L::kPoint;
+        const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
+        const T *ta = qa + L::kTG * L::kArr;
+        T h0, h1, h2, d0, d1, d2;
+        if constexpr (L::kPre) {
+            const T *ha = qa + L::kHG * L::kArr, *da = qa + L::kDG * L::kArr;
+            h0 = ha[0], h1 = ha[1], h2 = ha[2], d0 = da[0], d1 = da[1], d2 = da[2];
+        } else {
+            const T *cf = pc + q * L::kCoef;
+            const T ch = cf[0], cd = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
+            h0 = ch * a0, h1 = ch * a1, h2 = ch * a2, d0 = cd * a0, d1 = cd * a1, d2 = cd * a2;
+        }
+        gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
+        A00 = acc_t(h0, b0, A00);
+        A11 = acc_t(h1, b1, A11);
+        A22 = acc_t(h2, b2, A22);
+        A01 = acc_t(h0, b1, acc_t(h1, b0, A01));
+        A02 = acc_t(h0, b2, acc_t(h2, b0, A02));
+        A12 = acc_t(h1, b2, acc_t(h2, b1, A12));
+        B01 = acc_t(d0, b1, acc_t(-d1, b0, B01));
+        B02 = acc_t(d0, b2, acc_t(-d2, b0, B02));
+        B12 = acc_t(d1, b2, acc_t(-d2, b1, B12));
+    }
+    // (two-float running sums are normalised once, here)
+    A00 = acc_norm(A00), A11 = acc_norm(A11), A22 = acc_norm(A22);
+    A01 = acc_norm(A01), A02 = acc_norm(A02), A12 = acc_norm(A12);
+    B01 = acc_norm(B01), B02 = acc_norm(B02), B12 = acc_norm(B12);
+    gs = acc_norm(gs);
+    Kab[0][0] = fma_t(T(2), A00, gs);
+    Kab[1][1] = fma_t(T(2), A11, gs);
+    Kab[2][2] = fma_t(T(2), A22, gs);
+    Kab[0][1] = A01 + B01, Kab[1][0] = A01 - B01;
+    Kab[0][2] = A02 + B02, Kab[2][0] = A02 - B02;
+    Kab[1][2] = A12 + B12, Kab[2][1] = A12 - B12;
+}
+
+// Diagonal block K_aa,ik = 2 sum_q h_ai g_ak + delta_ik sum_q tg_a . g_a of element slot ee and,
+// with want_r, the residual R_a = sum_q c Tg g_a.
+template <typename T, int kUnrollQ>
+__device__ __forceinline__ void diag_block(const TangentSmem<T> &sm, int ee, int a, bool want_r, T Kab[3][3],
+                                           T Ra[3]) {
+    using L = TangentLayout<T>;
+    const T *pa = sm.v + ee * L::kElem + 3 * a;
+    const T *pc = sm.coef + ee * 8 * L::kCoef;
+    T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
+    T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
+#pragma unroll kUnrollQ
+    for (int q = 0; q < 8; q++) {
+        const T *qa = pa + q * L::kPoint;
+        const T *cf = pc + q * L::kCoef;
+        const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
+        const T *ta = qa + L::kTG * L::kArr;
+        T h0, h1, h2;
+        if constexpr (L::kPre) {
+            const T *ha = qa + L::kHG * L::kArr;
+            h0 = ha[0], h1 = ha[1], h2 = ha[2];
+        } else {
+            const T ch = cf[0];
+            h0 = ch * b0, h1 = ch * b1, h2 = ch * b2;
+        }
+        gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
+        k00 = acc_t(h0, b0, k00);
+        k11 = acc_t(h1, b1, k11);
+        k22 = acc_t(h2, b2, k22);
+        k12 = acc_t(h1, b2, k12);
+        k02 = acc_t(h0, b2, k02);
+        k01 = acc_t(h0, b1, k01);
+        if (want_r) {
+            Ra0 = acc_t(cf[2], b0, acc_t(cf[7], b1, acc_t(cf[6], b2, Ra0)));
+            Ra1 = acc_t(cf[7], b0, acc_t(cf[3], b1, acc_t(cf[5], b2, Ra1)));
+            Ra2 = acc_t(cf[6], b0, acc_t(cf[5], b1, acc_t(cf[4], b2, Ra2)));
+        }
+    }
+    k00 = acc_norm(k00), k11 = acc_norm(k11), k22 = acc_norm(k22);
+    k12 = acc_norm(k12), k02 = acc_norm(k02), k01 = acc_norm(k01);
+    gs = acc_norm(gs);
+    Kab[0][0] = fma_t(T(2), k00, gs);
+    Kab[1][1] = fma_t(T(2), k11, gs);
+    Kab[2][2] = fma_t(T(2), k22, gs);
+    Kab[1][2] = Kab[2][1] = k12 + k12;
+    Kab[0][2] = Kab[2][0] = k02 + k02;
+    Kab[0][1] = Kab[1][0] = k01 + k01;
+    Ra[0] = acc_norm(Ra0);
+    Ra[1] = acc_norm(Ra1);
+    Ra[2] = acc_norm(Ra2);
+}
+
+// Work item `it` of a group (element slot ee, nodes a <= b, off = a < b).
+__device__ __forceinline__ void item_nodes(int it, int &ee, int &a, int &b, bool &off) {
     const int grp = it / kGroupItems, r = it - kGroupItems * grp;
     off = r < kGroupOff;
     if (off) {
@@ -169,85 +269,18 @@ __device__ __forceinline__ void tangent_item(const TangentSmem<T> &sm, int it, b
         ee = kGroup * grp + (j >> 3);
         a = b = j & 7;
     }
-    const T *pa = sm.v + ee * L::kElem + 3 * a;
-    const T *pb = sm.v + ee * L::kElem + 3 * b;
-    const T *pc = sm.coef + ee * 8 * L::kCoef;
-    if (off) {
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
-        T gs = T(0);
-#pragma unroll 2
-        for (int q = 0; q < 8; q++) {
-            const T *qa = pa + q * L::kPoint;
-            const T *qb = pb + q * L::kPoint;
-            const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
-            const T *ta = qa + L::kTG * L::kArr;
-            T l0, l1, l2, m0, m1, m2;
-            if constexpr (L::kPre) {
-                const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
-                l0 = la[0], l1 = la[1], l2 = la[2], m0 = ma[0], m1 = ma[1], m2 = ma[2];
-            } else {
-                const T *cf = pc + q * L::kCoef;
-                const T lam = cf[0], m = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
-                l0 = lam * a0, l1 = lam * a1, l2 = lam * a2, m0 = m * a0, m1 = m * a1, m2 = m * a2;
-            }
-            gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
-            Kab[0][0] = fma_t(l0, b0, fma_t(m0, b0, Kab[0][0]));
-            Kab[0][1] = fma_t(l0, b1, fma_t(m1, b0, Kab[0][1]));
-            Kab[0][2] = fma_t(l0, b2, fma_t(m2, b0, Kab[0][2]));
-            Kab[1][0] = fma_t(l1, b0, fma_t(m0, b1, Kab[1][0]));
-            Kab[1][1] = fma_t(l1, b1, fma_t(m1, b1, Kab[1][1]));
-            Kab[1][2] = fma_t(l1, b2, fma_t(m2, b1, Kab[1][2]));
-            Kab[2][0] = fma_t(l2, b0, fma_t(m0, b2, Kab[2][0]));
-            Kab[2][1] = fma_t(l2, b1, fma_t(m1, b2, Kab[2][1]));
-            Kab[2][2] = fma_t(l2, b2, fma_t(m2, b2, Kab[2][2]));
-        }
-        Kab[0][0] += gs;
-        Kab[1][1] += gs;
-        Kab[2][2] += gs;
-    } else {
-        // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
-        T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
-        T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
-#pragma unroll 2
-        for (int q = 0; q < 8; q++) {
-            const T *qa = pa + q * L::kPoint;
-            const T *cf = pc + q * L::kCoef;
-            const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
-            const T *ta = qa + L::kTG * L::kArr;
-            T s0, s1, s2;
-            if constexpr (L::kPre) {
-                const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
-                s0 = la[0] + ma[0], s1 = la[1] + ma[1], s2 = la[2] + ma[2];
-            } else {
-                const T lm = cf[0] + cf[1];
-                s0 = lm * b0, s1 = lm * b1, s2 = lm * b2;
-            }
-            gs = fma_t(ta[0], b0, fma_t(ta[1], b1, fma_t(ta[2], b2, gs)));
-            k00 = fma_t(s0, b0, k00);
-            k11 = fma_t(s1, b1, k11);
-            k22 = fma_t(s2, b2, k22);
-            k12 = fma_t(s1, b2, k12);
-            k02 = fma_t(s0, b2, k02);
-            k01 = fma_t(s0, b1, k01);
-            if (want_r) {
-                Ra0 = fma_t(cf[2], b0, fma_t(cf[7], b1, fma_t(cf[6], b2, Ra0)));
-                Ra1 = fma_t(cf[7], b0, fma_t(cf[3], b1, fma_t(cf[5], b2, Ra1)));
-                Ra2 = fma_t(cf[6], b0, fma_t(cf[5], b1, fma_t(cf[4], b2, Ra2)));
-            }
-        }
-        Kab[0][0] = k00 + gs;
-        Kab[1][1] = k11 + gs;
-        Kab[2][2] = k22 + gs;
-        Kab[1][2] = Kab[2][1] = k12;
-        Kab[0][2] = Kab[2][0] = k02;
-        Kab[0][1] = Kab[1][0] = k01;
-        Ra[0] = Ra0;
-        Ra[1] = Ra1;
-        Ra[2] = Ra2;
-    }
+}
+
+// Block K_ab of work item `it` from the phase-1 records; for a diagonal item with want_r also
+// the residual R_a.
+template <typename T>
+__device__ __forceinline__ void tangent_item(const TangentSmem<T> &sm, int it, bool want_r, T Kab[3][3], T Ra[3],
+                                             int &ee, int &a, int &b, bool &off) {
+    item_nodes(it, ee, a, b, off);
+    if (off)
+        offdiag_block<T, 2>(sm, ee, a, b, Kab);
+    else
+        diag_block<T, 2>(sm, ee, a, want_r, Kab, Ra);
 }
 
 // Shared memory of the rows mode: the block's element matrices [element][24][24], as in the
@@ -335,6 +368,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         }
         const T cw = K.dJ * T(1.0 / 512.0);
         const T cl = cw * lam, cm = cw * m;
+        const T ch = T(0.5) * (cl + cm), cd = T(0.5) * (cl - cm);
         // c (tau + m I), tau = 0 in the linear law's tangent
         const T t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
         const T t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
@@ -363,8 +397,8 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                 g[j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
                 r[L::kG * L::kArr + j] = g[j];
                 if constexpr (L::kPre) {
-                    r[L::kLG * L::kArr + j] = cl * g[j];
-                    r[L::kMG * L::kArr + j] = cm * g[j];
+                    r[L::kHG * L::kArr + j] = ch * g[j];
+                    r[L::kDG * L::kArr + j] = cd * g[j];
                 }
             }
             r[L::kTG * L::kArr + 0] = t00 * g[0] + t01 * g[1] + t02 * g[2];
@@ -372,8 +406,8 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             r[L::kTG * L::kArr + 2] = t02 * g[0] + t12 * g[1] + t22 * g[2];
         }
         T *pc = sm.coef + (es * 8 + l) * L::kCoef;
-        pc[0] = cl;
-        pc[1] = cm;
+        pc[0] = ch;
+        pc[1] = cd;
         pc[2] = cw * Tg[0][0];
         pc[3] = cw * Tg[1][1];
         pc[4] = cw * Tg[2][2];
@@ -392,70 +426,16 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         // arithmetic otherwise stalls on instruction fetch: 0.9% faster at 128^3)
         constexpr int kUnrollQ = std::is_same<T, df64>::value ? 1 : 2;
         for (int it = threadIdx.x; it < L::kElems * 36; it += blockDim.x) {
-            const int grp = it / kGroupItems, r = it - kGroupItems * grp;
-            const bool off = r < kGroupOff;
             int ee, a, b;
-            if (off) {
-                const int eg = r / 28;
-                const int p = r - 28 * eg;
-                ee = kGroup * grp + eg;
-                // p -> (a, b), a < b, in row order: row a starts at 7a - a(a-1)/2
-                a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
-                b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
-            } else {
-                const int j = r - kGroupOff;
-                ee = kGroup * grp + (j >> 3);
-                a = b = j & 7;
-            }
+            bool off;
+            item_nodes(it, ee, a, b, off);
             const int32_t eid = sm.elem[ee];
             if (eid < 0) continue;
-            const T *pa = sm.v + ee * L::kElem + 3 * a;
-            const T *pb = sm.v + ee * L::kElem + 3 * b;
-            const T *pc = sm.coef + ee * 8 * L::kCoef;
             const int32_t na = sm.node[ee][a];
             const int64_t sbase = 64 * (int64_t)eid;
             T Kab[3][3];
             if (off) {
-#pragma unroll
-                for (int i = 0; i < 3; i++)
-#pragma unroll
-                    for (int k = 0; k < 3; k++) Kab[i][k] = T(0);
-                T gs = T(0);
-#pragma unroll kUnrollQ
-                for (int q = 0; q < 8; q++) {
-                    const T *qa = pa + q * L::kPoint;
-                    const T *qb = pb + q * L::kPoint;
-                    const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
-                    const T *ta = qa + L::kTG * L::kArr;
-                    T l0, l1, l2, m0, m1, m2;
-                    if constexpr (L::kPre) {
-                        const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
-                        l0 = la[0], l1 = la[1], l2 = la[2], m0 = ma[0], m1 = ma[1], m2 = ma[2];
-                    } else {
-                        const T *cf = pc + q * L::kCoef;
-                        const T lam = cf[0], m = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
-                        l0 = lam * a0, l1 = lam * a1, l2 = lam * a2, m0 = m * a0, m1 = m * a1, m2 = m * a2;
-                    }
-                    gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
-                    Kab[0][0] = acc_t(l0, b0, acc_t(m0, b0, Kab[0][0]));
-                    Kab[0][1] = acc_t(l0, b1, acc_t(m1, b0, Kab[0][1]));
-                    Kab[0][2] = acc_t(l0, b2, acc_t(m2, b0, Kab[0][2]));
-                    Kab[1][0] = acc_t(l1, b0, acc_t(m0, b1, Kab[1][0]));
-                    Kab[1][1] = acc_t(l1, b1, acc_t(m1, b1, Kab[1][1]));
-                    Kab[1][2] = acc_t(l1, b2, acc_t(m2, b1, Kab[1][2]));
-                    Kab[2][0] = acc_t(l2, b0, acc_t(m0, b2, Kab[2][0]));
-                    Kab[2][1] = acc_t(l2, b1, acc_t(m1, b2, Kab[2][1]));
-                    Kab[2][2] = acc_t(l2, b2, acc_t(m2, b2, Kab[2][2]));
-                }
-                // (two-float running sums are normalised once, here)
-#pragma unroll
-                for (int i = 0; i < 3; i++)
-#pragma unroll
-                    for (int k = 0; k < 3; k++) Kab[i][k] = acc_norm(Kab[i][k]);
-                gs = acc_norm(gs);
-                Kab[0][0] += gs;
-                Kab[1][1] += gs;
-                Kab[2][2] += gs;
+                offdiag_block<T, kUnrollQ>(sm, ee, a, b, Kab);
                 {
                     const int32_t nb = sm.node[ee][b];
                     const int sab = slotmap[sbase + 8 * a + b];
@@ -477,46 +457,9 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                     }
                 }
             } else {
-                // a == b: K_aa,ik = sum_q (c lam + c m) g_ai g_ak + delta_ik sum_q tg_a . g_a
-                T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
-                T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
-#pragma unroll kUnrollQ
-                for (int q = 0; q < 8; q++) {
-                    const T *qa = pa + q * L::kPoint;
-                    const T *cf = pc + q * L::kCoef;
-                    const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
-                    const T *ta = qa + L::kTG * L::kArr;
-                    T s0, s1, s2;
-                    if constexpr (L::kPre) {
-                        const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr;
-                        s0 = la[0] + ma[0], s1 = la[1] + ma[1], s2 = la[2] + ma[2];
-                    } else {
-                        const T lm = cf[0] + cf[1];
-                        s0 = lm * b0, s1 = lm * b1, s2 = lm * b2;
-                    }
-                    gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
-                    k00 = acc_t(s0, b0, k00);
-                    k11 = acc_t(s1, b1, k11);
-                    k22 = acc_t(s2, b2, k22);
-                    k12 = acc_t(s1, b2, k12);
-                    k02 = acc_t(s0, b2, k02);
-                    k01 = acc_t(s0, b1, k01);
-                    if (R) {
-                        Ra0 = acc_t(cf[2], b0, acc_t(cf[7], b1, acc_t(cf[6], b2, Ra0)));
-                        Ra1 = acc_t(cf[7], b0, acc_t(cf[3], b1, acc_t(cf[5], b2, Ra1)));
-                        Ra2 = acc_t(cf[6], b0, acc_t(cf[5], b1, acc_t(cf[4], b2, Ra2)));
-                    }
-                }
-                k00 = acc_norm(k00), k11 = acc_norm(k11), k22 = acc_norm(k22);
-                k12 = acc_norm(k12), k02 = acc_norm(k02), k01 = acc_norm(k01);
-                gs = acc_norm(gs);
-                Ra0 = acc_norm(Ra0), Ra1 = acc_norm(Ra1), Ra2 = acc_norm(Ra2);
-                Kab[0][0] = k00 + gs;
-                Kab[1][1] = k11 + gs;
-                Kab[2][2] = k22 + gs;
-                Kab[1][2] = Kab[2][1] = k12;
-                Kab[0][2] = Kab[2][0] = k02;
-                Kab[0][1] = Kab[1][0] = k01;
+                T Ra[3];
+                diag_block<T, kUnrollQ>(sm, ee, a, R != nullptr, Kab, Ra);
+                const T Ra0 = Ra[0], Ra1 = Ra[1], Ra2 = Ra[2];
                 {
                     const int saa = slotmap[sbase + 9 * a];
                     const bool faa = kFirst && ((sm.first[ee][a] >> a) & 1);
@@ -567,17 +510,9 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         for (int j = 0; j < kIters; j++) {
             const int it = threadIdx.x + j * L::kThreads;
             if (it < kItems) {
-                const int grp = it / kGroupItems, r = it - kGroupItems * grp;
                 int ee, a, b;
-                if (r < kGroupOff) {
-                    const int eg = r / 28, p = r - 28 * eg;
-                    ee = kGroup * grp + eg;
-                    a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
-                    b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
-                } else {
-                    ee = kGroup * grp + ((r - kGroupOff) >> 3);
-                    a = b = (r - kGroupOff) & 7;
-                }
+                bool off;
+                item_nodes(it, ee, a, b, off);
                 VT *me = mat + (size_t)ee * 576;
 #pragma unroll
                 for (int i = 0; i < 3; i++)
