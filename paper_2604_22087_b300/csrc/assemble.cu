@@ -19,6 +19,7 @@ struct ElemArgs {
     const int32_t *__restrict__ conn;
     const double *__restrict__ coords;
     const double *__restrict__ geom;    // per-element reference geometry (read by the FP64 kernels)
+    const double *__restrict__ lap;     // per-element L_ab (element.cuh, kLap*; read by the tangent)
     double *lin;                        // FP64 linearisation store (element.cuh, kLin*): written by
                                         // the FP64 residual and tangent when set
     double *re;                         // element residual store [n_elem][8][3]: written by the
@@ -87,25 +88,28 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
 
 // ---------------------------------------------------------------------------- tangent
 // Phase 1 (8 lanes per element, lane = Gauss point): kinematics and constitutive update; per
-// Gauss point the spatial gradients g_a = F^-T G_a of the eight shape functions, the vectors
-// tg_a = c (tau + m I) g_a and the coefficients c lam, c m and c Tg go to shared memory
-// (c = w detJ, tau = F S F^T the Kirchhoff stress, m = mu - lam lnJ; the linear law has g = G,
-// m = mu, tau = 0 and Tg = sigma).  Phase 2 (one thread per element and node pair a <= b):
-//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi ] + delta_ik sum_q tg_a . g_b
+// Gauss point the spatial gradients g_a = F^-T G_a of the eight shape functions and the
+// coefficients c lam, c m and c Tg go to shared memory (c = w detJ, Tg the stress paired with g
+// in the residual: the Kirchhoff stress tau = F S F^T for the neo-Hookean law, sigma for the
+// linear one; m = mu - lam lnJ, and the linear law has g = G and m = mu).  Phase 2 (one thread
+// per element and node pair a <= b):
+//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi ] + delta_ik mu L_ab
 // which is the push-forward of sum_q w detJ G_aJ (delta_ik S_JL + F_iI CC_IJKL F_kK) G_bL for
-// the neo-Hookean CC (F CC F = lam I(x)I + 2 m Isym).  The diagonal-pair thread (a == b) also
-// forms the residual R_a = sum_q c Tg g_a (= sum_q w detJ P G_a).
+// the neo-Hookean CC (F CC F = lam I(x)I + 2 m Isym); L_ab = sum_q detJ G_a . G_b is the
+// element's reference Laplacian from the mesh's cache (element.cuh, kLap*), because the
+// geometric term sum_q c g_a^T (tau + m I) g_b equals mu L_ab for both laws.  The diagonal-pair
+// thread (a == b) also forms the residual R_a = sum_q c Tg g_a (= sum_q w detJ P G_a).
 //
 // With h_a = (c lam + c m)/2 g_a and d_a = (c lam - c m)/2 g_a (so c lam g_a = h_a + d_a and
-// c m g_a = h_a - d_a), an off-diagonal block is K_ab = A + B + diag(A_ii + gs) with
+// c m g_a = h_a - d_a), the block is, for i != k, K_ab,ik = A_ik + B_ik with
 //   A_ik = sum_q h_ai g_bk + h_ak g_bi  (symmetric),   B_ik = sum_q d_ai g_bk - d_ak g_bi  (skew),
-// K_ab,ik = A_ik + B_ik for i != k and K_ab,ii = 2 sum_q h_ai g_bi + gs_ab, gs_ab = sum_q tg_a . g_b:
-// 18 multiply-adds per Gauss point instead of the 21 of accumulating c lam g_ai g_bk and
-// c m g_ak g_bi separately.  FP64 elements, bound by B300's FP64 pipe, store h_a and d_a; FP32
-// and two-float elements form them from g_a and two coefficients, keeping the smaller record,
-// which leaves room for more resident blocks.
+// and K_ab,ii = 2 sum_q h_ai g_bi + mu L_ab: 15 multiply-adds per Gauss point, against 21 for
+// accumulating c lam g_ai g_bk, c m g_ak g_bi and the geometric term tg_a . g_b separately.
+// FP64 elements, bound by B300's FP64 pipe, store h_a and d_a; FP32 and two-float elements form
+// them from g_a and two coefficients, keeping the smaller record, which leaves room for more
+// resident blocks.
 
-// Shared memory: one array per per-node vector (g, tg and, for FP64, c lam g and c m g), each
+// Shared memory: one array per per-node vector (g and, for FP64, h and d), each
 // [element][Gauss point][node][3], nodes 3 entries apart, so that the eight nodes of an element
 // read in phase 2 fall on distinct banks.  Elements are 200 entries apart (8 mod 32 words for
 // FP32, 16 mod 32 for 8-byte types), which also spreads the up to four elements of one warp
@@ -124,13 +128,13 @@ struct TangentLayout {
     // are held in registers until the matrices are assembled, and three items per thread
     // instead of five were 5% faster (four warps: slower).
     static constexpr int kThreads = kPre ? 192 : (std::is_same<T, float>::value ? 96 : 8 * kElems);
-    static constexpr int kNumVec = kPre ? 4 : 2;
+    static constexpr int kNumVec = kPre ? 3 : 1;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
     static constexpr int kArr = kElems * kElem;
     // per (element, Gauss point): (c lam + c m)/2, (c lam - c m)/2, c Tg (00,11,22,12,02,01); odd stride
     static constexpr int kCoef = 9;
-    enum { kG = 0, kTG = 1, kHG = 2, kDG = 3 };
+    enum { kG = 0, kHG = 1, kDG = 2 };
     // FP64 values: each CSR block's first writer stores and no clearing pass is needed (saves
     // the 4 GB memset at 128^3).  The two-float kernel was measured slower that way (the
     // partial-sector first stores and the divergent store/accumulate paths cost more than the
@@ -145,6 +149,7 @@ struct TangentSmem {
     T coef[TangentLayout<T>::kElems * 8 * TangentLayout<T>::kCoef];
     int32_t node[TangentLayout<T>::kElems][8];
     int32_t elem[TangentLayout<T>::kElems];
+    T mu[TangentLayout<T>::kElems];
     uint8_t first[TangentLayout<T>::kElems][8];  // first-writer bits of each node's blocks (FP64)
 };
 
@@ -156,19 +161,18 @@ constexpr int kGroup = 8, kGroupItems = kGroup * 36, kGroupOff = kGroup * 28;
 
 // Off-diagonal block K_ab (a < b) of element slot ee from the phase-1 records.
 template <typename T, int kUnrollQ>
-__device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, int a, int b, T Kab[3][3]) {
+__device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, int a, int b, T gs, T Kab[3][3]) {
     using L = TangentLayout<T>;
     const T *pa = sm.v + ee * L::kElem + 3 * a;
     const T *pb = sm.v + ee * L::kElem + 3 * b;
     const T *pc = sm.coef + ee * 8 * L::kCoef;
     T A00 = T(0), A11 = T(0), A22 = T(0), A01 = T(0), A02 = T(0), A12 = T(0);
-    T B01 = T(0), B02 = T(0), B12 = T(0), gs = T(0);
+    T B01 = T(0), B02 = T(0), B12 = T(0);
 #pragma unroll kUnrollQ
     for (int q = 0; q < 8; q++) {
         const T *qa = pa + q * L::kPoint;
         const T *qb = pb + q * L::kPoint;
         const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
-        const T *ta = qa + L::kTG * L::kArr;
         T h0, h1, h2, d0, d1, d2;
         if constexpr (L::kPre) {
             const T *ha = qa + L::kHG * L::kArr, *da = qa + L::kDG * L::kArr;
@@ -178,7 +182,6 @@ __device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, 
             const T ch = cf[0], cd = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
             h0 = ch * a0, h1 = ch * a1, h2 = ch * a2, d0 = cd * a0, d1 = cd * a1, d2 = cd * a2;
         }
-        gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
         A00 = acc_t(h0, b0, A00);
         A11 = acc_t(h1, b1, A11);
         A22 = acc_t(h2, b2, A22);
@@ -193,7 +196,6 @@ __device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, 
     A00 = acc_norm(A00), A11 = acc_norm(A11), A22 = acc_norm(A22);
     A01 = acc_norm(A01), A02 = acc_norm(A02), A12 = acc_norm(A12);
     B01 = acc_norm(B01), B02 = acc_norm(B02), B12 = acc_norm(B12);
-    gs = acc_norm(gs);
     Kab[0][0] = fma_t(T(2), A00, gs);
     Kab[1][1] = fma_t(T(2), A11, gs);
     Kab[2][2] = fma_t(T(2), A22, gs);
@@ -202,22 +204,21 @@ __device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, 
     Kab[1][2] = A12 + B12, Kab[2][1] = A12 - B12;
 }
 
-// Diagonal block K_aa,ik = 2 sum_q h_ai g_ak + delta_ik sum_q tg_a . g_a of element slot ee and,
+// Diagonal block K_aa,ik = 2 sum_q h_ai g_ak + delta_ik gs (gs = mu L_aa) of element slot ee and,
 // with want_r, the residual R_a = sum_q c Tg g_a.
 template <typename T, int kUnrollQ>
-__device__ __forceinline__ void diag_block(const TangentSmem<T> &sm, int ee, int a, bool want_r, T Kab[3][3],
+__device__ __forceinline__ void diag_block(const TangentSmem<T> &sm, int ee, int a, bool want_r, T gs, T Kab[3][3],
                                            T Ra[3]) {
     using L = TangentLayout<T>;
     const T *pa = sm.v + ee * L::kElem + 3 * a;
     const T *pc = sm.coef + ee * 8 * L::kCoef;
     T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
-    T gs = T(0), Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
+    T Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
 #pragma unroll kUnrollQ
     for (int q = 0; q < 8; q++) {
         const T *qa = pa + q * L::kPoint;
         const T *cf = pc + q * L::kCoef;
         const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
-        const T *ta = qa + L::kTG * L::kArr;
         T h0, h1, h2;
         if constexpr (L::kPre) {
             const T *ha = qa + L::kHG * L::kArr;
@@ -226,7 +227,6 @@ __device__ __forceinline__ void diag_block(const TangentSmem<T> &sm, int ee, int
             const T ch = cf[0];
             h0 = ch * b0, h1 = ch * b1, h2 = ch * b2;
         }
-        gs = acc_t(ta[0], b0, acc_t(ta[1], b1, acc_t(ta[2], b2, gs)));
         k00 = acc_t(h0, b0, k00);
         k11 = acc_t(h1, b1, k11);
         k22 = acc_t(h2, b2, k22);
@@ -241,7 +241,6 @@ __device__ __forceinline__ void diag_block(const TangentSmem<T> &sm, int ee, int
     }
     k00 = acc_norm(k00), k11 = acc_norm(k11), k22 = acc_norm(k22);
     k12 = acc_norm(k12), k02 = acc_norm(k02), k01 = acc_norm(k01);
-    gs = acc_norm(gs);
     Kab[0][0] = fma_t(T(2), k00, gs);
     Kab[1][1] = fma_t(T(2), k11, gs);
     Kab[2][2] = fma_t(T(2), k22, gs);
@@ -253,8 +252,9 @@ __device__ __forceinline__ void diag_block(const TangentSmem<T> &sm, int ee, int
     Ra[2] = acc_norm(Ra2);
 }
 
-// Work item `it` of a group (element slot ee, nodes a <= b, off = a < b).
-__device__ __forceinline__ void item_nodes(int it, int &ee, int &a, int &b, bool &off) {
+// Work item `it` of a group (element slot ee, nodes a <= b, off = a < b; li = the pair's index in
+// the element's L_ab, element.cuh kLap*).
+__device__ __forceinline__ void item_nodes(int it, int &ee, int &a, int &b, bool &off, int &li) {
     const int grp = it / kGroupItems, r = it - kGroupItems * grp;
     off = r < kGroupOff;
     if (off) {
@@ -264,23 +264,34 @@ __device__ __forceinline__ void item_nodes(int it, int &ee, int &a, int &b, bool
         // p -> (a, b), a < b, in row order: row a starts at 7a - a(a-1)/2
         a = (p >= 7) + (p >= 13) + (p >= 18) + (p >= 22) + (p >= 25) + (p >= 27);
         b = p - (7 * a - (a * (a - 1)) / 2) + a + 1;
+        li = p;
     } else {
         const int j = r - kGroupOff;
         ee = kGroup * grp + (j >> 3);
         a = b = j & 7;
+        li = kLapDiag + a;
     }
+}
+
+// The geometric term mu L_ab of item (ee, li) (an inactive slot reads element 0's entry).
+template <typename T>
+__device__ __forceinline__ T item_gs(const TangentSmem<T> &sm, const double *__restrict__ lap, int ee, int li) {
+    const int64_t eid = sm.elem[ee] < 0 ? 0 : sm.elem[ee];
+    return sm.mu[ee] * from_double<T>(__ldg(lap + kLapPairs * eid + li));
 }
 
 // Block K_ab of work item `it` from the phase-1 records; for a diagonal item with want_r also
 // the residual R_a.
 template <typename T>
-__device__ __forceinline__ void tangent_item(const TangentSmem<T> &sm, int it, bool want_r, T Kab[3][3], T Ra[3],
-                                             int &ee, int &a, int &b, bool &off) {
-    item_nodes(it, ee, a, b, off);
+__device__ __forceinline__ void tangent_item(const TangentSmem<T> &sm, const double *__restrict__ lap, int it,
+                                             bool want_r, T Kab[3][3], T Ra[3], int &ee, int &a, int &b, bool &off) {
+    int li;
+    item_nodes(it, ee, a, b, off, li);
+    const T gs = item_gs(sm, lap, ee, li);
     if (off)
-        offdiag_block<T, 2>(sm, ee, a, b, Kab);
+        offdiag_block<T, 2>(sm, ee, a, b, gs, Kab);
     else
-        diag_block<T, 2>(sm, ee, a, want_r, Kab, Ra);
+        diag_block<T, 2>(sm, ee, a, want_r, gs, Kab, Ra);
 }
 
 // Shared memory of the rows mode: the block's element matrices [element][24][24], as in the
@@ -320,12 +331,11 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         gauss_kinematics<T, false, false>(A.conn, A.coords, u, e, l, node, K, cu, A.geom);
         ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
         const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
-        // Per law: W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau of the geometric term,
-        // Tg (the stress paired with g in the residual) and m.
-        T W[3][3], tau[3][3], Tg[3][3], m;
+        // Per law: W with g_a = W^T (8 dN_a/dxi), Tg (the stress paired with g in the residual) and m.
+        T W[3][3], Tg[3][3], m;
         bool ok = true;
         if (mt.law == JETSCI_LINEAR_ELASTIC) {
-            // g = G: W = Jp^-1; sigma = lam tr(H) I + mu (H + H^T), H = Du Jp^-1; tau = 0
+            // g = G: W = Jp^-1; sigma = lam tr(H) I + mu (H + H^T), H = Du Jp^-1
             const T rdJ = my_rcp(K.dJ);
 #pragma unroll
             for (int d = 0; d < 3; d++)
@@ -342,7 +352,6 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     Tg[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : T(0));
-                    tau[i][j] = T(0);
                 }
             m = mu;
         } else {
@@ -358,7 +367,6 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     W[d][j] = st.aj[d][j] * st.rdj;
-                    tau[d][j] = st.tau[d][j];
                     Tg[d][j] = st.tau[d][j];
                 }
         }
@@ -369,9 +377,6 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         const T cw = K.dJ * T(1.0 / 512.0);
         const T cl = cw * lam, cm = cw * m;
         const T ch = T(0.5) * (cl + cm), cd = T(0.5) * (cl - cm);
-        // c (tau + m I), tau = 0 in the linear law's tangent
-        const T t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
-        const T t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
         // 1 +- xi, 1 +- eta, 1 +- zeta at the lane's Gauss point (selected for FP64: element.cuh)
         T xp, xm, yp, ym, zp, zm;
         if constexpr (std::is_same<T, double>::value) {
@@ -386,8 +391,18 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 #pragma unroll
         for (int a = 0; a < 8; a++) {
             const int bits = hex_bits_of_node(a);
-            const T fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
-            const T yz = fy * fz, xz = fx * fz, xy = fx * fy;
+            T yz, xz, xy;
+            if constexpr (std::is_same<T, double>::value) {
+                // each product of two of 1 +- g is (1+g)^2, (1+g)(1-g) or (1-g)^2: selected, not
+                // multiplied (the node's factor is 1 + g where its sign matches the point's)
+                const bool mx = ((bits ^ l) & 1) == 0, my = ((bits ^ l) & 2) == 0, mz = ((bits ^ l) & 4) == 0;
+                yz = my ? (mz ? kGaussPP : kGaussPM) : (mz ? kGaussPM : kGaussMM);
+                xz = mx ? (mz ? kGaussPP : kGaussPM) : (mz ? kGaussPM : kGaussMM);
+                xy = mx ? (my ? kGaussPP : kGaussPM) : (my ? kGaussPM : kGaussMM);
+            } else {
+                const T fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
+                yz = fy * fz, xz = fx * fz, xy = fx * fy;
+            }
             // 8 dN_a/dxi at the Gauss point
             const T n0 = (bits & 1) ? yz : -yz, n1 = (bits & 2) ? xz : -xz, n2 = (bits & 4) ? xy : -xy;
             T *r = pv + 3 * a;
@@ -401,9 +416,6 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                     r[L::kDG * L::kArr + j] = cd * g[j];
                 }
             }
-            r[L::kTG * L::kArr + 0] = t00 * g[0] + t01 * g[1] + t02 * g[2];
-            r[L::kTG * L::kArr + 1] = t01 * g[0] + t11 * g[1] + t12 * g[2];
-            r[L::kTG * L::kArr + 2] = t02 * g[0] + t12 * g[1] + t22 * g[2];
         }
         T *pc = sm.coef + (es * 8 + l) * L::kCoef;
         pc[0] = ch;
@@ -416,7 +428,10 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         pc[7] = cw * Tg[0][1];
         sm.node[es][hex_node_of_lane(l)] = node;
         sm.first[es][hex_node_of_lane(l)] = kFirst ? first[8 * e + hex_node_of_lane(l)] : 0;
-        if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
+        if (l == 0) {
+            sm.elem[es] = active ? (int32_t)e : -1;
+            sm.mu[es] = mu;
+        }
     }
     __syncthreads();
     static_assert(L::kElems % kGroup == 0 && kGroupOff % 32 == 0 && kGroupItems % 32 == 0,
@@ -426,16 +441,17 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         // arithmetic otherwise stalls on instruction fetch: 0.9% faster at 128^3)
         constexpr int kUnrollQ = std::is_same<T, df64>::value ? 1 : 2;
         for (int it = threadIdx.x; it < L::kElems * 36; it += blockDim.x) {
-            int ee, a, b;
+            int ee, a, b, li;
             bool off;
-            item_nodes(it, ee, a, b, off);
+            item_nodes(it, ee, a, b, off, li);
             const int32_t eid = sm.elem[ee];
             if (eid < 0) continue;
+            const T gs = item_gs(sm, A.lap, ee, li);
             const int32_t na = sm.node[ee][a];
             const int64_t sbase = 64 * (int64_t)eid;
             T Kab[3][3];
             if (off) {
-                offdiag_block<T, kUnrollQ>(sm, ee, a, b, Kab);
+                offdiag_block<T, kUnrollQ>(sm, ee, a, b, gs, Kab);
                 {
                     const int32_t nb = sm.node[ee][b];
                     const int sab = slotmap[sbase + 8 * a + b];
@@ -458,7 +474,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                 }
             } else {
                 T Ra[3];
-                diag_block<T, kUnrollQ>(sm, ee, a, R != nullptr, Kab, Ra);
+                diag_block<T, kUnrollQ>(sm, ee, a, R != nullptr, gs, Kab, Ra);
                 const T Ra0 = Ra[0], Ra1 = Ra[1], Ra2 = Ra[2];
                 {
                     const int saa = slotmap[sbase + 9 * a];
@@ -490,7 +506,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                 T Kab[3][3], Ra[3];
                 int ee, a, b;
                 bool off;
-                tangent_item<T>(sm, it, R != nullptr, Kab, Ra, ee, a, b, off);
+                tangent_item<T>(sm, A.lap, it, R != nullptr, Kab, Ra, ee, a, b, off);
 #pragma unroll
                 for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -510,9 +526,9 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         for (int j = 0; j < kIters; j++) {
             const int it = threadIdx.x + j * L::kThreads;
             if (it < kItems) {
-                int ee, a, b;
+                int ee, a, b, li;
                 bool off;
-                item_nodes(it, ee, a, b, off);
+                item_nodes(it, ee, a, b, off, li);
                 VT *me = mat + (size_t)ee * 576;
 #pragma unroll
                 for (int i = 0; i < 3; i++)
@@ -746,10 +762,54 @@ __global__ void __launch_bounds__(128) k_fill_geom(const int32_t *__restrict__ c
     *geom_field(p, kGeomA0 + 5) = A0[0][1];
 }
 
+// L_ab (element.cuh, kLap*): each lane forms its Gauss point's share detJ G_a . G_b =
+// (adj(Jp)^T n_a) . (adj(Jp)^T n_b) / (512 det Jp), n_a = 8 dN_a/dxi, and the element's 8 lanes
+// sum the shares by butterfly (the same sum in every lane); lane l writes pairs l, l + 8, ...
+__global__ void __launch_bounds__(128) k_fill_lap(const int32_t *__restrict__ conn, const double *__restrict__ coords,
+                                                  int64_t n, double *__restrict__ lap) {
+    const int l = threadIdx.x & 7;
+    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool active = slot < n;
+    const int64_t e = active ? slot : n - 1;
+    int32_t node;
+    GaussKinematics<double> K;
+    double cu[3];
+    gauss_kinematics_coords<double>(conn, coords, nullptr, e, l, node, K, cu);
+    const double xp = (l & 1) ? kGaussP : kGaussM, xm = (l & 1) ? kGaussM : kGaussP;
+    const double yp = (l & 2) ? kGaussP : kGaussM, ym = (l & 2) ? kGaussM : kGaussP;
+    const double zp = (l & 4) ? kGaussP : kGaussM, zm = (l & 4) ? kGaussM : kGaussP;
+    double v[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        const int bits = hex_bits_of_node(a);
+        const double fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
+        const double n0 = (bits & 1) ? fy * fz : -fy * fz, n1 = (bits & 2) ? fx * fz : -fx * fz;
+        const double n2 = (bits & 4) ? fx * fy : -fx * fy;
+#pragma unroll
+        for (int j = 0; j < 3; j++) v[a][j] = K.aJ[0][j] * n0 + K.aJ[1][j] * n1 + K.aJ[2][j] * n2;
+    }
+    const double w = 1.0 / (512.0 * K.dJ);
+    double *out = lap + (int64_t)kLapPairs * e;
+    int p = 0;
+#pragma unroll
+    for (int a = 0; a < 8; a++)
+#pragma unroll
+        for (int b = a; b < 8; b++) {
+            const int idx = (a == b) ? kLapDiag + a : p++;
+            double x = (v[a][0] * v[b][0] + v[a][1] * v[b][1] + v[a][2] * v[b][2]) * w;
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            x += __shfl_xor_sync(0xffffffffu, x, 4);
+            if (active && (idx & 7) == l) out[idx] = x;
+        }
+}
+
 jetsci_status launch_fill_geom(jetsci_mesh m, cudaStream_t s) {
     if (m->n_elem == 0) return JETSCI_OK;
     const unsigned grid = (unsigned)((8 * m->n_elem + 127) / 128);
     k_fill_geom<<<grid, 128, 0, s>>>(m->d_conn, m->d_coords, m->n_elem, m->d_geom);
+    JETSCI_CUDA_TRY(cudaGetLastError());
+    k_fill_lap<<<grid, 128, 0, s>>>(m->d_conn, m->d_coords, m->n_elem, m->d_lap);
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
 }
@@ -769,6 +829,7 @@ static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
     A.conn = m->d_conn;
     A.coords = m->d_coords;
     A.geom = m->d_geom;
+    A.lap = m->d_lap;
     A.lin = nullptr;
     A.re = nullptr;
     A.phase = m->d_phase;

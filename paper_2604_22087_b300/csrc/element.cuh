@@ -157,6 +157,7 @@ __host__ __device__ constexpr int hex_bits_of_node(int a) { return a ^ ((a >> 1)
 constexpr double kGaussG = 0.57735026918962576451;
 constexpr double kGaussG2 = kGaussG * kGaussG;                      // (+-g)(+-g) = +-g^2
 constexpr double kGaussP = 1.0 + kGaussG, kGaussM = 1.0 - kGaussG;  // 1 +- g
+constexpr double kGaussPP = kGaussP * kGaussP, kGaussPM = kGaussP * kGaussM, kGaussMM = kGaussM * kGaussM;
 
 // a b for two Gauss coordinates a, b in {+g, -g}: +-g^2 with the sign of a b.
 template <typename T>
@@ -283,6 +284,15 @@ __device__ __forceinline__ double *geom_field(double *p, int f) { return p + 16 
 __device__ __forceinline__ double2 geom_pair(const double *__restrict__ p, int k) {
     return __ldg(reinterpret_cast<const double2 *>(p + 16 * k));
 }
+
+// Reference "Laplacian" of an element, kept per mesh for the tangent kernels: per node pair
+// L_ab = sum_q detJ_q G_a,q . G_b,q (G_a = dN_a/dX, the reference shape-function gradient), as
+// [element][36] doubles: the 28 pairs a < b in row order (0, 1), (0, 2), ..., (6, 7), then the 8
+// pairs a == b.  For both laws the geometric and identity parts of the spatial tangent combine to
+// c (tau + m I) = c mu F F^T (neo-Hookean: tau + m I = mu b; linear: tau = 0, m = mu), and
+// (F F^T g_a) . g_b = (F G_a) . (F^-T G_b) = G_a . G_b, so the term delta_ik sum_q tg_a . g_b of
+// K_ab,ik is mu L_ab: fixed by the reference geometry, whatever the deformation.
+constexpr int kLapPairs = 36, kLapDiag = 28;
 
 // Linearisation of the neo-Hookean state at the last FP64 or two-float residual or tangent call,
 // kept per mesh for matrix-free products at that state: adj(j) (0-8), m (9), 1 / det Jp (10) and

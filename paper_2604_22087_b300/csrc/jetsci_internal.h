@@ -49,6 +49,8 @@ struct jetsci_mesh_s {
     int32_t re_prec = -1;               // ... in this precision (TF32 recorded as FP32)
     double *d_geom = nullptr;           // [n_elem][13][8][2]: reference geometry at the Gauss points
                                         // (element.cuh, kGeom*), read by the FP64 kernels
+    double *d_lap = nullptr;            // [n_elem][36]: L_ab = sum_q detJ G_a . G_b per node pair
+                                        // (element.cuh, kLap*), read by the tangent kernels
     int32_t *d_phase = nullptr;         // [n_elem]
     int64_t *d_rowptr = nullptr;        // [n_dof+1]
     int32_t *d_col = nullptr;           // [nnz]
@@ -141,7 +143,7 @@ jetsci_status ensure_block_workspace(jetsci_mesh m, size_t values_bytes, cudaStr
 template <typename VT>
 jetsci_status launch_gather_rows(jetsci_mesh m, const VT *blocks, const double *Re, VT *vals, double *R,
                                  cudaStream_t s);
-// Fills m->d_geom (element.cuh, kGeom*) from the connectivity and coordinates.
+// Fills m->d_geom (element.cuh, kGeom*) and m->d_lap (kLap*) from the connectivity and coordinates.
 jetsci_status launch_fill_geom(jetsci_mesh m, cudaStream_t s);
 jetsci_status launch_material_grad(jetsci_mesh m, const double *u, const double *E_elem,
                                    const double *R, double *g, int precision, cudaStream_t s);

@@ -123,6 +123,7 @@ static void free_mesh(jetsci_mesh m) {
     cudaFree(m->d_conn);
     cudaFree(m->d_coords);
     cudaFree(m->d_geom);
+    cudaFree(m->d_lap);
     cudaFree(m->d_lin);
     cudaFree(m->d_re);
     cudaFree(m->d_phase);
@@ -269,6 +270,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     if ((st = dev_alloc(&m->d_conn, 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_coords, 3 * n_nodes))) return st;
     if ((st = dev_alloc(&m->d_geom, (size_t)26 * 8 * n_elem))) return st;
+    if ((st = dev_alloc(&m->d_lap, (size_t)36 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_lin, (size_t)12 * 8 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_re, (size_t)24 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_phase, n_elem))) return st;
