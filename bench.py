@@ -379,9 +379,11 @@ def run_reference(args, rank):
     # mesh at this rate would take n_elem / value seconds per step.
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elem/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall,
-            "ms_per_step_note": f"one step = the oracle on {pool.P} host cores over {elems} elements of the workload; "
-                                f"the full {prob.n_elem}-element mesh at this rate would take "
-                                f"{prob.n_elem / v:.1f} s per step (extrapolated, not run)",
+            "ms_per_step_note": (f"one step = the oracle on {pool.P} host cores over the whole {prob.n_elem}-element "
+                                 f"mesh ({pool.P} slabs that tile it)" if elems == prob.n_elem else
+                                 f"one step = the oracle on {pool.P} host cores over {elems} elements of the workload; "
+                                 f"the full {prob.n_elem}-element mesh at this rate would take "
+                                 f"{prob.n_elem / v:.1f} s per step (extrapolated, not run)"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(prob, args.n), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "elem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
