@@ -2,17 +2,18 @@
 // the row-gather tangent assembly.
 //
 // The tangent in pair form, as the CUDA-core kernels use it:
-//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi ] + delta_ik sum_q tg_a . g_b
+//   K_ab,ik = sum_q [ c lam g_ai g_bk + c m g_ak g_bi ] + delta_ik mu L_ab
 // with g_a = F^-T G_a the spatial shape-function gradients at Gauss point q, c = w detJ,
-// m = mu - lam lnJ (mu for Hooke) and tg_a = c (tau + m I) g_a (tau the Kirchhoff stress).  Its
-// two rank-8 parts are contractions over the Gauss points: with P[(a,i), q] = g_ai,
+// m = mu - lam lnJ (mu for Hooke) and L_ab = sum_q detJ G_a . G_b the element's reference
+// Laplacian (the geometric term sum_q c g_a^T (tau + m I) g_b equals mu L_ab for both laws; the
+// mesh caches L_ab, element.cuh kLap*).  The two rank-8 parts are contractions over the Gauss
+// points: with P[(a,i), q] = g_ai,
 //   T1 = P diag(c lam) P^T,   T2 = P diag(c m) P^T,   K_ab,ik = T1[(a,i),(b,k)] + T2[(a,k),(b,i)] + ...
 // Four elements share one tcgen05.mma (kind::tf32, M = 128, N = 48, K = 32, as four MMAs of
 // K = 8): A holds P of the four elements block-diagonally (row (e,a,i), column (e,q), zero
 // outside the element's eight columns) and B the columns c lam g_b | c m g_b (row (term,b,k),
 // column (e,q)).  Accumulator row (e,a,i) so receives T1 and T2 of its own element only, in 48
-// TMEM columns.  The geometric term (36 dot products per element and point) is reduced over the
-// Gauss-point lanes on the CUDA cores.
+// TMEM columns.  The epilogue adds mu L_ab on the diagonal of each 3 x 3 block.
 //
 // Persistent CTAs (two per SM, as TMEM allows: 256 columns each) loop over batches of 16
 // elements = four groups of four; warp w evaluates group w (lane = element x Gauss point) and
@@ -55,7 +56,7 @@ struct __align__(128) TgSmem {
     unsigned char A[kTgGroups][kTgATile];
     unsigned char B[kTgGroups][kTgBTile];
     float t2[kTgT2Groups][96 * kTgT2Stride];  // T2 rows of two groups, [row][kTgT2Stride]
-    float geo[kTgElems][36];                  // sum_q tg_a . g_b, pairs a <= b row by row
+    float geo[kTgElems][kLapPairs];           // mu L_ab of each element (kLap* order)
     int32_t elem[kTgElems];
     uint64_t mbar;
     uint32_t tmem_base;
@@ -71,8 +72,13 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// pair (a, b), a <= b, of the 36 pairs of an element ordered row by row
-__device__ __forceinline__ int tg_pair(int a, int b) { return 8 * a - (a * (a - 1)) / 2 + (b - a); }
+// index of node pair (a, b) in an element's L_ab (element.cuh, kLap*): the pairs a < b row by
+// row, then the diagonal
+__device__ __forceinline__ int tg_lap(int a, int b) {
+    if (a == b) return kLapDiag + a;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return 7 * lo - (lo * (lo - 1)) / 2 + (hi - lo - 1);
+}
 
 struct Tf32Args {
     const int32_t *__restrict__ conn;
@@ -80,6 +86,7 @@ struct Tf32Args {
     const int32_t *__restrict__ phase;
     const Material *__restrict__ mats;
     const double *__restrict__ E_elem;
+    const double *__restrict__ lap;  // per-element L_ab (kLap* order)
     int64_t n;         // elements 0 .. n - 1
     uint32_t *flags;
 };
@@ -164,8 +171,8 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
             const Material &mat = A.mats[cur.ph];
             const float lam = A.E_elem ? (float)(cur.E * mat.lam1) : (float)mat.lam;
             const float mu = A.E_elem ? (float)(cur.E * mat.mu1) : (float)mat.mu;
-            // W with g_a = W^T (8 dN_a/dxi), the Kirchhoff stress tau, m, and the residual moment Q
-            float W[3][3], tau[3][3], Q[3][3], m;
+            // W with g_a = W^T (8 dN_a/dxi), m, and the residual moment Q
+            float W[3][3], Q[3][3], m;
             bool ok = true;
             if (mat.law == JETSCI_LINEAR_ELASTIC) {
                 const float rdJ = 1.0f / K.dJ;
@@ -182,10 +189,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
 #pragma unroll
                 for (int i = 0; i < 3; i++)
 #pragma unroll
-                    for (int j = 0; j < 3; j++) {
-                        sg[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : 0.0f);
-                        tau[i][j] = 0.0f;
-                    }
+                    for (int j = 0; j < 3; j++) sg[i][j] = mu * (H[i][j] + H[j][i]) + ((i == j) ? ltr : 0.0f);
 #pragma unroll
                 for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -201,10 +205,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
 #pragma unroll
                 for (int d = 0; d < 3; d++)
 #pragma unroll
-                    for (int j = 0; j < 3; j++) {
-                        W[d][j] = st.aj[d][j] * st.rdj;
-                        tau[d][j] = st.tau[d][j];
-                    }
+                    for (int j = 0; j < 3; j++) W[d][j] = st.aj[d][j] * st.rdj;
 #pragma unroll
                 for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -217,14 +218,11 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
             }
             const float cw = K.dJ * (1.0f / 512.0f);
             const float cl = cw * lam, cm = cw * m;
-            const float t00 = cw * tau[0][0] + cm, t11 = cw * tau[1][1] + cm, t22 = cw * tau[2][2] + cm;
-            const float t12 = cw * tau[1][2], t02 = cw * tau[0][2], t01 = cw * tau[0][1];
             const float xp = 1.0f + K.xi, xm = 1.0f - K.xi, yp = 1.0f + K.eta, ym = 1.0f - K.eta;
             const float zp = 1.0f + K.zeta, zm = 1.0f - K.zeta;
             unsigned char *At = sm.A[w];
             unsigned char *Bt = sm.B[w];
             const int kc = 8 * el + l;  // this lane's column of A and B
-            float g[8][3], tg[8][3];
 #pragma unroll
             for (int a = 0; a < 8; a++) {
                 const int bits = hex_bits_of_node(a);
@@ -232,50 +230,21 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
                 const float yz = fy * fz, xz = fx * fz, xy = fx * fy;
                 const float n0 = (bits & 1) ? yz : -yz, n1 = (bits & 2) ? xz : -xz, n2 = (bits & 4) ? xy : -xy;
 #pragma unroll
-                for (int j = 0; j < 3; j++) g[a][j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
-                tg[a][0] = t00 * g[a][0] + t01 * g[a][1] + t02 * g[a][2];
-                tg[a][1] = t01 * g[a][0] + t11 * g[a][1] + t12 * g[a][2];
-                tg[a][2] = t02 * g[a][0] + t12 * g[a][1] + t22 * g[a][2];
-#pragma unroll
                 for (int i = 0; i < 3; i++) {
+                    const float g = W[0][i] * n0 + W[1][i] * n1 + W[2][i] * n2;
                     // A: the element's own row block (the other elements' rows of this column
                     // hold the zeros written at the start)
-                    *reinterpret_cast<float *>(At + tg_offset(24 * el + 3 * a + i, kc)) = to_tf32(g[a][i]);
-                    *reinterpret_cast<float *>(Bt + tg_offset(3 * a + i, kc)) = to_tf32(cl * g[a][i]);
-                    *reinterpret_cast<float *>(Bt + tg_offset(24 + 3 * a + i, kc)) = to_tf32(cm * g[a][i]);
+                    *reinterpret_cast<float *>(At + tg_offset(24 * el + 3 * a + i, kc)) = to_tf32(g);
+                    *reinterpret_cast<float *>(Bt + tg_offset(3 * a + i, kc)) = to_tf32(cl * g);
+                    *reinterpret_cast<float *>(Bt + tg_offset(24 + 3 * a + i, kc)) = to_tf32(cm * g);
                 }
             }
-            // geometric term: d_p = tg_a . g_b for the 36 pairs, summed over the 8 Gauss-point lanes
-            // by a reduce-scatter (halves exchanged across lanes 4, 2, 1 apart); lane l ends with
-            // the sums of pairs 18 (l>>2 & 1) + 9 (l>>1 & 1) + 5 (l & 1) + j, j < 5 (< 4 for odd l)
-            float d[36];
+            // geometric term: mu L_ab of the element, lane l holding pairs l, l + 8, ...
+            {
+                const double *le = A.lap + (int64_t)kLapPairs * e;
 #pragma unroll
-            for (int a = 0; a < 8; a++)
-#pragma unroll
-                for (int bb = a; bb < 8; bb++)
-                    d[tg_pair(a, bb)] = tg[a][0] * g[bb][0] + tg[a][1] * g[bb][1] + tg[a][2] * g[bb][2];
-            const bool h4 = (l >> 2) & 1, h2 = (l >> 1) & 1, h1 = l & 1;
-            float d18[18], d9[9], d5[5];
-#pragma unroll
-            for (int j = 0; j < 18; j++) {
-                const float keep = h4 ? d[18 + j] : d[j], give = h4 ? d[j] : d[18 + j];
-                d18[j] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+                for (int j = l; j < kLapPairs; j += 8) sm.geo[es][j] = mu * (float)__ldg(le + j);
             }
-#pragma unroll
-            for (int j = 0; j < 9; j++) {
-                const float keep = h2 ? d18[9 + j] : d18[j], give = h2 ? d18[j] : d18[9 + j];
-                d9[j] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
-            }
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                const float lo = d9[j], hi = j + 5 < 9 ? d9[j + 5] : 0.0f;
-                const float keep = h1 ? hi : lo, give = h1 ? lo : hi;
-                d5[j] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
-            }
-            const int p0 = 18 * h4 + 9 * h2 + 5 * h1;
-#pragma unroll
-            for (int j = 0; j < 5; j++)
-                if (5 * h1 + j < 9) sm.geo[es][p0 + j] = d5[j];
             // residual: nodal forces of the lane's node
             float f[3];
             nodal_force_of_moment(Q, K, l, f);
@@ -345,7 +314,7 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
                     const float *t2e = sm.t2[gg] + 24 * rel * kTgT2Stride;
 #pragma unroll
                     for (int bb = 0; bb < 8; bb++) {
-                        const float geo = sm.geo[ee][ra <= bb ? tg_pair(ra, bb) : tg_pair(bb, ra)];
+                        const float geo = sm.geo[ee][tg_lap(ra, bb)];
 #pragma unroll
                         for (int k = 0; k < 3; k++)
                             rowv[3 * bb + k] += t2e[(3 * bb + ri) * kTgT2Stride + 3 * ra + k] + (k == ri ? geo : 0.0f);
@@ -377,6 +346,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, float *vals, double *R
     A.phase = m->d_phase;
     A.mats = m->d_mats;
     A.E_elem = E_elem;
+    A.lap = m->d_lap;
     A.flags = m->d_flags;
     const size_t smem = sizeof(TgSmem);
     // row-gather assembly: element rows (one persistent launch, elements in order), then the row pass
