@@ -6,23 +6,28 @@
 // with g_a = F^-T G_a the spatial shape-function gradients at Gauss point q, c = w detJ,
 // m = mu - lam lnJ (mu for Hooke) and L_ab = sum_q detJ G_a . G_b the element's reference
 // Laplacian (the geometric term sum_q c g_a^T (tau + m I) g_b equals mu L_ab for both laws; the
-// mesh caches L_ab, element.cuh kLap*).  The two rank-8 parts are contractions over the Gauss
-// points: with P[(a,i), q] = g_ai,
-//   T1 = P diag(c lam) P^T,   T2 = P diag(c m) P^T,   K_ab,ik = T1[(a,i),(b,k)] + T2[(a,k),(b,i)] + ...
-// Four elements share one tcgen05.mma (kind::tf32, M = 128, N = 48, K = 32, as four MMAs of
-// K = 8): A holds P of the four elements block-diagonally (row (e,a,i), column (e,q), zero
-// outside the element's eight columns) and B the columns c lam g_b | c m g_b (row (term,b,k),
-// column (e,q)).  Accumulator row (e,a,i) so receives T1 and T2 of its own element only, in 48
-// TMEM columns.  The epilogue adds mu L_ab on the diagonal of each 3 x 3 block.
+// mesh caches L_ab, element.cuh kLap*).  With g_a = W^T n_a, where n_a = 8 dN_a/dxi at the point
+// is the same for every element (W = j^-1, j = 8 dx/dxi), the two material terms become
+//   K_ab,ik = sum_{q,r,s} n_ar n_bs V_q[(r,s),(i,k)],   V_q[(r,s),(i,k)] = c lam W_ri W_sk + c m W_rk W_si:
+// one product of a constant matrix N[(a,b),(r,s,q)] = n_ar n_bs (64 node pairs x 72) with the
+// elements' V (nine rows (i,k) per element, 72 columns (r,s,q)).  Twenty-four elements share one
+// tcgen05.mma chain (kind::tf32, M = 128 of which the 64 pair rows are used, N = 224 of which 216
+// are used, K = 72): accumulator row (a,b), column 8 (3 (3i + k) + o) + j holds K_ab,ik of element
+// 8 o + j (o = octet) without the geometric term, so
+// the epilogue needs no transposition and adds mu L_ab on the diagonal of each 3 x 3 block.  N is
+// split into two TF32 parts (hi + lo, two MMAs per K step), which leaves the rounding of V as the
+// only TF32 rounding (N itself is formed in FP32); every V entry is dense (no block-diagonal
+// zeros).
 //
-// Persistent CTAs (two per SM, as TMEM allows: 256 columns each) loop over batches of 16
-// elements = four groups of four; warp w evaluates group w (lane = element x Gauss point) and
-// writes its operand columns, one thread issues the 16 MMAs, then every warp reads its TMEM lane
-// quarter of each group's accumulator and T2 is transposed within node blocks through shared
-// memory.  Per CTA the zeros of the block-diagonal A tiles are written once (a lane only ever
-// writes its own element's rows), and the gathers of the next batch are issued before the
-// current batch's arithmetic: the connectivity two batches ahead, the coordinates and
-// displacements one batch ahead.
+// Persistent CTAs (six warps, two CTAs per SM: 256 TMEM columns and about 105 KB of shared
+// memory each) loop over batches of 24 elements: thread = element x Gauss point writes its
+// point's 81 V entries, one thread issues the 18 MMAs, then the four warps that see TMEM lanes
+// 0-63 (warps 0, 1, 4 and 5; each reads the lanes of its quarter) read the accumulator rows of
+// the 64 node pairs, one octet of elements per 8-column load, into the element matrices, laid
+// out in shared memory over the V tile; one bulk asynchronous copy writes them out while the
+// next batch's kinematics run (phase 1 waits for its reads before storing V).  The
+// gathers of the next batch are issued before the current batch's arithmetic: the connectivity
+// two batches ahead, the coordinates and displacements one batch ahead.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,36 +39,31 @@
 
 namespace jetsci {
 
-constexpr int kTgGroups = 4;                   // MMA groups per CTA (one per warp)
-constexpr int kTgElems = 4 * kTgGroups;        // elements per CTA
-constexpr int kTgK = 32;                       // 4 elements x 8 Gauss points
-constexpr int kTgN = 48;                       // 2 terms x 8 nodes x 3 components
-constexpr uint32_t kTgCols = 64;               // TMEM columns per group (48 used)
-constexpr uint32_t kTgTmemCols = kTgGroups * kTgCols;
-// K-major core matrices (8 rows x 16 bytes) with 144 B between core matrices along K (16 B of
-// padding): a warp's 32 lanes (8 element columns x 4 per core matrix) write one row of a tile
-// on 32 distinct banks.
-constexpr uint32_t kTgLBO = 144;
-constexpr uint32_t kTgSBO = (kTgK / 4) * kTgLBO;  // 8-row blocks
-constexpr int kTgATile = 12 * kTgSBO;             // rows 0..95 (M = 128: see below)
-constexpr int kTgBTile = 6 * kTgSBO;              // 48 rows
-constexpr int kTgT2Stride = 25;                   // floats per row of the T2 transposition buffer
+constexpr int kTnE = 24;                           // elements per batch (three octets)
+constexpr int kTnThreads = 8 * kTnE;               // thread = element x Gauss point in phase 1
+constexpr int kTnK = 72;                           // columns (r, s, q): 8 (3 r + s) + q
+constexpr int kTnCols = 9 * kTnE;                  // accumulator columns 8 (3 (3 i + k) + octet) + element
+constexpr int kTnN = (kTnCols + 15) / 16 * 16;     // the MMA's N (a multiple of 16; the last rows unused)
+constexpr uint32_t kTnTmemCols = 256;
+// K-major core matrices (8 rows x 16 bytes), no padding: LBO = step along K, SBO = 8-row step
+constexpr uint32_t kTnLBO = 128;
+constexpr uint32_t kTnSBO = (kTnK / 4) * kTnLBO;
+constexpr int kTnATile = 8 * kTnSBO;               // the 64 pair rows of N
+constexpr int kTnBTile = (kTnN / 8) * kTnSBO;      // 224 rows of V (216 used)
 
-// The MMA reads 128 rows of A; rows 96..127 (row blocks 12..15) fall on the next tile or on the
-// B tiles and produce accumulator rows that are never read, so they need neither zeros nor room.
-constexpr int kTgT2Groups = 2;  // groups whose T2 rows the transposition buffer holds at once
-struct __align__(128) TgSmem {
-    unsigned char A[kTgGroups][kTgATile];
-    unsigned char B[kTgGroups][kTgBTile];
-    float t2[kTgT2Groups][96 * kTgT2Stride];  // T2 rows of two groups, [row][kTgT2Stride]
-    float geo[kTgElems][kLapPairs];           // mu L_ab of each element (kLap* order)
-    int32_t elem[kTgElems];
+// The MMA reads 128 rows of A; rows 64..127 fall on the next bytes of shared memory (the lo part,
+// then the V tile) and produce accumulator rows that are never read.
+struct __align__(128) TnSmem {
+    unsigned char A[2][kTnATile];       // N, hi and lo TF32 parts
+    unsigned char B[kTnBTile];          // V of the batch's 24 elements
+    float geo[kTnE][kLapPairs];         // mu L_ab of each element (kLap* order)
+    int32_t elem[kTnE];
     uint64_t mbar;
     uint32_t tmem_base;
 };
 
-__device__ __forceinline__ uint32_t tg_offset(int r, int k) {
-    return (uint32_t)((r >> 3) * kTgSBO + (k >> 2) * kTgLBO + (r & 7) * 16 + (k & 3) * 4);
+__device__ __forceinline__ uint32_t tn_offset(int r, int k) {
+    return (uint32_t)((r >> 3) * kTnSBO + (k >> 2) * kTnLBO + (r & 7) * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -78,6 +78,17 @@ __device__ __forceinline__ int tg_lap(int a, int b) {
     if (a == b) return kLapDiag + a;
     const int lo = a < b ? a : b, hi = a < b ? b : a;
     return 7 * lo - (lo * (lo - 1)) / 2 + (hi - lo - 1);
+}
+
+// n_a,r = 8 dN_a/dxi_r at Gauss point q (lane bits of q: xi, eta, zeta signs), in FP32: each
+// factor 1 +- g where the node's and the point's signs agree or differ
+__device__ __forceinline__ float tn_nref(int q, int a, int r) {
+    const int bits = hex_bits_of_node(a);
+    const float f[3] = {((bits ^ q) & 1) ? (float)kGaussM : (float)kGaussP,
+                        ((bits ^ q) & 2) ? (float)kGaussM : (float)kGaussP,
+                        ((bits ^ q) & 4) ? (float)kGaussM : (float)kGaussP};
+    const float sgn = (bits >> r) & 1 ? 1.0f : -1.0f;
+    return sgn * f[(r + 1) % 3] * f[(r + 2) % 3];
 }
 
 struct Tf32Args {
@@ -103,7 +114,7 @@ struct Tf32Gather {
 // element of the lane in batch b (the last element for the slots past the end), and whether
 // the slot is one
 __device__ __forceinline__ int64_t tf32_elem(const Tf32Args &A, int64_t b, int es, bool &active) {
-    const int64_t slot = b * kTgElems + es;
+    const int64_t slot = b * kTnE + es;
     active = slot < A.n;
     return active ? slot : A.n - 1;
 }
@@ -127,29 +138,33 @@ __device__ __forceinline__ void tf32_gather_values(const Tf32Args &A, const doub
 // Element pass of the row-gather assembly: the element's 24 x 24 stiffness rows go to vals = the
 // workspace [element][24][24] and, if R is given, its nodal forces to R = the workspace's residual
 // part [element][local node][3].
-__global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restrict__ u, float *__restrict__ vals,
+__global__ void __launch_bounds__(kTnThreads, 2) k_tf32(Tf32Args A, const double *__restrict__ u, float *__restrict__ vals,
                                               double *__restrict__ R) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    TgSmem &sm = *reinterpret_cast<TgSmem *>(smem_raw);
-    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-    const int el = lane >> 3, l = lane & 7;  // element in the group, Gauss point
-    const int es = t >> 3;                   // element slot in the batch (= 4 w + el)
-    if (w == 0) tc::tmem_alloc(&sm.tmem_base, kTgTmemCols);
+    TnSmem &sm = *reinterpret_cast<TnSmem *>(smem_raw);
+    const int t = threadIdx.x, w = t >> 5;
+    const int l = t & 7;   // Gauss point
+    const int es = t >> 3; // element slot in the batch
+    if (w == 0) tc::tmem_alloc(&sm.tmem_base, kTnTmemCols);
     if (t == 0) {
         tc::mbar_init(&sm.mbar, 1);
         tc::fence_mbar_init();
     }
-    // zeros of the A tiles, once: every lane later writes only its own element's rows in its
-    // column, so the other elements' rows there stay zero
-    {
-        uint4 *z = reinterpret_cast<uint4 *>(&sm.A[0][0]);
-        for (int i = t; i < (int)(sizeof(sm.A) / 16); i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    // the constant operand N[(a,b), 8 (3 r + s) + q] = n_ar n_bs at point q, as hi + lo TF32 parts
+    for (int idx = t; idx < 64 * kTnK; idx += kTnThreads) {
+        const int row = idx / kTnK, col = idx - kTnK * row;
+        const int a = row >> 3, b = row & 7, rs = col >> 3, q = col & 7;
+        const float x = tn_nref(q, a, rs / 3) * tn_nref(q, b, rs % 3);
+        const float hi = to_tf32(x);
+        const float lo = to_tf32(x - hi);  // (exact: x - hi has at most 13 significant bits)
+        *reinterpret_cast<float *>(sm.A[0] + tn_offset(row, col)) = hi;
+        *reinterpret_cast<float *>(sm.A[1] + tn_offset(row, col)) = lo;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tm = sm.tmem_base;
-    const int64_t n_batches = (A.n + kTgElems - 1) / kTgElems;
+    const int64_t n_batches = (A.n + kTnE - 1) / kTnE;
     const int64_t G = gridDim.x;
     int64_t b = blockIdx.x;
     Tf32Gather cur, nxt;
@@ -218,32 +233,39 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
             }
             const float cw = K.dJ * (1.0f / 512.0f);
             const float cl = cw * lam, cm = cw * m;
-            const float xp = 1.0f + K.xi, xm = 1.0f - K.xi, yp = 1.0f + K.eta, ym = 1.0f - K.eta;
-            const float zp = 1.0f + K.zeta, zm = 1.0f - K.zeta;
-            unsigned char *At = sm.A[w];
-            unsigned char *Bt = sm.B[w];
-            const int kc = 8 * el + l;  // this lane's column of A and B
+            // V_q[(r,s),(i,k)] = c lam W_ri W_sk + c m W_rk W_si at row 8 (3 (3 i + k) + octet) + j,
+            // column 8 (3 r + s) + q; the entry of ((s,r),(k,i)) is the same
+            float Lw[3][3], Mw[3][3];
 #pragma unroll
-            for (int a = 0; a < 8; a++) {
-                const int bits = hex_bits_of_node(a);
-                const float fx = (bits & 1) ? xp : xm, fy = (bits & 2) ? yp : ym, fz = (bits & 4) ? zp : zm;
-                const float yz = fy * fz, xz = fx * fz, xy = fx * fy;
-                const float n0 = (bits & 1) ? yz : -yz, n1 = (bits & 2) ? xz : -xz, n2 = (bits & 4) ? xy : -xy;
+            for (int r = 0; r < 3; r++)
 #pragma unroll
-                for (int i = 0; i < 3; i++) {
-                    const float g = W[0][i] * n0 + W[1][i] * n1 + W[2][i] * n2;
-                    // A: the element's own row block (the other elements' rows of this column
-                    // hold the zeros written at the start)
-                    *reinterpret_cast<float *>(At + tg_offset(24 * el + 3 * a + i, kc)) = to_tf32(g);
-                    *reinterpret_cast<float *>(Bt + tg_offset(3 * a + i, kc)) = to_tf32(cl * g);
-                    *reinterpret_cast<float *>(Bt + tg_offset(24 + 3 * a + i, kc)) = to_tf32(cm * g);
-                }
-            }
+                for (int i = 0; i < 3; i++) Lw[r][i] = cl * W[r][i], Mw[r][i] = cm * W[r][i];
+            // the previous batch's rows have left the V tile (their bulk copy read it)
+            if (t == 0) tc::bulk_wait_read();
+            __syncthreads();
+            unsigned char *Bt = sm.B;
+            // V row (= accumulator column) of component c of this element
+            auto vrow = [&](int c) { return 8 * (3 * c + (es >> 3)) + (es & 7); };
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int s2 = 0; s2 < 3; s2++)
+#pragma unroll
+                    for (int i = 0; i < 3; i++)
+#pragma unroll
+                        for (int k = 0; k < 3; k++) {
+                            const int self = 9 * (3 * r + s2) + 3 * i + k, mirror = 9 * (3 * s2 + r) + 3 * k + i;
+                            if (self > mirror) continue;
+                            const float v = to_tf32(fmaf(Lw[r][i], W[s2][k], Mw[r][k] * W[s2][i]));
+                            *reinterpret_cast<float *>(Bt + tn_offset(vrow(3 * i + k), 8 * (3 * r + s2) + l)) = v;
+                            if (mirror != self)
+                                *reinterpret_cast<float *>(Bt + tn_offset(vrow(3 * k + i), 8 * (3 * s2 + r) + l)) = v;
+                        }
             // geometric term: mu L_ab of the element, lane l holding pairs l, l + 8, ...
             {
                 const double *le = A.lap + (int64_t)kLapPairs * e;
 #pragma unroll
-                for (int j = l; j < kLapPairs; j += 8) sm.geo[es][j] = mu * (float)__ldg(le + j);
+                for (int j = l; j < kLapPairs; j += 8) sm.geo[es][j] = mu * from_double<float>(__ldg(le + j));
             }
             // residual: nodal forces of the lane's node
             float f[3];
@@ -260,82 +282,59 @@ __global__ void __launch_bounds__(128) k_tf32(Tf32Args A, const double *__restri
         __syncthreads();
         tc::fence_after_sync();
         if (t == 0) {
-            const uint32_t id = tc::idesc_tf32(128, kTgN);
-            for (int g = 0; g < kTgGroups; g++) {
-                const uint32_t a0 = tc::smem_addr(sm.A[g]), b0 = tc::smem_addr(sm.B[g]);
-                // one MMA of K = 8 covers two core matrices along K
-                for (int kk = 0; kk < kTgK / 8; kk++)
-                    tc::mma_tf32(tm + kTgCols * g, tc::smem_desc(a0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO),
-                                 tc::smem_desc(b0 + kk * 2 * kTgLBO, kTgLBO, kTgSBO), id, kk > 0 ? 1u : 0u);
-            }
+            const uint32_t id = tc::idesc_tf32(128, kTnN);
+            const uint32_t b0 = tc::smem_addr(sm.B);
+            // one MMA of K = 8 covers two core matrices along K; N's hi and lo parts in turn
+            for (int kk = 0; kk < kTnK / 8; kk++)
+                for (int part = 0; part < 2; part++)
+                    tc::mma_tf32(tm, tc::smem_desc(tc::smem_addr(sm.A[part]) + kk * 2 * kTnLBO, kTnLBO, kTnSBO),
+                                 tc::smem_desc(b0 + kk * 2 * kTnLBO, kTnLBO, kTnSBO), id, (kk | part) ? 1u : 0u);
             tc::mma_commit(&sm.mbar);
         }
         const bool ok = tc::mbar_wait_bounded(&sm.mbar, it & 1);
         tc::fence_after_sync();
         if (!ok && t == 0) atomicOr(A.flags, JETSCI_FLAG_NONFINITE);
-        // ---------------- epilogue: thread t owns accumulator row r = t of each group (TMEM lane
-        // t); rows 96..127 (warp 3) carry nothing.  Two groups at a time: their T2 rows into the
-        // transposition buffer, then each row
-        //   K[(a,i),(b,k)] = T1[(a,i),(b,k)] + T2[(b,i),(a,k)] + delta_ik geo(a,b)
-        // (T2 is symmetric: its entry ((a,k),(b,i)) is row (b,i), column (a,k)).
-        const int r = t, rel = r / 24, ra = (r % 24) / 3, ri = r % 3;
-        for (int g0 = 0; g0 < kTgGroups; g0 += kTgT2Groups) {
-            if (w < 3) {
-#pragma unroll
-                for (int gg = 0; gg < kTgT2Groups; gg++) {
-                    float v16[16], v8[8];
-                    tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * (g0 + gg) + 24), v16);
-                    tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * (g0 + gg) + 40), v8);
-                    float *dst = sm.t2[gg] + r * kTgT2Stride;
-#pragma unroll
-                    for (int c = 0; c < 16; c++) dst[c] = v16[c];
-#pragma unroll
-                    for (int c = 0; c < 8; c++) dst[16 + c] = v8[c];
-                }
-            }
-            __syncthreads();
-            if (w < 3) {
+        // ---------------- epilogue: thread t < 64 owns accumulator row t = node pair (a, b); the
+        // batch's element matrices are laid out in [element][24][24] order over the V tile (free
+        // once the MMAs completed: conflict-free stores), then every thread copies them out, one
+        // contiguous span of 16-byte stores
+        float *stage = reinterpret_cast<float *>(sm.B);
+        if ((w & 3) < 2) {  // warps 0, 1: components 0-4; warps 4, 5: components 5-8
+            const int pr = 32 * (w & 1) + (t & 31), pa = pr >> 3, pb = pr & 7, li = tg_lap(pa, pb);
+            float *dst = stage + 24 * (3 * pa) + 3 * pb;
+            const int c0 = w < 4 ? 0 : 5, c1 = w < 4 ? 5 : 9;
 #pragma unroll 1
-                for (int gg = 0; gg < kTgT2Groups; gg++) {
-                    const int g = g0 + gg;
-                    float rowv[24];
-                    {
-                        float v16[16], v8[8];
-                        tc::tmem_ld16(tc::tmem_lane_addr(tm, kTgCols * g), v16);
-                        tc::tmem_ld8(tc::tmem_lane_addr(tm, kTgCols * g + 16), v8);
+            for (int c = c0; c < c1; c++) {
+                const int i = c / 3, k = c - 3 * i;
+#pragma unroll 1
+                for (int o = 0; o < kTnE / 8; o++) {
+                    float v[8];
+                    tc::tmem_ld8(tc::tmem_lane_addr(tm, 8 * (3 * c + o)), v);
 #pragma unroll
-                        for (int c = 0; c < 16; c++) rowv[c] = v16[c];
-#pragma unroll
-                        for (int c = 0; c < 8; c++) rowv[16 + c] = v8[c];
+                    for (int j = 0; j < 8; j++) {
+                        const int el = 8 * o + j;
+                        dst[576 * el + 24 * i + k] = (i == k) ? v[j] + sm.geo[el][li] : v[j];
                     }
-                    const int ee = 4 * g + rel;
-                    const int32_t eid = sm.elem[ee];
-                    if (eid < 0) continue;
-                    const float *t2e = sm.t2[gg] + 24 * rel * kTgT2Stride;
-#pragma unroll
-                    for (int bb = 0; bb < 8; bb++) {
-                        const float geo = sm.geo[ee][tg_lap(ra, bb)];
-#pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            rowv[3 * bb + k] += t2e[(3 * bb + ri) * kTgT2Stride + 3 * ra + k] + (k == ri ? geo : 0.0f);
-                    }
-                    // row 3a + i of K_e: 96 contiguous bytes
-                    float4 *dst = reinterpret_cast<float4 *>(vals + 576 * (int64_t)eid + 24 * (3 * ra + ri));
-#pragma unroll
-                    for (int c = 0; c < 6; c++)
-                        dst[c] = make_float4(rowv[4 * c], rowv[4 * c + 1], rowv[4 * c + 2], rowv[4 * c + 3]);
                 }
             }
-            tc::fence_before_sync();
-            __syncthreads();  // the buffer, geo and elem are reused; the next MMA overwrites TMEM
-            tc::fence_after_sync();
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();  // the element matrices are laid out; the next MMA may overwrite TMEM
+        tc::fence_after_sync();
+        if (t == 0) {  // one bulk copy of the batch's contiguous rows; it drains during the next phase 1
+            const int64_t e0 = b * kTnE;
+            const int n_el = (int)(A.n - e0 < kTnE ? A.n - e0 : kTnE);
+            tc::bulk_store(vals + 576 * e0, stage, (uint32_t)n_el * 576u * (uint32_t)sizeof(float));
+            tc::bulk_commit();
         }
         cur = nxt;
         if (b + 2 * G < n_batches) tf32_gather_conn(A, b + 2 * G, es, l, nxt);
     }
+    if (t == 0) tc::bulk_wait();  // the last batch's rows are written before the CTA exits
     tc::fence_before_sync();
     __syncthreads();
-    if (w == 0) tc::tmem_dealloc(tm, kTgTmemCols);
+    if (w == 0) tc::tmem_dealloc(tm, kTnTmemCols);
 }
 
 jetsci_status launch_tf32(jetsci_mesh m, const double *u, float *vals, double *R, const double *E_elem,
@@ -348,7 +347,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, float *vals, double *R
     A.E_elem = E_elem;
     A.lap = m->d_lap;
     A.flags = m->d_flags;
-    const size_t smem = sizeof(TgSmem);
+    const size_t smem = sizeof(TnSmem);
     // row-gather assembly: element rows (one persistent launch, elements in order), then the row pass
     void *ws = nullptr;
     double *Re = nullptr;
@@ -360,10 +359,10 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, float *vals, double *R
         int sms = 0;
         JETSCI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
         A.n = m->n_elem;
-        const int64_t n_batches = (A.n + kTgElems - 1) / kTgElems;
-        // two CTAs per SM: 256 TMEM columns and about 104 KB of shared memory each
+        const int64_t n_batches = (A.n + kTnE - 1) / kTnE;
+        // two CTAs per SM: 256 TMEM columns and about 105 KB of shared memory each
         const unsigned grid = (unsigned)std::min<int64_t>(n_batches, 2 * (int64_t)std::max(sms, 1));
-        k_tf32<<<grid, 128, smem, s>>>(A, u, (float *)ws, Re);
+        k_tf32<<<grid, kTnThreads, smem, s>>>(A, u, (float *)ws, Re);
         JETSCI_CUDA_TRY(cudaGetLastError());
     }
     return launch_gather_rows<float>(m, (const float *)ws, Re, vals, R, s);

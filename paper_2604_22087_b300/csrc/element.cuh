@@ -59,12 +59,23 @@ __device__ __forceinline__ df64 shfl_xor8<df64>(df64 v, int mask) {
     return shfl_xor_df(v, mask, 8);
 }
 
+// x with its sign flipped when neg: by integer sign-bit operations, so that the butterflies below
+// (x - p on some lanes of a warp, x + p on the others) issue one addition of the partner's value
+// with the sign each lane needs; x - p is x + (-p) exactly, so the results are unchanged.
+__device__ __forceinline__ float neg_if(float x, bool neg) {
+    return __uint_as_float(__float_as_uint(x) ^ (neg ? 0x80000000u : 0u));
+}
+__device__ __forceinline__ double neg_if(double x, bool neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+__device__ __forceinline__ df64 neg_if(df64 x, bool neg) { return df64(neg_if(x.h, neg), neg_if(x.l, neg)); }
+
 // Nodal values (lane = node in binary order) -> 8 * monomial coefficient (lane = monomial).
 __device__ __forceinline__ double butterfly_forward(double v, int l) {
 #pragma unroll
     for (int s = 1; s < 8; s <<= 1) {
-        double p = shfl_xor8(v, s);
-        v = (l & s) ? v - p : v + p;
+        const double p = shfl_xor8(v, s);
+        v = v + neg_if(p, (l & s) != 0);  // v - p where bit s of l is set, v + p elsewhere
     }
     return v;
 }
@@ -108,7 +119,7 @@ __device__ __forceinline__ float monomial_coeff<float>(double v, int l) {
 #pragma unroll
     for (int s = 1; s < 8; s <<= 1) {
         const df64 p = shfl_xor_df(x, s, 8);
-        x = (l & s) ? x - p : x + p;
+        x = x + neg_if(p, (l & s) != 0);  // x - p where bit s of l is set, x + p elsewhere
     }
     return __fadd_rn(x.h, x.l);
 }
@@ -119,8 +130,8 @@ template <typename T>
 __device__ __forceinline__ T butterfly_transpose(T v, int l) {
 #pragma unroll
     for (int s = 1; s < 8; s <<= 1) {
-        T p = shfl_xor8(v, s);
-        v = (l & s) ? v + p : v - p;
+        const T p = shfl_xor8(v, s);
+        v = v + neg_if(p, (l & s) == 0);  // v + p where bit s of l is set, v - p elsewhere
     }
     return v;
 }

@@ -153,6 +153,20 @@ __device__ __forceinline__ uint32_t tmem_lane_addr(uint32_t base, int col) {
     return base + ((quarter * 32u) << 16) + (uint32_t)col;
 }
 
+// Bulk asynchronous copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from
+// shared to global memory, in this thread's current bulk group; make the shared-memory writes
+// visible to the async proxy first (fence_smem_to_async).
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until the thread's bulk groups have finished reading their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until the thread's bulk groups have completed (their writes performed).
+__device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void st_bf16(unsigned char *tile, int r, int k, int K, float x) {
     *reinterpret_cast<__nv_bfloat16 *>(tile + core_offset(r, k, K)) = __float2bfloat16_rn(x);
 }
