@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kTnThreads, 2) k_tf32(Tf32Args A, const double
             {
                 const double *le = A.lap + (int64_t)kLapPairs * e;
 #pragma unroll
-                for (int j = l; j < kLapPairs; j += 8) sm.geo[es][j] = mu * from_double<float>(__ldg(le + j));
+                for (int j = l; j < kLapPairs; j += 8) sm.geo[es][j] = mu * (float)__ldg(le + j);  // (a cast: the FP64 pipe is idle here; the integer conversion measured 6% slower)
             }
             // residual: nodal forces of the lane's node
             float f[3];
