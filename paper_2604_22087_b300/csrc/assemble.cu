@@ -28,6 +28,7 @@ struct ElemArgs {
     const Material *__restrict__ mats;
     const double *__restrict__ E_elem;
     const int32_t *__restrict__ elems;  // element ids of one colour (NULL = identity)
+    const uint8_t *__restrict__ order;  // FP64 tangent: the colour's off-diagonal item order (or NULL)
     int64_t n;                          // number of elements in the list
     uint32_t *flags;
 };
@@ -41,13 +42,27 @@ __device__ __forceinline__ void raise_flag(uint32_t *flags, uint32_t bits) {
     if (bits) atomicOr(flags, bits);
 }
 
-// CSR scatter of one value: the first writer of a block stores (no read), later writers add.
-template <typename VT>
-__device__ __forceinline__ void put_or_add(VT *dst, VT v, bool first) {
-    if (first)
-        *dst = v;
-    else
-        *dst += v;
+// CSR scatter of one 3 x 3 block at slot s of node n's rows (kTrans: the transpose): the first
+// writer of a block stores (no read), later writers add.  The choice is made once per block: a
+// lane-wise choice per value was executed as predicated additions, which occupy the FP64 pipe
+// whether or not a lane adds.
+template <typename VT, typename T, bool kTrans>
+__device__ __forceinline__ void put_or_add_block(VT *__restrict__ vals, const int64_t *__restrict__ rowptr,
+                                                 int32_t n, int s, const T K[3][3], bool first) {
+    VT *row[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) row[i] = vals + rowptr[3 * (int64_t)n + i] + 3 * s;
+    if (first) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) row[i][k] = store_as<VT>(kTrans ? K[k][i] : K[i][k]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) row[i][k] += store_as<VT>(kTrans ? K[k][i] : K[i][k]);
+    }
 }
 
 // ---------------------------------------------------------------------------- residual
@@ -443,7 +458,12 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         for (int it = threadIdx.x; it < L::kElems * 36; it += blockDim.x) {
             int ee, a, b, li;
             bool off;
-            item_nodes(it, ee, a, b, off, li);
+            int itm = it;
+            if (kFirst && A.order) {  // (first-writer pairs grouped into whole warps)
+                const int grp = it / kGroupItems, r = it - kGroupItems * grp;
+                if (r < kGroupOff) itm = kGroupItems * grp + A.order[r];
+            }
+            item_nodes(itm, ee, a, b, off, li);
             const int32_t eid = sm.elem[ee];
             if (eid < 0) continue;
             const T gs = item_gs(sm, A.lap, ee, li);
@@ -456,21 +476,12 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                     const int32_t nb = sm.node[ee][b];
                     const int sab = slotmap[sbase + 8 * a + b];
                     const int sba = slotmap[sbase + 8 * b + a];
-                    // the block's first writer (lowest colour) stores, later colours accumulate
+                    // the block's first writer (lowest colour) stores, later colours accumulate;
+                    // one choice per block, so a warp whose lanes all store issues no additions
                     const bool fab = kFirst && ((sm.first[ee][a] >> b) & 1);
                     const bool fba = kFirst && ((sm.first[ee][b] >> a) & 1);
-#pragma unroll
-                    for (int i = 0; i < 3; i++) {
-                        VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * sab;
-#pragma unroll
-                        for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), fab);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        VT *dst = vals + rowptr[3 * (int64_t)nb + k] + 3 * sba;
-#pragma unroll
-                        for (int i = 0; i < 3; i++) put_or_add(dst + i, store_as<VT>(Kab[i][k]), fba);
-                    }
+                    put_or_add_block<VT, T, false>(vals, rowptr, na, sab, Kab, fab);
+                    put_or_add_block<VT, T, true>(vals, rowptr, nb, sba, Kab, fba);
                 }
             } else {
                 T Ra[3];
@@ -479,12 +490,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                 {
                     const int saa = slotmap[sbase + 9 * a];
                     const bool faa = kFirst && ((sm.first[ee][a] >> a) & 1);
-#pragma unroll
-                    for (int i = 0; i < 3; i++) {
-                        VT *dst = vals + rowptr[3 * (int64_t)na + i] + 3 * saa;
-#pragma unroll
-                        for (int k = 0; k < 3; k++) put_or_add(dst + k, store_as<VT>(Kab[i][k]), faa);
-                    }
+                    put_or_add_block<VT, T, false>(vals, rowptr, na, saa, Kab, faa);
                 }
                 if (R) {
                     const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
@@ -831,6 +837,7 @@ static ElemArgs make_args(jetsci_mesh m, const double *E_elem) {
     A.geom = m->d_geom;
     A.lap = m->d_lap;
     A.lin = nullptr;
+    A.order = nullptr;
     A.re = nullptr;
     A.phase = m->d_phase;
     A.mats = m->d_mats;
@@ -907,13 +914,16 @@ static jetsci_status tangent_colours(jetsci_mesh m, ElemArgs A, const double *u,
     // One launch per colour.  Splitting colours into L2-sized chunks (chunk-major order) was
     // measured slower at 128^3 for every precision: the 8x more, smaller launches lose more
     // in launch tails than the L2-resident read-modify-writes gain.
-    for_each_colour(m, [&](const int32_t *elems, int64_t n) {
-        A.elems = elems;
+    for (int c = 0; c < m->n_colours; c++) {
+        const int64_t n = m->colour_ptr[c + 1] - m->colour_ptr[c];
+        if (n <= 0) continue;
+        A.elems = m->d_colour_elems + m->colour_ptr[c];
         A.n = n;
+        A.order = m->d_item_order + 224 * (int64_t)c;
         unsigned grid = (unsigned)((A.n + TangentLayout<T>::kElems - 1) / TangentLayout<T>::kElems);
         k_tangent<T, VT, false><<<grid, TangentLayout<T>::kThreads, smem, s>>>(A, u, m->d_rowptr, m->d_slot,
                                                                               m->d_first, vals, R);
-    });
+    }
     JETSCI_CUDA_TRY(cudaGetLastError());
     return JETSCI_OK;
 }

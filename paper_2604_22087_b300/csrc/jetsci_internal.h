@@ -55,6 +55,8 @@ struct jetsci_mesh_s {
     int64_t *d_rowptr = nullptr;        // [n_dof+1]
     int32_t *d_col = nullptr;           // [nnz]
     uint8_t *d_slot = nullptr;          // [n_elem*64]: slot[a*8+b] = rank of node b among node a's neighbours
+    uint8_t *d_item_order = nullptr;    // [n_colours][224]: order of the FP64 tangent's off-diagonal
+                                        // work items per colour (assemble.cu, first-writer grouping)
     uint8_t *d_first = nullptr;         // [n_elem*8]: bit b of byte a set = the element writes CSR block
                                         // (node a, node b) first (lowest colour among its elements)
     int32_t *d_colour_elems = nullptr;  // [n_elem], grouped by colour, ascending within a colour

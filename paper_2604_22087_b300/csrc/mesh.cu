@@ -131,6 +131,7 @@ static void free_mesh(jetsci_mesh m) {
     cudaFree(m->d_col);
     cudaFree(m->d_slot);
     cudaFree(m->d_first);
+    cudaFree(m->d_item_order);
     cudaFree(m->d_colour_elems);
     cudaFree(m->d_ne_ptr);
     cudaFree(m->d_ne);
@@ -278,6 +279,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     if ((st = dev_alloc(&m->d_col, m->nnz))) return st;
     if ((st = dev_alloc(&m->d_slot, 64 * n_elem))) return st;
     if ((st = dev_alloc(&m->d_first, 8 * n_elem))) return st;
+    if ((st = dev_alloc(&m->d_item_order, (size_t)224 * std::max(n_col, 1)))) return st;
     if ((st = dev_alloc(&m->d_colour_elems, n_elem))) return st;
     if ((st = dev_alloc(&m->d_ne_ptr, n_nodes + 1))) return st;
     if ((st = dev_alloc(&m->d_ne, 8 * n_elem))) return st;
@@ -343,6 +345,31 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cleanup_tmp();
     if (e != cudaSuccess) return cuda_fail(e, "pattern build");
+    // Order of the FP64 tangent's off-diagonal work items in each colour (assemble.cu): the node
+    // pairs (a < b) the colour's middle element writes first come first, for each of a block's
+    // eight elements in turn, then the others.  On a structured mesh every interior element of a
+    // colour has the middle element's first-writer bits, and the groups fill whole warps.
+    std::vector<uint8_t> order((size_t)224 * std::max(n_col, 1));
+    for (int c = 0; c < n_col; c++) {
+        uint8_t mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int64_t len = m->colour_ptr[c + 1] - m->colour_ptr[c];
+        if (len > 0) {
+            const int64_t rep = colour_elems[m->colour_ptr[c] + len / 2];
+            e = cudaMemcpy(mask, m->d_first + 8 * rep, 8, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "first-writer masks");
+        }
+        uint8_t *o = order.data() + (size_t)224 * c;
+        int n = 0;
+        for (int pass = 0; pass < 2; pass++)
+            for (int ee = 0; ee < 8; ee++)
+                for (int pa = 0, p = 0; pa < 8; pa++)
+                    for (int pb = pa + 1; pb < 8; pb++, p++) {
+                        const bool first = (mask[pa] >> pb) & 1;
+                        if (first == (pass == 0)) o[n++] = (uint8_t)(28 * ee + p);
+                    }
+    }
+    e = cudaMemcpy(m->d_item_order, order.data(), order.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "tangent item order");
     return JETSCI_OK;
 }
 
