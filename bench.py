@@ -49,7 +49,21 @@ TANGENT_BYTES_PER_ELEM_FP64 = 4_409.0
 # DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
 # coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
-TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_695.0
+TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_463.0
+# FP32 element kernels are bound by instruction issue (4 warp instructions per clock per SM), not by
+# a math pipe or DRAM: warp instructions per element from one ncu capture each of the 64^3 fibre
+# RVE (profiles/k_tangent_fp32_fibre64.md, k_gather_rows_fp32_fibre64.md, k_apply_mf_fp32_fibre64.md,
+# k_residual_fp32_fibre64.md), with their DRAM bytes per element and the algorithmic bytes (FP32
+# tangent: the write-once FP32 CSR values 980 + slot map 64 + u, R and connectivity 82 + L_ab 288;
+# matrix-free K.v: u, v, coordinates and the y write 98 + connectivity and phase 33).
+FP32_FORMS = {
+    "tangent_csr_fp32": {"warp_instr": 765.0 + 349.0, "dram_bytes": 2639.0 + 3528.0, "alg_bytes": 1414.0,
+                         "kernels": "k_tangent<float,float,1> (element pass) + k_gather_rows<float> (row pass)"},
+    "apply_matrix_free_fp32": {"warp_instr": 377.0, "dram_bytes": 858.0, "alg_bytes": 131.0,
+                               "kernels": "k_apply_mf<float,0> (eight colour launches)"},
+    "residual_fp32": {"warp_instr": 291.0, "dram_bytes": 662.0, "alg_bytes": 107.0,
+                      "kernels": "k_residual<float,0> (eight colour launches)"},
+}
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
 # index (a node's three rows share one column list); v and y are per-row and stay in L2.
 SPMV_BYTES_PER_NNZ = {"fp64": 8.0 + 4.0 / 3.0, "fp32": 4.0 + 4.0 / 3.0}
@@ -969,6 +983,21 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
         mesh.norm2(R, out=nrm, stream=stream)
 
     rec("step_fp64_csr_only", timeit(fp64_csr_step, stream))
+    # the FP32 forms against their own bound (instruction issue) and against HBM
+    peaks, _ = load_peaks()
+    issue_peak = 4.0 * 148 * peaks.get("sm_max_mhz", 2032.0) * 1e6  # warp instructions per second
+    for name, f in FP32_FORMS.items():
+        sec = out[name]["ms"] * 1e-3
+        out[name]["roofline"] = {
+            "bound": "issue", "kernels": f["kernels"],
+            "issue_frac": f["warp_instr"] * prob.n_elem / sec / issue_peak,
+            "warp_instr_per_elem": f["warp_instr"],
+            "hbm_frac_algorithmic": f["alg_bytes"] * prob.n_elem / sec / 1e9 / peaks["hbm_gbs"],
+            "hbm_frac_dram": f["dram_bytes"] * prob.n_elem / sec / 1e9 / peaks["hbm_gbs"],
+            "dram_bytes_per_elem": f["dram_bytes"], "algorithmic_bytes_per_elem": f["alg_bytes"],
+            "note": "issue_frac: ncu warp instructions per element x elements / time over 4 per clock per SM "
+                    "at the maximum SM clock; hbm_frac_*: algorithmic and ncu DRAM bytes per element over "
+                    "the measured HBM peak"}
     if not args.no_extras:
         s, tinfo = train_surrogate(J, torch, I)
         out["surrogate_training"] = tinfo
