@@ -35,7 +35,7 @@ struct ElemArgs {
 
 template <typename T>
 __device__ __forceinline__ bool finite3(const T f[3]) {
-    return isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]);
+    return finite_t(f[0]) && finite_t(f[1]) && finite_t(f[2]);
 }
 
 __device__ __forceinline__ void raise_flag(uint32_t *flags, uint32_t bits) {
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     T f[3];
     nodal_force_of_moment(Q, K, l, f);
     if (active) {
-        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+        uint32_t bits = (positive(K.dJ) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
                         (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
         raise_flag(A.flags, bits);
 #pragma unroll
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                 }
         }
         if (active) {
-            uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE);
+            uint32_t bits = (positive(K.dJ) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE);
             raise_flag(A.flags, bits);
         }
         const T cw = K.dJ * T(1.0 / 512.0);
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                     put_or_add_block<VT, T, false>(vals, rowptr, na, saa, Kab, faa);
                 }
                 if (R) {
-                    const bool fin = isfinite(Ra0) && isfinite(Ra1) && isfinite(Ra2);
+                    const bool fin = finite_t(Ra0) && finite_t(Ra1) && finite_t(Ra2);
                     if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
                     R[3 * (int64_t)na] += to_double(Ra0);
                     R[3 * (int64_t)na + 1] += to_double(Ra1);
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                     for (int k = 0; k < 3; k++) res[j][3 * i + k] = store_as<VT>(Kab[i][k]);
                 const int32_t eid = sm.elem[ee];
                 if (!off && R && eid >= 0) {
-                    const bool fin = isfinite(Ra[0]) && isfinite(Ra[1]) && isfinite(Ra[2]);
+                    const bool fin = finite_t(Ra[0]) && finite_t(Ra[1]) && finite_t(Ra[2]);
                     if (!fin) raise_flag(A.flags, JETSCI_FLAG_NONFINITE);
 #pragma unroll
                     for (int i = 0; i < 3; i++) R[3 * (8 * (int64_t)eid + a) + i] = to_double(Ra[i]);
@@ -657,7 +657,7 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
     T f[3];
     nodal_force_of_moment(Q, K, l, f);
     if (active) {
-        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+        uint32_t bits = (positive(K.dJ) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
                         (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
         raise_flag(A.flags, bits);
 #pragma unroll
@@ -704,8 +704,8 @@ __global__ void __launch_bounds__(128) k_material_grad(ElemArgs A, const double 
                R[3 * (int64_t)node + 2] * to_double(f[2]);
     d = allreduce8(d);
     if (active && l == 0) {
-        uint32_t bits = (K.dJ > T(0) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
-                        (isfinite(d) ? 0u : JETSCI_FLAG_NONFINITE);
+        uint32_t bits = (positive(K.dJ) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
+                        (finite_t(d) ? 0u : JETSCI_FLAG_NONFINITE);
         raise_flag(A.flags, bits);
         g[e] = d;
     }

@@ -70,6 +70,19 @@ __device__ __forceinline__ double neg_if(double x, bool neg) {
 }
 __device__ __forceinline__ df64 neg_if(df64 x, bool neg) { return df64(neg_if(x.h, neg), neg_if(x.l, neg)); }
 
+// x > 0 and isfinite(x).  For doubles these test the bit pattern with integer operations: an
+// FP64 comparison issues on the FP64 pipe, whose slots the FP64 element kernels need for their
+// arithmetic.  positive is false for NaN and for both zeros, as the comparison is.
+__device__ __forceinline__ bool positive(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool positive(df64 x) { return x.h > 0.0f || (x.h == 0.0f && x.l > 0.0f); }
+__device__ __forceinline__ bool finite_t(double x) { return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff; }
+__device__ __forceinline__ bool finite_t(float x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_t(df64 x) { return isfinite(x); }
+
 // Nodal values (lane = node in binary order) -> 8 * monomial coefficient (lane = monomial).
 __device__ __forceinline__ double butterfly_forward(double v, int l) {
 #pragma unroll
@@ -584,7 +597,7 @@ __device__ __forceinline__ void constitutive(int law, T lam, T mu, const T H[3][
     T aF[3][3];
     adj3(c.F, aF);
     T J = c.F[0][0] * aF[0][0] + c.F[0][1] * aF[1][0] + c.F[0][2] * aF[2][0];
-    c.ok = J > T(0);
+    c.ok = positive(J);
     T Js = c.ok ? J : T(1);
     T rJ = my_rcp(Js);
     T lnJ = my_log(Js);
@@ -638,7 +651,7 @@ __device__ __forceinline__ void neo_hookean_state(const GaussKinematics<T> &K, T
     adj3(s.jm, s.aj);
     const T dj = s.jm[0][0] * s.aj[0][0] + s.jm[0][1] * s.aj[1][0] + s.jm[0][2] * s.aj[2][0];
     const T pj = K.dJ * dj;
-    s.ok = pj > T(0);
+    s.ok = positive(pj);
     const T r = my_rcp(s.ok ? pj : T(1));
     s.rdj = K.dJ * r;
     s.rdJ = dj * r;
