@@ -230,6 +230,39 @@ def test_fp32_bounds(case):
     assert relerr(yc.cpu().numpy(), ref["y_csr"]) <= min(2e-4, g["ycsr"])
 
 
+def test_large_volume_change_fp64():
+    """Neo-Hookean FP64 residual, tangent and matrix-free products (from u and at the stored
+    linearisation) at a large smooth deformation, u_1 = 0.12 sin(pi X_1): the volume ratio J runs
+    over about [0.62, 1.38], so Gauss points (often of one warp) take both ln J paths, the series
+    in J - 1 for |J - 1| < 1/16 and the library log beyond.  Against the oracle (numpy log)."""
+    J = jetsci()
+    coords, conn = I.box_mesh(6, 5, 4, distort=0.2, seed=17)
+    g = np.random.default_rng(17)
+    phase = (g.uniform(size=len(conn)) < 0.5).astype(np.int32)
+    u0 = np.zeros_like(coords)
+    u0[:, 0] = 0.12 * np.sin(np.pi * coords[:, 0])
+    u0 += g.uniform(-1e-3, 1e-3, coords.shape)
+    prob = I.Problem("large_volume_change", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                     u0.ravel(), g.uniform(-1, 1, coords.size))
+    dux = 0.12 * np.pi * np.cos(np.pi * coords[:, 0])
+    assert dux.min() < -0.1 and dux.max() > 0.1 and np.any(np.abs(dux) < 0.05)  # both paths
+    mesh = J.Mesh.of(prob)
+    om = oracle.Mesh.of(prob)
+    rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
+    y_ref = oracle.apply_tangent(om, prob.u, prob.v)
+    u, v = cuda(prob.u), cuda(prob.v)
+    assert relerr(mesh.residual(u).cpu().numpy(), R_ref) <= FP64_TOL
+    R = mesh.new_vector()
+    vals = mesh.tangent_csr(u, R=R)
+    assert relerr(vals.cpu().numpy(), vals_ref) <= FP64_TOL
+    assert relerr(R.cpu().numpy(), R_ref) <= FP64_TOL
+    assert relerr(mesh.apply_tangent(None, v).cpu().numpy(), y_ref) <= FP64_TOL  # stored linearisation
+    assert relerr(mesh.apply_tangent(u, v).cpu().numpy(), y_ref) <= FP64_TOL
+    assert mesh.check() == 0
+    mesh.close()
+
+
 def test_bitwise_determinism(case):
     prob, mesh, _, _ = case
     u, v = cuda(prob.u), cuda(prob.v)
