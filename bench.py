@@ -57,11 +57,11 @@ TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_491.0
 # tangent: the write-once FP32 CSR values 980 + slot map 64 + u, R and connectivity 82 + L_ab 288;
 # matrix-free K.v: u, v, coordinates and the y write 98 + connectivity and phase 33).
 FP32_FORMS = {
-    "tangent_csr_fp32": {"warp_instr": 765.0 + 349.0, "dram_bytes": 2639.0 + 3528.0, "alg_bytes": 1414.0,
+    "tangent_csr_fp32": {"warp_instr": 720.0 + 349.0, "dram_bytes": 2639.0 + 3528.0, "alg_bytes": 1414.0,
                          "kernels": "k_tangent<float,float,1> (element pass) + k_gather_rows<float> (row pass)"},
-    "apply_matrix_free_fp32": {"warp_instr": 377.0, "dram_bytes": 858.0, "alg_bytes": 131.0,
+    "apply_matrix_free_fp32": {"warp_instr": 308.0, "dram_bytes": 858.0, "alg_bytes": 131.0,
                                "kernels": "k_apply_mf<float,0> (eight colour launches)"},
-    "residual_fp32": {"warp_instr": 291.0, "dram_bytes": 662.0, "alg_bytes": 107.0,
+    "residual_fp32": {"warp_instr": 245.0, "dram_bytes": 662.0, "alg_bytes": 107.0,
                       "kernels": "k_residual<float,0> (eight colour launches)"},
 }
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
