@@ -10,24 +10,25 @@
 // is the same for every element (W = j^-1, j = 8 dx/dxi), the two material terms become
 //   K_ab,ik = sum_{q,r,s} n_ar n_bs V_q[(r,s),(i,k)],   V_q[(r,s),(i,k)] = c lam W_ri W_sk + c m W_rk W_si:
 // one product of a constant matrix N[(a,b),(r,s,q)] = n_ar n_bs (64 node pairs x 72) with the
-// elements' V (nine rows (i,k) per element, 72 columns (r,s,q)).  Twenty-four elements share one
-// tcgen05.mma chain (kind::tf32, M = 128 of which the 64 pair rows are used, N = 224 of which 216
-// are used, K = 72): accumulator row (a,b), column 8 (3 (3i + k) + o) + j holds K_ab,ik of element
-// 8 o + j (o = octet) without the geometric term, so
-// the epilogue needs no transposition and adds mu L_ab on the diagonal of each 3 x 3 block.  N is
-// split into two TF32 parts (hi + lo, two MMAs per K step), which leaves the rounding of V as the
-// only TF32 rounding (N itself is formed in FP32); every V entry is dense (no block-diagonal
-// zeros).
+// elements' V (72 columns (r,s,q)).  Since K_ba,ki = K_ab,ik, only the six components i <= k are
+// formed: six rows of V per element, and the epilogue takes K_ab,ik for i > k from the row of
+// pair (b,a).  Forty elements share one tcgen05.mma chain (kind::tf32, M = 128 of which the 64
+// pair rows are used, N = 240, K = 72): accumulator row (a,b), column 8 (5 c + o) + j holds
+// component c of K_ab of element 8 o + j (o = octet) without the geometric term, which the
+// epilogue adds (mu L_ab) on the diagonal of each 3 x 3 block.  N is split into two TF32 parts
+// (hi + lo, two MMAs per K step), which leaves the rounding of V as the only TF32 rounding (N
+// itself is formed in FP32); every V entry is dense (no block-diagonal zeros).
 //
-// Persistent CTAs (six warps, two CTAs per SM: 256 TMEM columns and about 105 KB of shared
-// memory each) loop over batches of 24 elements: thread = element x Gauss point writes its
-// point's 81 V entries, one thread issues the 18 MMAs, then the four warps that see TMEM lanes
-// 0-63 (warps 0, 1, 4 and 5; each reads the lanes of its quarter) read the accumulator rows of
-// the 64 node pairs, one octet of elements per 8-column load, into the element matrices, laid
-// out in shared memory over the V tile; one bulk asynchronous copy writes them out while the
-// next batch's kinematics run (phase 1 waits for its reads before storing V).  The
-// gathers of the next batch are issued before the current batch's arithmetic: the connectivity
-// two batches ahead, the coordinates and displacements one batch ahead.
+// Persistent CTAs (ten warps, two CTAs per SM: 256 TMEM columns and about 110 KB of shared
+// memory each) loop over batches of 40 elements: thread = element x Gauss point writes its
+// point's 54 V entries, one thread issues the 18 MMAs, then the six warps that see TMEM lanes
+// 0-63 (warps 0, 1, 4, 5, 8 and 9; each reads the lanes of its quarter, two components each)
+// read the accumulator rows of the 64 node pairs, one octet of elements per 8-column load, into
+// the element matrices, laid out in shared memory over the V tile three octets at a time; one
+// bulk asynchronous copy per chunk writes them out, the last one while the next batch's
+// kinematics run (V stores wait for its reads).  The gathers of the next batch are issued
+// before the current batch's arithmetic: the connectivity two batches ahead, the coordinates
+// and displacements one batch ahead.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,25 +40,34 @@
 
 namespace jetsci {
 
-constexpr int kTnE = 24;                           // elements per batch (three octets)
+constexpr int kTnE = 40;                           // elements per batch (five octets)
+constexpr int kTnOct = kTnE / 8;
 constexpr int kTnThreads = 8 * kTnE;               // thread = element x Gauss point in phase 1
 constexpr int kTnK = 72;                           // columns (r, s, q): 8 (3 r + s) + q
-constexpr int kTnCols = 9 * kTnE;                  // accumulator columns 8 (3 (3 i + k) + octet) + element
-constexpr int kTnN = (kTnCols + 15) / 16 * 16;     // the MMA's N (a multiple of 16; the last rows unused)
+constexpr int kTnComp = 6;                         // components (i, k), i <= k
+constexpr int kTnN = kTnComp * kTnE;               // accumulator columns 8 (5 c + octet) + element (240)
 constexpr uint32_t kTnTmemCols = 256;
 // K-major core matrices (8 rows x 16 bytes), no padding: LBO = step along K, SBO = 8-row step
 constexpr uint32_t kTnLBO = 128;
 constexpr uint32_t kTnSBO = (kTnK / 4) * kTnLBO;
 constexpr int kTnATile = 8 * kTnSBO;               // the 64 pair rows of N
-constexpr int kTnBTile = (kTnN / 8) * kTnSBO;      // 224 rows of V (216 used)
+constexpr int kTnBTile = (kTnN / 8) * kTnSBO;      // 240 rows of V
+static_assert(kTnN % 16 == 0 && kTnN <= (int)kTnTmemCols, "MMA N");
+static_assert(kTnThreads == 320, "the epilogue gives two components to each of the six warps on TMEM lanes 0-63");
+// octets of element rows staged over the V tile at a time (each written by one bulk copy)
+constexpr int kTnStageOct = kTnBTile / (8 * 576 * 4);
+static_assert(kTnStageOct >= 1, "an octet of element rows fits over the V tile");
+
+// Component c of the accumulator: (i, k) = (0,0) (1,1) (2,2) (0,1) (0,2) (1,2)
+__host__ __device__ constexpr int tn_comp_i(int c) { return c < 3 ? c : (c < 5 ? 0 : 1); }
+__host__ __device__ constexpr int tn_comp_k(int c) { return c < 3 ? c : (c == 3 ? 1 : 2); }
 
 // The MMA reads 128 rows of A; rows 64..127 fall on the next bytes of shared memory (the lo part,
 // then the V tile) and produce accumulator rows that are never read.
 struct __align__(128) TnSmem {
     unsigned char A[2][kTnATile];       // N, hi and lo TF32 parts
-    unsigned char B[kTnBTile];          // V of the batch's 24 elements
+    unsigned char B[kTnBTile];          // V of the batch's elements; then half of their rows
     float geo[kTnE][kLapPairs];         // mu L_ab of each element (kLap* order)
-    int32_t elem[kTnE];
     uint64_t mbar;
     uint32_t tmem_base;
 };
@@ -233,34 +243,42 @@ __global__ void __launch_bounds__(kTnThreads, 2) k_tf32(Tf32Args A, const double
             }
             const float cw = K.dJ * (1.0f / 512.0f);
             const float cl = cw * lam, cm = cw * m;
-            // V_q[(r,s),(i,k)] = c lam W_ri W_sk + c m W_rk W_si at row 8 (3 (3 i + k) + octet) + j,
-            // column 8 (3 r + s) + q; the entry of ((s,r),(k,i)) is the same
+            // V_q[(r,s),(i,k)] = c lam W_ri W_sk + c m W_rk W_si for the components i <= k, at row
+            // 8 (5 c + octet) + j, column 8 (3 r + s) + q.  The diagonal components are
+            // (c lam + c m) W_ri W_si, the same for (r,s) and (s,r).
             float Lw[3][3], Mw[3][3];
 #pragma unroll
             for (int r = 0; r < 3; r++)
 #pragma unroll
                 for (int i = 0; i < 3; i++) Lw[r][i] = cl * W[r][i], Mw[r][i] = cm * W[r][i];
+            const float cs = cl + cm;
             // the previous batch's rows have left the V tile (their bulk copy read it)
             if (t == 0) tc::bulk_wait_read();
             __syncthreads();
             unsigned char *Bt = sm.B;
             // V row (= accumulator column) of component c of this element
-            auto vrow = [&](int c) { return 8 * (3 * c + (es >> 3)) + (es & 7); };
+            auto vrow = [&](int c) { return 8 * (kTnOct * c + (es >> 3)) + (es & 7); };
+            auto vput = [&](int c, int r, int s2, float v) {
+                *reinterpret_cast<float *>(Bt + tn_offset(vrow(c), 8 * (3 * r + s2) + l)) = v;
+            };
 #pragma unroll
-            for (int r = 0; r < 3; r++)
+            for (int i = 0; i < 3; i++)
 #pragma unroll
-                for (int s2 = 0; s2 < 3; s2++)
+                for (int r = 0; r < 3; r++)
 #pragma unroll
-                    for (int i = 0; i < 3; i++)
+                    for (int s2 = r; s2 < 3; s2++) {
+                        const float v = to_tf32(cs * W[r][i] * W[s2][i]);
+                        vput(i, r, s2, v);
+                        if (s2 != r) vput(i, s2, r, v);
+                    }
 #pragma unroll
-                        for (int k = 0; k < 3; k++) {
-                            const int self = 9 * (3 * r + s2) + 3 * i + k, mirror = 9 * (3 * s2 + r) + 3 * k + i;
-                            if (self > mirror) continue;
-                            const float v = to_tf32(fmaf(Lw[r][i], W[s2][k], Mw[r][k] * W[s2][i]));
-                            *reinterpret_cast<float *>(Bt + tn_offset(vrow(3 * i + k), 8 * (3 * r + s2) + l)) = v;
-                            if (mirror != self)
-                                *reinterpret_cast<float *>(Bt + tn_offset(vrow(3 * k + i), 8 * (3 * s2 + r) + l)) = v;
-                        }
+            for (int c = 3; c < kTnComp; c++) {
+                const int i = tn_comp_i(c), k = tn_comp_k(c);
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int s2 = 0; s2 < 3; s2++) vput(c, r, s2, to_tf32(fmaf(Lw[r][i], W[s2][k], Mw[r][k] * W[s2][i])));
+            }
             // geometric term: mu L_ab of the element, lane l holding pairs l, l + 8, ...
             {
                 const double *le = A.lap + (int64_t)kLapPairs * e;
@@ -273,7 +291,6 @@ __global__ void __launch_bounds__(kTnThreads, 2) k_tf32(Tf32Args A, const double
             if (R && active)
 #pragma unroll
                 for (int i = 0; i < 3; i++) R[3 * (8 * e + hex_node_of_lane(l)) + i] = to_double(f[i]);
-            if (l == 0) sm.elem[es] = active ? (int32_t)e : -1;
         }
         // the next batch's coordinates and displacements (its connectivity has arrived)
         if (b + G < n_batches) tf32_gather_values(A, u, nxt);
@@ -294,39 +311,58 @@ __global__ void __launch_bounds__(kTnThreads, 2) k_tf32(Tf32Args A, const double
         const bool ok = tc::mbar_wait_bounded(&sm.mbar, it & 1);
         tc::fence_after_sync();
         if (!ok && t == 0) atomicOr(A.flags, JETSCI_FLAG_NONFINITE);
-        // ---------------- epilogue: thread t < 64 owns accumulator row t = node pair (a, b); the
-        // batch's element matrices are laid out in [element][24][24] order over the V tile (free
-        // once the MMAs completed: conflict-free stores), then every thread copies them out, one
-        // contiguous span of 16-byte stores
+        // ---------------- epilogue, kTnStageOct octets of the batch at a time: the thread of
+        // TMEM lane t < 64 owns accumulator row t = node pair (a, b).  Its component (i, k),
+        // i <= k, is K_ab,ik, and for i < k also K_ba,ki.  The chunk's element matrices are laid
+        // out in [element][24][24] order over the V tile (free once the MMAs completed), then one
+        // bulk asynchronous copy writes them out as one contiguous span; the next chunk waits
+        // until that copy has read the tile, the next batch's V stores until the last one's.
         float *stage = reinterpret_cast<float *>(sm.B);
-        if ((w & 3) < 2) {  // warps 0, 1: components 0-4; warps 4, 5: components 5-8
-            const int pr = 32 * (w & 1) + (t & 31), pa = pr >> 3, pb = pr & 7, li = tg_lap(pa, pb);
-            float *dst = stage + 24 * (3 * pa) + 3 * pb;
-            const int c0 = w < 4 ? 0 : 5, c1 = w < 4 ? 5 : 9;
+        const int64_t eb = b * kTnE;
 #pragma unroll 1
-            for (int c = c0; c < c1; c++) {
-                const int i = c / 3, k = c - 3 * i;
+        for (int o0 = 0; o0 < kTnOct; o0 += kTnStageOct) {
+            const int64_t e0 = eb + 8 * o0;
+            if (e0 >= A.n) break;  // (uniform over the CTA)
+            const int nco = kTnOct - o0 < kTnStageOct ? kTnOct - o0 : kTnStageOct;
+            const int n_el = (int)(A.n - e0 < 8 * nco ? A.n - e0 : 8 * nco);
+            if (o0 > 0) {
+                if (t == 0) tc::bulk_wait_read();
+                __syncthreads();
+            }
+            if ((w & 3) < 2) {  // warps 0 and 1, 4 and 5, 8 and 9 (TMEM lanes 0-63): two components each
+                const int pr = 32 * (w & 1) + (t & 31), pa = pr >> 3, pb = pr & 7, li = tg_lap(pa, pb);
 #pragma unroll 1
-                for (int o = 0; o < kTnE / 8; o++) {
-                    float v[8];
-                    tc::tmem_ld8(tc::tmem_lane_addr(tm, 8 * (3 * c + o)), v);
+                for (int cc = 0; cc < 2; cc++) {
+                    const int c = 2 * (w >> 2) + cc, i = tn_comp_i(c), k = tn_comp_k(c);
+                    const bool dg = c < 3;
+                    float *dst = stage + 24 * (3 * pa + i) + 3 * pb + k;
+                    float *dsT = stage + 24 * (3 * pb + k) + 3 * pa + i;
 #pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        const int el = 8 * o + j;
-                        dst[576 * el + 24 * i + k] = (i == k) ? v[j] + sm.geo[el][li] : v[j];
+                    for (int oo = 0; oo < kTnStageOct; oo++) {
+                        if (oo >= nco) break;
+                        float v[8];
+                        tc::tmem_ld8(tc::tmem_lane_addr(tm, 8 * (kTnOct * c + o0 + oo)), v);
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            const int el = 8 * oo + j;
+                            if (dg) {
+                                dst[576 * el] = v[j] + sm.geo[8 * o0 + el][li];
+                            } else {
+                                dst[576 * el] = v[j];
+                                dsT[576 * el] = v[j];
+                            }
+                        }
                     }
                 }
             }
-        }
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();  // the element matrices are laid out; the next MMA may overwrite TMEM
-        tc::fence_after_sync();
-        if (t == 0) {  // one bulk copy of the batch's contiguous rows; it drains during the next phase 1
-            const int64_t e0 = b * kTnE;
-            const int n_el = (int)(A.n - e0 < kTnE ? A.n - e0 : kTnE);
-            tc::bulk_store(vals + 576 * e0, stage, (uint32_t)n_el * 576u * (uint32_t)sizeof(float));
-            tc::bulk_commit();
+            tc::fence_smem_to_async();
+            tc::fence_before_sync();
+            __syncthreads();  // the chunk's element matrices are laid out (after the last: the next MMA may overwrite TMEM)
+            tc::fence_after_sync();
+            if (t == 0) {  // the last copy drains during the next batch's phase 1
+                tc::bulk_store(vals + 576 * e0, stage, (uint32_t)n_el * 576u * (uint32_t)sizeof(float));
+                tc::bulk_commit();
+            }
         }
         cur = nxt;
         if (b + 2 * G < n_batches) tf32_gather_conn(A, b + 2 * G, es, l, nxt);
@@ -360,7 +396,7 @@ jetsci_status launch_tf32(jetsci_mesh m, const double *u, float *vals, double *R
         JETSCI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
         A.n = m->n_elem;
         const int64_t n_batches = (A.n + kTnE - 1) / kTnE;
-        // two CTAs per SM: 256 TMEM columns and about 105 KB of shared memory each
+        // two CTAs per SM: 256 TMEM columns and about 112 KB of shared memory each
         const unsigned grid = (unsigned)std::min<int64_t>(n_batches, 2 * (int64_t)std::max(sms, 1));
         k_tf32<<<grid, kTnThreads, smem, s>>>(A, u, (float *)ws, Re);
         JETSCI_CUDA_TRY(cudaGetLastError());
