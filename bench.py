@@ -50,8 +50,8 @@ TANGENT_BYTES_PER_ELEM_FP64 = 4_409.0
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
 # coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
 TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_491.0
-# FP32 element kernels are bound by instruction issue (4 warp instructions per clock per SM), not by
-# a math pipe or DRAM: warp instructions per element from one ncu capture each of the 64^3 fibre
+# FP32-value element kernels are bound by instruction issue (4 warp instructions per clock per SM),
+# not by a math pipe or DRAM: warp instructions per element from one ncu capture each of the 64^3 fibre
 # RVE (profiles/k_tangent_fp32_fibre64.md, k_gather_rows_fp32_fibre64.md, k_apply_mf_fp32_fibre64.md,
 # k_residual_fp32_fibre64.md), with their DRAM bytes per element and the algorithmic bytes (FP32
 # tangent: the write-once FP32 CSR values 980 + slot map 64 + u, R and connectivity 82 + L_ab 288;
@@ -63,6 +63,11 @@ FP32_FORMS = {
                                "kernels": "k_apply_mf<float,0> (eight colour launches)"},
     "residual_fp32": {"warp_instr": 245.0, "dram_bytes": 662.0, "alg_bytes": 107.0,
                       "kernels": "k_residual<float,0> (eight colour launches)"},
+    # TF32: the tensor-core element pass (profiles/k_tf32_tangent_fibre64.md, tensor pipe active
+    # 20.7% of its cycles) + the same row pass; the same algorithmic bytes as the FP32 tangent
+    "tangent_csr_tf32": {"warp_instr": 474.0 + 349.0, "dram_bytes": 2642.0 + 3528.0, "alg_bytes": 1414.0,
+                         "kernels": "k_tf32 (tensor-core element pass) + k_gather_rows<float> (row pass)",
+                         "tensor_pipe_active_element_pass": 0.207},
 }
 # Algorithmic bytes per CSR non-zero of the sparse product: the value plus a third of a column
 # index (a node's three rows share one column list); v and y are per-row and stay in L2.
@@ -995,6 +1000,7 @@ def measure_forms(J, torch, I, mesh, prob, stream, u, v, vals64, args):
             "hbm_frac_algorithmic": f["alg_bytes"] * prob.n_elem / sec / 1e9 / peaks["hbm_gbs"],
             "hbm_frac_dram": f["dram_bytes"] * prob.n_elem / sec / 1e9 / peaks["hbm_gbs"],
             "dram_bytes_per_elem": f["dram_bytes"], "algorithmic_bytes_per_elem": f["alg_bytes"],
+            **{k: v for k, v in f.items() if k.startswith("tensor_pipe")},
             "note": "issue_frac: ncu warp instructions per element x elements / time over 4 per clock per SM "
                     "at the maximum SM clock; hbm_frac_*: algorithmic and ncu DRAM bytes per element over "
                     "the measured HBM peak"}
