@@ -66,7 +66,7 @@ __host__ __device__ constexpr int tn_comp_k(int c) { return c < 3 ? c : (c == 3 
 // then the V tile) and produce accumulator rows that are never read.
 struct __align__(128) TnSmem {
     unsigned char A[2][kTnATile];       // N, hi and lo TF32 parts
-    unsigned char B[kTnBTile];          // V of the batch's elements; then half of their rows
+    unsigned char B[kTnBTile];          // V of the batch's elements; then up to three octets of their rows
     float geo[kTnE][kLapPairs];         // mu L_ab of each element (kLap* order)
     uint64_t mbar;
     uint32_t tmem_base;
