@@ -802,3 +802,34 @@ def test_medium_box_row_gather_fp32_tf32():
         assert torch.equal(vals, vals2)
     assert mesh.check() == 0
     mesh.close()
+
+
+@pytest.mark.parametrize("n", [1, 7, 8, 23, 24, 25, 39, 40, 41, 81, 121])
+def test_row_gather_batch_edges(n):
+    """Element counts around the row-gather element passes' batch edges: partial octets, a batch
+    of 40 tensor-core elements whose last staged chunk is partial or empty, several batches.  A
+    chain of n distorted elements (box n x 1 x 1), FP32 and TF32 tangents from NaN-prefilled
+    outputs against the oracle within their guards, and the FP64 tangent at 1e-12."""
+    J = jetsci()
+    coords, conn = I.box_mesh(n, 1, 1, distort=0.2, seed=40 + n)
+    g = np.random.default_rng(40 + n)
+    phase = (g.uniform(size=len(conn)) < 0.5).astype(np.int32)
+    prob = I.Problem(f"chain_{n}", coords, conn, phase, I.composite_materials(I.LAW_NEO_HOOKEAN),
+                     g.uniform(-3e-3, 3e-3, coords.size), g.uniform(-1, 1, coords.size))
+    mesh = J.Mesh.of(prob)
+    om = oracle.Mesh.of(prob)
+    rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
+    u = cuda(prob.u)
+    for name in ("FP64", "FP32", "TF32"):
+        p = getattr(J, name)
+        R = torch.full((mesh.n_dof,), float("nan"), dtype=torch.float64, device="cuda")
+        vals = mesh.new_values(p)
+        vals.fill_(float("nan"))
+        mesh.tangent_csr(u, vals=vals, R=R, precision=p)
+        tv = FP64_TOL if name == "FP64" else GUARD[name]["vals"]
+        tr = FP64_TOL if name == "FP64" else GUARD[name]["R"]
+        assert relerr(vals.cpu().numpy(), vals_ref) <= tv, name
+        assert relerr(R.cpu().numpy(), R_ref) <= tr, name
+    assert mesh.check() == 0
+    mesh.close()
