@@ -84,9 +84,14 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     ElemMaterial mt = element_material(A.mats, A.phase, A.E_elem, e, false);
     T Q[3][3];
     NeoHookeanState<T> st;
-    const bool ok = residual_moment<T>(K, mt.law, from_double<T>(mt.lam), from_double<T>(mt.mu), Q, &st);
+    const T lam = from_double<T>(mt.lam), mu = from_double<T>(mt.mu);
+    const bool ok = residual_moment<T>(K, mt.law, lam, mu, Q, &st);
     if constexpr (!std::is_same<T, float>::value)  // FP64 and two-float calls store the state
-        if (A.lin && active && mt.law != JETSCI_LINEAR_ELASTIC) lin_store_t<T>(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
+        if (A.lin && active && mt.law != JETSCI_LINEAR_ELASTIC) {
+            LinCoeffs<T> c;
+            lin_coeffs(st.aj, st.rdj, st.rdJ, K.dJ, st.m, lam, mu, c);
+            lin_store_t<T>(A.lin, e, l, c);
+        }
     T f[3];
     nodal_force_of_moment(Q, K, l, f);
     if (active) {
@@ -376,7 +381,11 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             ok = st.ok;
             m = st.m;
             if constexpr (!std::is_same<T, float>::value)  // FP64 and two-float calls store the state
-                if (A.lin && active) lin_store_t<T>(A.lin, e, l, st.aj, st.m, st.rdJ, st.rdj);
+                if (A.lin && active) {
+                    LinCoeffs<T> c;
+                    lin_coeffs(st.aj, st.rdj, st.rdJ, K.dJ, st.m, lam, mu, c);
+                    lin_store_t<T>(A.lin, e, l, c);
+                }
 #pragma unroll
             for (int d = 0; d < 3; d++)
 #pragma unroll
@@ -564,9 +573,12 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 // F^-1 = Jp j^-1, J = det j / det Jp and h = Dv j^-1 (Dv = 8 dv/dxi), and forms the moment
 // Q = Y adj(Jp)^T directly:
 //   Q = (mu / det Jp) Dv adj(Jp) adj(Jp)^T + (det Jp / det j^2) M' adj(j)^T,
-//   M' = m h'^T + lam tr(h') I,  h' = Dv adj(j) = det j h.
-// kReuse (FP64 and two-float): the neo-Hookean state comes from the mesh's linearisation store
-// (the last FP64 or two-float residual or tangent, at its u) instead of u; u is not read.
+//   M' = m h'^T + lam tr(h') I,  h' = Dv adj(j) = det j h,
+// i.e. Q = s1 Dv adj(Jp) adj(Jp)^T + (alpha h'^T + beta tr(h') I) adj(j)^T with the per-point
+// coefficients s1 = mu / det Jp, alpha = m det Jp / det j^2, beta = lam det Jp / det j^2
+// (element.cuh, lin_coeffs).
+// kReuse (FP64 and two-float): the coefficients come from the mesh's linearisation store (the
+// last FP64 or two-float residual or tangent, at its u) instead of u; u is not read.
 template <typename T, bool kReuse>
 __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__restrict__ u,
                                                  const double *__restrict__ v, double *__restrict__ y) {
@@ -607,25 +619,21 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
 #pragma unroll
             for (int d = 0; d < 3; d++) Q[i][d] = Y[i][0] * K.aJ[d][0] + Y[i][1] * K.aJ[d][1] + Y[i][2] * K.aJ[d][2];
     } else {
-        T m, rdj, rdJ, aj[3][3];
+        LinCoeffs<T> c;
         if constexpr (kReuse) {
-            lin_load_t<T>(A.lin, e, l, aj, m, rdJ, rdj);  // (states outside the law were flagged when stored)
+            lin_load_t<T>(A.lin, e, l, c);  // (states outside the law were flagged when stored)
         } else {
             NeoHookeanState<T> st;
             neo_hookean_state(K, lam, mu, st);
             ok = st.ok;
-            m = st.m, rdj = st.rdj, rdJ = st.rdJ;
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int k = 0; k < 3; k++) aj[i][k] = st.aj[i][k];
+            lin_coeffs(st.aj, st.rdj, st.rdJ, K.dJ, st.m, lam, mu, c);
         }
         T hp[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * aj[0][k] + Dv[i][1] * aj[1][k] + Dv[i][2] * aj[2][k];
-        const T ltr = lam * (hp[0][0] + hp[1][1] + hp[2][2]);
+            for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * c.aj[0][k] + Dv[i][1] * c.aj[1][k] + Dv[i][2] * c.aj[2][k];
+        const T btr = c.beta * (hp[0][0] + hp[1][1] + hp[2][2]);
         // A0 = adj(Jp) adj(Jp)^T (symmetric; read from the geometry cache for FP64 and two-float)
         T A0[3][3];
         if constexpr (std::is_same<T, double>::value || std::is_same<T, df64>::value) {
@@ -639,18 +647,19 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
         } else {
             adj_gram(K.aJ, A0);
         }
-        const T s1 = mu * rdJ, s2 = K.dJ * rdj * rdj;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            // row i of M' = m h'^T + lam tr(h') I
-            const T M0 = fma_t(m, hp[0][i], (i == 0) ? ltr : T(0));
-            const T M1 = fma_t(m, hp[1][i], (i == 1) ? ltr : T(0));
-            const T M2 = fma_t(m, hp[2][i], (i == 2) ? ltr : T(0));
+            // row i of alpha h'^T + beta tr(h') I
+            const T M0 = fma_t(c.alpha, hp[0][i], (i == 0) ? btr : T(0));
+            const T M1 = fma_t(c.alpha, hp[1][i], (i == 1) ? btr : T(0));
+            const T M2 = fma_t(c.alpha, hp[2][i], (i == 2) ? btr : T(0));
 #pragma unroll
             for (int d = 0; d < 3; d++) {
                 const T p1 = Dv[i][0] * A0[0][d] + Dv[i][1] * A0[1][d] + Dv[i][2] * A0[2][d];
-                const T p2 = M0 * aj[d][0] + M1 * aj[d][1] + M2 * aj[d][2];
-                Q[i][d] = fma_t(s1, p1, s2 * p2);
+                T q = c.s1 * p1;
+                q = fma_t(M0, c.aj[d][0], q);
+                q = fma_t(M1, c.aj[d][1], q);
+                Q[i][d] = fma_t(M2, c.aj[d][2], q);
             }
         }
     }

@@ -340,34 +340,49 @@ __device__ __forceinline__ double2 geom_pair(const double *__restrict__ p, int k
 constexpr int kLapPairs = 36, kLapDiag = 28;
 
 // Linearisation of the neo-Hookean state at the last FP64 or two-float residual or tangent call,
-// kept per mesh for matrix-free products at that state: adj(j) (0-8), m (9), 1 / det Jp (10) and
-// 1 / det j (11) per element and Gauss point, in pairs as [element][6][Gauss point][2] doubles.
-constexpr int kLinAj = 0, kLinM = 9, kLinRdJ = 10, kLinRdj = 11, kLinPairs = 6;
+// kept per mesh for matrix-free products at that state, in the form those products use
+// (apply_mf_element): adj(j) (0-8), alpha = m det Jp / det j^2 (9), beta = lam det Jp / det j^2
+// (10) and s1 = mu / det Jp (11) per element and Gauss point, in pairs as
+// [element][6][Gauss point][2] doubles.
+constexpr int kLinAj = 0, kLinAlpha = 9, kLinBeta = 10, kLinS1 = 11, kLinPairs = 6;
 
-__device__ __forceinline__ void lin_store(double *__restrict__ lin, int64_t e, int l, const double aj[3][3], double m,
-                                          double rdJ, double rdj) {
-    const double f[2 * kLinPairs] = {aj[0][0], aj[0][1], aj[0][2], aj[1][0], aj[1][1], aj[1][2],
-                                     aj[2][0], aj[2][1], aj[2][2], m,        rdJ,      rdj};
+template <typename T>
+struct LinCoeffs {
+    T aj[3][3];
+    T alpha, beta, s1;
+};
+
+// The coefficients at a neo-Hookean state: adj(j), 1 / det j (rdj), 1 / det Jp (rdJ), det Jp
+// (dJ), m = mu - lam ln J.
+template <typename T>
+__device__ __forceinline__ void lin_coeffs(const T aj[3][3], T rdj, T rdJ, T dJ, T m, T lam, T mu, LinCoeffs<T> &c) {
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) c.aj[i][k] = aj[i][k];
+    const T s2 = dJ * rdj * rdj;
+    c.alpha = s2 * m;
+    c.beta = s2 * lam;
+    c.s1 = mu * rdJ;
+}
+
+// The coefficients of a two-float (or FP64) neo-Hookean update, stored in FP64 (two-float values
+// rounded to the nearest double, about 48 significant bits either way).
+template <typename T>
+__device__ __forceinline__ void lin_store_t(double *__restrict__ lin, int64_t e, int l, const LinCoeffs<T> &c) {
+    const double f[2 * kLinPairs] = {to_double(c.aj[0][0]), to_double(c.aj[0][1]), to_double(c.aj[0][2]),
+                                     to_double(c.aj[1][0]), to_double(c.aj[1][1]), to_double(c.aj[1][2]),
+                                     to_double(c.aj[2][0]), to_double(c.aj[2][1]), to_double(c.aj[2][2]),
+                                     to_double(c.alpha),    to_double(c.beta),     to_double(c.s1)};
     double2 *p = reinterpret_cast<double2 *>(lin + (int64_t)2 * kLinPairs * 8 * e + 2 * l);
 #pragma unroll
     for (int k = 0; k < kLinPairs; k++) p[8 * k] = make_double2(f[2 * k], f[2 * k + 1]);
 }
 
-// The state of a two-float (or FP64) neo-Hookean update, stored in FP64 (two-float values rounded
-// to the nearest double, about 48 significant bits either way).
+// The stored coefficients in the element type T (FP64 as stored; two-float by splitting each
+// double).
 template <typename T>
-__device__ __forceinline__ void lin_store_t(double *__restrict__ lin, int64_t e, int l, const T aj[3][3], T m, T rdJ,
-                                            T rdj) {
-    double a[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) a[i][k] = to_double(aj[i][k]);
-    lin_store(lin, e, l, a, to_double(m), to_double(rdJ), to_double(rdj));
-}
-
-__device__ __forceinline__ void lin_load(const double *__restrict__ lin, int64_t e, int l, double aj[3][3], double &m,
-                                         double &rdJ, double &rdj) {
+__device__ __forceinline__ void lin_load_t(const double *__restrict__ lin, int64_t e, int l, LinCoeffs<T> &c) {
     const double2 *p = reinterpret_cast<const double2 *>(lin + (int64_t)2 * kLinPairs * 8 * e + 2 * l);
     double f[2 * kLinPairs];
 #pragma unroll
@@ -379,25 +394,10 @@ __device__ __forceinline__ void lin_load(const double *__restrict__ lin, int64_t
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) aj[i][j] = f[kLinAj + 3 * i + j];
-    m = f[kLinM];
-    rdJ = f[kLinRdJ];
-    rdj = f[kLinRdj];
-}
-
-// The stored state in the element type T (FP64 as stored; two-float by splitting each double).
-template <typename T>
-__device__ __forceinline__ void lin_load_t(const double *__restrict__ lin, int64_t e, int l, T aj[3][3], T &m, T &rdJ,
-                                           T &rdj) {
-    double a[3][3], md, rJ, rj;
-    lin_load(lin, e, l, a, md, rJ, rj);
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) aj[i][k] = from_double<T>(a[i][k]);
-    m = from_double<T>(md);
-    rdJ = from_double<T>(rJ);
-    rdj = from_double<T>(rj);
+        for (int j = 0; j < 3; j++) c.aj[i][j] = from_double<T>(f[kLinAj + 3 * i + j]);
+    c.alpha = from_double<T>(f[kLinAlpha]);
+    c.beta = from_double<T>(f[kLinBeta]);
+    c.s1 = from_double<T>(f[kLinS1]);
 }
 
 // Kinematics at the lane's Gauss point from the lane's node's coordinates X and nodal field
