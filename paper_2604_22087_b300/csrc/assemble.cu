@@ -125,11 +125,15 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
 //   A_ik = sum_q h_ai g_bk + h_ak g_bi  (symmetric),   B_ik = sum_q d_ai g_bk - d_ak g_bi  (skew),
 // and K_ab,ii = 2 sum_q h_ai g_bi + mu L_ab: 15 multiply-adds per Gauss point, against 21 for
 // accumulating c lam g_ai g_bk, c m g_ak g_bi and the geometric term tg_a . g_b separately.
-// FP64 elements, bound by B300's FP64 pipe, store h_a and d_a; FP32 and two-float elements form
-// them from g_a and two coefficients, keeping the smaller record, which leaves room for more
-// resident blocks.
+// FP32 and two-float elements form h_a and d_a from g_a and two coefficients, keeping the
+// smaller record, which leaves room for more resident blocks.  FP64 elements, bound by B300's
+// FP64 pipe, store l_a = c lam g_a, m_a = c m g_a and s_a = l_a + m_a and accumulate the entries
+// directly, K_ab,ik = sum_q l_ai g_bk + m_ak g_bi (i != k) and sum_q s_ai g_bi + mu L_ab
+// (i == k): also 15 multiply-adds per Gauss point, with the sums of the diagonal entries
+// starting from mu L_ab and no finishing operations (the A +- B and 2 A + mu L_ab of the
+// symmetric/skew form: 9 per off-diagonal pair), for 3 more multiplies per node and point.
 
-// Shared memory: one array per per-node vector (g and, for FP64, h and d), each
+// Shared memory: one array per per-node vector (g and, for FP64, l, m and s), each
 // [element][Gauss point][node][3], nodes 3 entries apart, so that the eight nodes of an element
 // read in phase 2 fall on distinct banks.  Elements are 200 entries apart (8 mod 32 words for
 // FP32, 16 mod 32 for 8-byte types), which also spreads the up to four elements of one warp
@@ -148,13 +152,13 @@ struct TangentLayout {
     // are held in registers until the matrices are assembled, and three items per thread
     // instead of five were 5% faster (four warps: slower).
     static constexpr int kThreads = kPre ? 192 : (std::is_same<T, float>::value ? 96 : 8 * kElems);
-    static constexpr int kNumVec = kPre ? 3 : 1;
+    static constexpr int kNumVec = kPre ? 4 : 1;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
     static constexpr int kArr = kElems * kElem;
     // per (element, Gauss point): (c lam + c m)/2, (c lam - c m)/2, c Tg (00,11,22,12,02,01); odd stride
     static constexpr int kCoef = 9;
-    enum { kG = 0, kHG = 1, kDG = 2 };
+    enum { kG = 0, kLG = 1, kMG = 2, kSG = 3 };  // g, c lam g, c m g, (c lam + c m) g (FP64)
     // FP64 values: each CSR block's first writer stores and no clearing pass is needed (saves
     // the 4 GB memset at 128^3).  The two-float kernel was measured slower that way (the
     // partial-sector first stores and the divergent store/accumulate paths cost more than the
@@ -185,6 +189,32 @@ __device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, 
     using L = TangentLayout<T>;
     const T *pa = sm.v + ee * L::kElem + 3 * a;
     const T *pb = sm.v + ee * L::kElem + 3 * b;
+    if constexpr (L::kPre) {
+        // FP64: K_ab,ik = sum_q l_ai g_bk + m_ak g_bi for i != k and sum_q s_ai g_bi + mu L_ab
+        // for i == k (l = c lam g, m = c m g, s = l + m): 15 multiply-adds per Gauss point and no
+        // finishing operations (the diagonal sums start from mu L_ab)
+        T K00 = gs, K11 = gs, K22 = gs, K01 = T(0), K10 = T(0), K02 = T(0), K20 = T(0), K12 = T(0), K21 = T(0);
+#pragma unroll kUnrollQ
+        for (int q = 0; q < 8; q++) {
+            const T *qa = pa + q * L::kPoint;
+            const T *qb = pb + q * L::kPoint;
+            const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
+            const T *la = qa + L::kLG * L::kArr, *ma = qa + L::kMG * L::kArr, *sa = qa + L::kSG * L::kArr;
+            const T l0 = la[0], l1 = la[1], l2 = la[2], m0 = ma[0], m1 = ma[1], m2 = ma[2];
+            K00 = acc_t(sa[0], b0, K00);
+            K11 = acc_t(sa[1], b1, K11);
+            K22 = acc_t(sa[2], b2, K22);
+            K01 = acc_t(l0, b1, acc_t(m1, b0, K01));
+            K10 = acc_t(l1, b0, acc_t(m0, b1, K10));
+            K02 = acc_t(l0, b2, acc_t(m2, b0, K02));
+            K20 = acc_t(l2, b0, acc_t(m0, b2, K20));
+            K12 = acc_t(l1, b2, acc_t(m2, b1, K12));
+            K21 = acc_t(l2, b1, acc_t(m1, b2, K21));
+        }
+        Kab[0][0] = K00, Kab[1][1] = K11, Kab[2][2] = K22;
+        Kab[0][1] = K01, Kab[1][0] = K10, Kab[0][2] = K02, Kab[2][0] = K20, Kab[1][2] = K12, Kab[2][1] = K21;
+        return;
+    }
     const T *pc = sm.coef + ee * 8 * L::kCoef;
     T A00 = T(0), A11 = T(0), A22 = T(0), A01 = T(0), A02 = T(0), A12 = T(0);
     T B01 = T(0), B02 = T(0), B12 = T(0);
@@ -193,15 +223,9 @@ __device__ __forceinline__ void offdiag_block(const TangentSmem<T> &sm, int ee, 
         const T *qa = pa + q * L::kPoint;
         const T *qb = pb + q * L::kPoint;
         const T b0 = qb[0], b1 = qb[1], b2 = qb[2];
-        T h0, h1, h2, d0, d1, d2;
-        if constexpr (L::kPre) {
-            const T *ha = qa + L::kHG * L::kArr, *da = qa + L::kDG * L::kArr;
-            h0 = ha[0], h1 = ha[1], h2 = ha[2], d0 = da[0], d1 = da[1], d2 = da[2];
-        } else {
-            const T *cf = pc + q * L::kCoef;
-            const T ch = cf[0], cd = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
-            h0 = ch * a0, h1 = ch * a1, h2 = ch * a2, d0 = cd * a0, d1 = cd * a1, d2 = cd * a2;
-        }
+        const T *cf = pc + q * L::kCoef;
+        const T ch = cf[0], cd = cf[1], a0 = qa[0], a1 = qa[1], a2 = qa[2];
+        const T h0 = ch * a0, h1 = ch * a1, h2 = ch * a2, d0 = cd * a0, d1 = cd * a1, d2 = cd * a2;
         A00 = acc_t(h0, b0, A00);
         A11 = acc_t(h1, b1, A11);
         A22 = acc_t(h2, b2, A22);
@@ -232,21 +256,44 @@ __device__ __forceinline__ void diag_block(const TangentSmem<T> &sm, int ee, int
     using L = TangentLayout<T>;
     const T *pa = sm.v + ee * L::kElem + 3 * a;
     const T *pc = sm.coef + ee * 8 * L::kCoef;
-    T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
     T Ra0 = T(0), Ra1 = T(0), Ra2 = T(0);
+    if constexpr (L::kPre) {
+        // FP64: K_aa,ik = sum_q s_ai g_ak + delta_ik mu L_aa (s = (c lam + c m) g)
+        T k00 = gs, k11 = gs, k22 = gs, k12 = T(0), k02 = T(0), k01 = T(0);
+#pragma unroll kUnrollQ
+        for (int q = 0; q < 8; q++) {
+            const T *qa = pa + q * L::kPoint;
+            const T *cf = pc + q * L::kCoef;
+            const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
+            const T *sa = qa + L::kSG * L::kArr;
+            const T s0 = sa[0], s1 = sa[1], s2 = sa[2];
+            k00 = acc_t(s0, b0, k00);
+            k11 = acc_t(s1, b1, k11);
+            k22 = acc_t(s2, b2, k22);
+            k12 = acc_t(s1, b2, k12);
+            k02 = acc_t(s0, b2, k02);
+            k01 = acc_t(s0, b1, k01);
+            if (want_r) {
+                Ra0 = acc_t(cf[2], b0, acc_t(cf[7], b1, acc_t(cf[6], b2, Ra0)));
+                Ra1 = acc_t(cf[7], b0, acc_t(cf[3], b1, acc_t(cf[5], b2, Ra1)));
+                Ra2 = acc_t(cf[6], b0, acc_t(cf[5], b1, acc_t(cf[4], b2, Ra2)));
+            }
+        }
+        Kab[0][0] = k00, Kab[1][1] = k11, Kab[2][2] = k22;
+        Kab[1][2] = Kab[2][1] = k12;
+        Kab[0][2] = Kab[2][0] = k02;
+        Kab[0][1] = Kab[1][0] = k01;
+        Ra[0] = Ra0, Ra[1] = Ra1, Ra[2] = Ra2;
+        return;
+    }
+    T k00 = T(0), k11 = T(0), k22 = T(0), k12 = T(0), k02 = T(0), k01 = T(0);
 #pragma unroll kUnrollQ
     for (int q = 0; q < 8; q++) {
         const T *qa = pa + q * L::kPoint;
         const T *cf = pc + q * L::kCoef;
         const T b0 = qa[0], b1 = qa[1], b2 = qa[2];
-        T h0, h1, h2;
-        if constexpr (L::kPre) {
-            const T *ha = qa + L::kHG * L::kArr;
-            h0 = ha[0], h1 = ha[1], h2 = ha[2];
-        } else {
-            const T ch = cf[0];
-            h0 = ch * b0, h1 = ch * b1, h2 = ch * b2;
-        }
+        const T ch = cf[0];
+        const T h0 = ch * b0, h1 = ch * b1, h2 = ch * b2;
         k00 = acc_t(h0, b0, k00);
         k11 = acc_t(h1, b1, k11);
         k22 = acc_t(h2, b2, k22);
@@ -400,7 +447,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
         }
         const T cw = K.dJ * T(1.0 / 512.0);
         const T cl = cw * lam, cm = cw * m;
-        const T ch = T(0.5) * (cl + cm), cd = T(0.5) * (cl - cm);
+        const T ch = T(0.5) * (cl + cm), cd = T(0.5) * (cl - cm), cs = cl + cm;
         // 1 +- xi, 1 +- eta, 1 +- zeta at the lane's Gauss point (selected for FP64: element.cuh)
         T xp, xm, yp, ym, zp, zm;
         if constexpr (std::is_same<T, double>::value) {
@@ -436,8 +483,9 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
                 g[j] = W[0][j] * n0 + W[1][j] * n1 + W[2][j] * n2;
                 r[L::kG * L::kArr + j] = g[j];
                 if constexpr (L::kPre) {
-                    r[L::kHG * L::kArr + j] = ch * g[j];
-                    r[L::kDG * L::kArr + j] = cd * g[j];
+                    r[L::kLG * L::kArr + j] = cl * g[j];
+                    r[L::kMG * L::kArr + j] = cm * g[j];
+                    r[L::kSG * L::kArr + j] = cs * g[j];
                 }
             }
         }
