@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) k_residual(ElemArgs A, const double *__re
     if constexpr (!std::is_same<T, float>::value)  // FP64 and two-float calls store the state
         if (A.lin && active && mt.law != JETSCI_LINEAR_ELASTIC) {
             LinCoeffs<T> c;
-            lin_coeffs(st.aj, st.rdj, st.rdJ, K.dJ, st.m, lam, mu, c);
+            lin_coeffs(st.aj, st.rdj, K.dJ, st.lnJ, from_double<T>(element_lam_mu(A.mats, A.phase, e)), c);
             lin_store_t<T>(A.lin, e, l, c);
         }
     T f[3];
@@ -377,11 +377,11 @@ constexpr size_t tangent_smem_bytes(bool rows) {
 // then the block's element matrices are assembled over those records in shared memory and
 // written out as one contiguous span.
 template <typename T, typename VT, bool kRows>
-__global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs A, const double *__restrict__ u,
-                                                 const int64_t *__restrict__ rowptr,
-                                                 const uint8_t *__restrict__ slotmap,
-                                                 const uint8_t *__restrict__ first,
-                                                 VT *__restrict__ vals, double *__restrict__ R) {
+__device__ __forceinline__ void tangent_element_pass(ElemArgs A, const double *__restrict__ u,
+                                                     const int64_t *__restrict__ rowptr,
+                                                     const uint8_t *__restrict__ slotmap,
+                                                     const uint8_t *__restrict__ first,
+                                                     VT *__restrict__ vals, double *__restrict__ R) {
     using L = TangentLayout<T>;
     constexpr bool kFirst = L::kFirstWrites && !kRows;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
             if constexpr (!std::is_same<T, float>::value)  // FP64 and two-float calls store the state
                 if (A.lin && active) {
                     LinCoeffs<T> c;
-                    lin_coeffs(st.aj, st.rdj, st.rdJ, K.dJ, st.m, lam, mu, c);
+                    lin_coeffs(st.aj, st.rdj, K.dJ, st.lnJ, from_double<T>(element_lam_mu(A.mats, A.phase, e)), c);
                     lin_store_t<T>(A.lin, e, l, c);
                 }
 #pragma unroll
@@ -612,6 +612,25 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
     }
 }
 
+template <typename T, typename VT, bool kRows>
+__global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs A, const double *__restrict__ u,
+                                                 const int64_t *__restrict__ rowptr,
+                                                 const uint8_t *__restrict__ slotmap,
+                                                 const uint8_t *__restrict__ first,
+                                                 VT *__restrict__ vals, double *__restrict__ R) {
+    tangent_element_pass<T, VT, kRows>(A, u, rowptr, slotmap, first, vals, R);
+}
+
+// The FP64 scatter asks for four blocks per SM (80 registers; its 56 KB of shared memory allow
+// four), the occupancy its FP64-pipe-bound pair loop was tuned at.
+template <>
+__global__ void __launch_bounds__(TangentLayout<double>::kThreads, 4)
+    k_tangent<double, double, false>(ElemArgs A, const double *__restrict__ u, const int64_t *__restrict__ rowptr,
+                                     const uint8_t *__restrict__ slotmap, const uint8_t *__restrict__ first,
+                                     double *__restrict__ vals, double *__restrict__ R) {
+    tangent_element_pass<double, double, false>(A, u, rowptr, slotmap, first, vals, R);
+}
+
 // ---------------------------------------------------------------------------- K v, matrix-free
 // y_a += sum_q w detJ Y G_a with Y the linearised first Piola-Kirchhoff stress in the direction
 // Hv = grad_X v:  Y = sigma(Hv) for the linear law;  for the neo-Hookean law, with
@@ -622,9 +641,11 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
 // Q = Y adj(Jp)^T directly:
 //   Q = (mu / det Jp) Dv adj(Jp) adj(Jp)^T + (det Jp / det j^2) M' adj(j)^T,
 //   M' = m h'^T + lam tr(h') I,  h' = Dv adj(j) = det j h,
-// i.e. Q = s1 Dv adj(Jp) adj(Jp)^T + (alpha h'^T + beta tr(h') I) adj(j)^T with the per-point
-// coefficients s1 = mu / det Jp, alpha = m det Jp / det j^2, beta = lam det Jp / det j^2
-// (element.cuh, lin_coeffs).
+// i.e. Q = mu [Dv A0' + (alpha h'^T + beta tr(h') I) adj(j)^T] with A0' = adj(Jp) adj(Jp)^T /
+// det Jp from the geometry cache and the per-point coefficients alpha = (m / mu) det Jp / det j^2,
+// beta = (lam / mu) det Jp / det j^2 (element.cuh, lin_coeffs).  The nodal forces are linear in
+// Q and mu is the element's, so mu multiplies the three forces of a lane after the sum over the
+// Gauss points instead of each of the nine entries of Q at every point.
 // kReuse (FP64 and two-float): the coefficients come from the mesh's linearisation store (the
 // last FP64 or two-float residual or tangent, at its u) instead of u; u is not read.
 template <typename T, bool kReuse>
@@ -666,25 +687,40 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int d = 0; d < 3; d++) Q[i][d] = Y[i][0] * K.aJ[d][0] + Y[i][1] * K.aJ[d][1] + Y[i][2] * K.aJ[d][2];
-    } else {
-        LinCoeffs<T> c;
-        if constexpr (kReuse) {
-            lin_load_t<T>(A.lin, e, l, c);  // (states outside the law were flagged when stored)
-        } else {
-            NeoHookeanState<T> st;
-            neo_hookean_state(K, lam, mu, st);
-            ok = st.ok;
-            lin_coeffs(st.aj, st.rdj, st.rdJ, K.dJ, st.m, lam, mu, c);
-        }
+    } else if constexpr (std::is_same<T, float>::value) {
+        // FP32: Q = s1 Dv adj(Jp) adj(Jp)^T + (alpha h'^T + beta tr(h') I) adj(j)^T with
+        // s1 = mu / det Jp, alpha = m det Jp / det j^2, beta = lam det Jp / det j^2 (no cache; the
+        // mu-scaled form below took this issue-bound kernel from 56 to 64 registers, 0.86 -> 0.92 ms)
+        NeoHookeanState<T> st;
+        neo_hookean_state(K, lam, mu, st);
+        ok = st.ok;
+        const T s2 = K.dJ * st.rdj * st.rdj, al = s2 * st.m, be = s2 * lam, s1 = mu * st.rdJ;
+        T A0[3][3];
+        adj_gram(K.aJ, A0);
         T hp[3][3];
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * c.aj[0][k] + Dv[i][1] * c.aj[1][k] + Dv[i][2] * c.aj[2][k];
-        const T btr = c.beta * (hp[0][0] + hp[1][1] + hp[2][2]);
-        // A0 = adj(Jp) adj(Jp)^T (symmetric; read from the geometry cache for FP64 and two-float)
-        T A0[3][3];
-        if constexpr (std::is_same<T, double>::value || std::is_same<T, df64>::value) {
+            for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * st.aj[0][k] + Dv[i][1] * st.aj[1][k] + Dv[i][2] * st.aj[2][k];
+        const T btr = be * (hp[0][0] + hp[1][1] + hp[2][2]);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const T M0 = fma_t(al, hp[0][i], (i == 0) ? btr : T(0));
+            const T M1 = fma_t(al, hp[1][i], (i == 1) ? btr : T(0));
+            const T M2 = fma_t(al, hp[2][i], (i == 2) ? btr : T(0));
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const T p1 = Dv[i][0] * A0[0][d] + Dv[i][1] * A0[1][d] + Dv[i][2] * A0[2][d];
+                T q = s1 * p1;
+                q = fma_t(M0, st.aj[d][0], q);
+                q = fma_t(M1, st.aj[d][1], q);
+                Q[i][d] = fma_t(M2, st.aj[d][2], q);
+            }
+        }
+    } else {
+        LinCoeffs<T> c;
+        T A0[3][3];  // adj(Jp) adj(Jp)^T / det Jp (symmetric; from the geometry cache)
+        {
             const double *p = geom_point(A.geom, e, l);
             const double2 a01 = geom_pair(p, kGeomA0 / 2), a23 = geom_pair(p, kGeomA0 / 2 + 1),
                           a45 = geom_pair(p, kGeomA0 / 2 + 2);  // 00 11 | 22 12 | 02 01
@@ -692,19 +728,32 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
             A0[1][2] = A0[2][1] = from_double<T>(a23.y);
             A0[0][2] = A0[2][0] = from_double<T>(a45.x);
             A0[0][1] = A0[1][0] = from_double<T>(a45.y);
-        } else {
-            adj_gram(K.aJ, A0);
         }
+        if constexpr (kReuse) {
+            lin_load_t<T>(A.lin, e, l, c);  // (states outside the law were flagged when stored)
+        } else {
+            NeoHookeanState<T> st;
+            neo_hookean_state(K, lam, mu, st);
+            ok = st.ok;
+            lin_coeffs(st.aj, st.rdj, K.dJ, st.lnJ, from_double<T>(element_lam_mu(A.mats, A.phase, e)), c);
+        }
+        T hp[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) hp[i][k] = Dv[i][0] * c.aj[0][k] + Dv[i][1] * c.aj[1][k] + Dv[i][2] * c.aj[2][k];
+        const T btr = c.beta * (hp[0][0] + hp[1][1] + hp[2][2]);
+        // Q / mu = Dv A0 + (alpha h'^T + beta tr(h') I) adj(j)^T; mu is applied to the nodal forces
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            // row i of alpha h'^T + beta tr(h') I
             const T M0 = fma_t(c.alpha, hp[0][i], (i == 0) ? btr : T(0));
             const T M1 = fma_t(c.alpha, hp[1][i], (i == 1) ? btr : T(0));
             const T M2 = fma_t(c.alpha, hp[2][i], (i == 2) ? btr : T(0));
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                const T p1 = Dv[i][0] * A0[0][d] + Dv[i][1] * A0[1][d] + Dv[i][2] * A0[2][d];
-                T q = c.s1 * p1;
+                T q = Dv[i][0] * A0[0][d];
+                q = fma_t(Dv[i][1], A0[1][d], q);
+                q = fma_t(Dv[i][2], A0[2][d], q);
                 q = fma_t(M0, c.aj[d][0], q);
                 q = fma_t(M1, c.aj[d][1], q);
                 Q[i][d] = fma_t(M2, c.aj[d][2], q);
@@ -713,6 +762,10 @@ __device__ __forceinline__ void apply_mf_element(ElemArgs A, const double *__res
     }
     T f[3];
     nodal_force_of_moment(Q, K, l, f);
+    if constexpr (!std::is_same<T, float>::value)
+        if (mt.law != JETSCI_LINEAR_ELASTIC)  // (the neo-Hookean moment above is Q / mu: mu is the element's)
+#pragma unroll
+            for (int i = 0; i < 3; i++) f[i] = mu * f[i];
     if (active) {
         uint32_t bits = (positive(K.dJ) ? 0u : JETSCI_FLAG_BAD_ELEMENT) | (ok ? 0u : JETSCI_FLAG_BAD_STATE) |
                         (finite3(f) ? 0u : JETSCI_FLAG_NONFINITE);
@@ -806,6 +859,11 @@ __global__ void __launch_bounds__(128) k_fill_geom(const int32_t *__restrict__ c
     gauss_kinematics_coords<double>(conn, coords, nullptr, e, l, node, K, cu);
     double A0[3][3];
     adj_gram(K.aJ, A0);
+    const double rdJ = 1.0 / K.dJ;  // (the cache holds A0 / det Jp)
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) A0[i][j] *= rdJ;
     if (!active) return;
     double *p = geom + (int64_t)kGeomFields * 8 * e + 2 * l;
 #pragma unroll

@@ -282,6 +282,12 @@ struct ElemMaterial {
     double lam, mu;
 };
 
+// lam / mu of element e's phase (the same for any E at the phase's nu), read where it is used.
+__device__ __forceinline__ double element_lam_mu(const Material *__restrict__ mats, const int32_t *__restrict__ phase,
+                                                 int64_t e) {
+    return __ldg(&mats[__ldg(phase + e)].lam_mu);
+}
+
 __device__ __forceinline__ ElemMaterial element_material(const Material *__restrict__ mats,
                                                          const int32_t *__restrict__ phase,
                                                          const double *__restrict__ E_elem,
@@ -314,8 +320,8 @@ struct GaussKinematics {
 
 // Reference geometry of an element at its 8 Gauss points, kept per mesh for the FP64 kernels
 // (FP64 arithmetic is the scarce resource on this GPU, HBM bandwidth is not): fields Jp (0-8),
-// adj(Jp) (9-17), det Jp (18), an unused slot (19) and A0 = adj(Jp) adj(Jp)^T (20-25: 00 11 22
-// 12 02 01), stored in pairs as [element][field / 2][Gauss point][2] doubles, so that a lane
+// adj(Jp) (9-17), det Jp (18), an unused slot (19) and A0 = adj(Jp) adj(Jp)^T / det Jp (20-25:
+// 00 11 22 12 02 01; the matrix-free product's reference term), stored in pairs as [element][field / 2][Gauss point][2] doubles, so that a lane
 // reads two fields with one 16-byte load and an element's 8 lanes read 128 contiguous bytes.
 constexpr int kGeomJp = 0, kGeomAJ = 9, kGeomDJ = 18, kGeomA0 = 20, kGeomFields = 26;
 constexpr int kGeomKinPairs = 10;  // pairs holding Jp, adj(Jp) and det Jp
@@ -341,29 +347,28 @@ constexpr int kLapPairs = 36, kLapDiag = 28;
 
 // Linearisation of the neo-Hookean state at the last FP64 or two-float residual or tangent call,
 // kept per mesh for matrix-free products at that state, in the form those products use
-// (apply_mf_element): adj(j) (0-8), alpha = m det Jp / det j^2 (9), beta = lam det Jp / det j^2
-// (10) and s1 = mu / det Jp (11) per element and Gauss point, in pairs as
-// [element][6][Gauss point][2] doubles.
-constexpr int kLinAj = 0, kLinAlpha = 9, kLinBeta = 10, kLinS1 = 11, kLinPairs = 6;
+// (apply_mf_element): adj(j) (0-8), alpha = (m / mu) det Jp / det j^2 (9) and
+// beta = (lam / mu) det Jp / det j^2 (10) per element and Gauss point, and one padding value, in
+// pairs as [element][6][Gauss point][2] doubles.
+constexpr int kLinAj = 0, kLinAlpha = 9, kLinBeta = 10, kLinPairs = 6;
 
 template <typename T>
 struct LinCoeffs {
     T aj[3][3];
-    T alpha, beta, s1;
+    T alpha, beta;
 };
 
-// The coefficients at a neo-Hookean state: adj(j), 1 / det j (rdj), 1 / det Jp (rdJ), det Jp
-// (dJ), m = mu - lam ln J.
+// The coefficients at a neo-Hookean state: adj(j), 1 / det j (rdj), det Jp (dJ), ln J and
+// lam / mu (m / mu = 1 - (lam / mu) ln J).
 template <typename T>
-__device__ __forceinline__ void lin_coeffs(const T aj[3][3], T rdj, T rdJ, T dJ, T m, T lam, T mu, LinCoeffs<T> &c) {
+__device__ __forceinline__ void lin_coeffs(const T aj[3][3], T rdj, T dJ, T lnJ, T lam_mu, LinCoeffs<T> &c) {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int k = 0; k < 3; k++) c.aj[i][k] = aj[i][k];
     const T s2 = dJ * rdj * rdj;
-    c.alpha = s2 * m;
-    c.beta = s2 * lam;
-    c.s1 = mu * rdJ;
+    c.alpha = s2 * fma_t(-lam_mu, lnJ, T(1));
+    c.beta = s2 * lam_mu;
 }
 
 // The coefficients of a two-float (or FP64) neo-Hookean update, stored in FP64 (two-float values
@@ -373,7 +378,7 @@ __device__ __forceinline__ void lin_store_t(double *__restrict__ lin, int64_t e,
     const double f[2 * kLinPairs] = {to_double(c.aj[0][0]), to_double(c.aj[0][1]), to_double(c.aj[0][2]),
                                      to_double(c.aj[1][0]), to_double(c.aj[1][1]), to_double(c.aj[1][2]),
                                      to_double(c.aj[2][0]), to_double(c.aj[2][1]), to_double(c.aj[2][2]),
-                                     to_double(c.alpha),    to_double(c.beta),     to_double(c.s1)};
+                                     to_double(c.alpha),    to_double(c.beta),     0.0};
     double2 *p = reinterpret_cast<double2 *>(lin + (int64_t)2 * kLinPairs * 8 * e + 2 * l);
 #pragma unroll
     for (int k = 0; k < kLinPairs; k++) p[8 * k] = make_double2(f[2 * k], f[2 * k + 1]);
@@ -397,7 +402,6 @@ __device__ __forceinline__ void lin_load_t(const double *__restrict__ lin, int64
         for (int j = 0; j < 3; j++) c.aj[i][j] = from_double<T>(f[kLinAj + 3 * i + j]);
     c.alpha = from_double<T>(f[kLinAlpha]);
     c.beta = from_double<T>(f[kLinBeta]);
-    c.s1 = from_double<T>(f[kLinS1]);
 }
 
 // Kinematics at the lane's Gauss point from the lane's node's coordinates X and nodal field

@@ -17,6 +17,7 @@ namespace jetsci {
 struct Material {
     double lam, mu;    // Lame constants of the phase's own E
     double lam1, mu1;  // Lame constants per unit E (same nu)
+    double lam_mu;     // lam / mu = 2 nu / (1 - 2 nu), the same for any E at this nu
     int32_t law;
     int32_t pad;
 };

@@ -172,6 +172,7 @@ static jetsci_status create_impl(const double *coords, int64_t n_nodes, const in
         m->mats[p].mu1 = 1.0 / (2.0 * (1.0 + nu));
         m->mats[p].lam = mt.E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
         m->mats[p].mu = mt.E / (2.0 * (1.0 + nu));
+        m->mats[p].lam_mu = 2.0 * nu / (1.0 - 2.0 * nu);
         m->mats[p].law = mt.law;
         m->mats[p].pad = 0;
     }
