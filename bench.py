@@ -36,20 +36,20 @@ sys.path.insert(0, ROOT)
 METRIC = "hex8 elem/s (residual+tangent, K·v) at 128³, surrogate vs plain, % of HBM peak"
 
 # Work per element of the dominant kernel, k_tangent<double,double>:
-# executed FP64 operations of the formulation (ncu on the 64^3 fibre RVE: 5,424 DFMA x 2 +
-# 192 DADD + 1,284 DMUL per element; the pair form accumulated entry by entry, with the
+# executed FP64 operations of the formulation (ncu on the 64^3 fibre RVE: 5,432 DFMA x 2 +
+# 192 DADD + 1,252 DMUL per element; the pair form accumulated entry by entry, with the
 # geometric term mu L_ab read from the reference-Laplacian cache) and the algorithmic bytes
 # (write-once CSR values 1,959 + slot map and masks 96 + u, R and connectivity 82 + the
 # reference-geometry cache 1,216 + the stored linearisation 768 + L_ab 288).
-TANGENT_FP64_FLOP_PER_ELEM = 12_324.0
-# The same operations counted as FP64-pipe instructions (5,424 DFMA + 192 DADD + 1,284 DMUL):
+TANGENT_FP64_FLOP_PER_ELEM = 12_308.0
+# The same operations counted as FP64-pipe instructions (5,432 DFMA + 192 DADD + 1,252 DMUL):
 # each takes one slot of the pipe (2 per clock per SM), whatever its flop count.
-TANGENT_FP64_INSTR_PER_ELEM = 6_900.0
+TANGENT_FP64_INSTR_PER_ELEM = 6_876.0
 TANGENT_BYTES_PER_ELEM_FP64 = 4_409.0
 # DRAM bytes (read + write) per element of k_tangent<double,double> from one ncu capture of the
 # 64^3 fibre RVE (profiles/k_tangent_fp64_fibre64.md), scaled by the element count (the
 # coloured read-modify-writes re-read CSR rows once per colour, so traffic grows with elements).
-TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_586.0
+TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_617.0
 # FP32-value element kernels are bound by instruction issue (4 warp instructions per clock per SM),
 # not by a math pipe or DRAM: warp instructions per element from one ncu capture each of the 64^3 fibre
 # RVE (profiles/k_tangent_fp32_fibre64.md, k_gather_rows_fp32_fibre64.md, k_apply_mf_fp32_fibre64.md,
@@ -864,13 +864,13 @@ def main():
                          "traffic_note": "bytes per tangent call (8 colour launches), ncu at 64^3 scaled by elements",
                          "kernel": "k_tangent<double,double>",
                          "peak_source": "FP64 pipe: 2 DFMA/clk/SM (measured FP64 FMA rate) x 2 flop x 148 SMs x the maximum SM clock",
-                         "flop_note": "achieved counts the flops this formulation executes (12,324 per element); "
+                         "flop_note": "achieved counts the flops this formulation executes (12,308 per element); "
                                       "the pair form that accumulated the geometric term per Gauss point executed "
                                       "16,860 for the same tangent, so fewer flops in less time can lower frac",
                          "ms_per_launch_group": ms_tangent,
                          "fp64_pipe_instr_frac": TANGENT_FP64_INSTR_PER_ELEM * prob.n_elem / (ms_tangent * 1e-3) /
                                                  (2.0 * 148 * peaks.get("sm_max_mhz", 2032.0) * 1e6),
-                         "fp64_pipe_instr_note": "FP64-pipe instructions (DFMA, DADD, DMUL: 6,900 per element, ncu) "
+                         "fp64_pipe_instr_note": "FP64-pipe instructions (DFMA, DADD, DMUL: 6,876 per element, ncu) "
                                                  "per second over the pipe's 2 per clock per SM: the share of the "
                                                  "pipe's issue slots the executed work fills (frac counts a DADD or "
                                                  "DMUL as 1 flop against a peak of 2)",
