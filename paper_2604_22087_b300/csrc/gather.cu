@@ -19,7 +19,7 @@ namespace {
 constexpr int kGroupLanes = 8;  // lanes per node (lane = column node lb of the element)
 constexpr int kNodesPerWarp = 32 / kGroupLanes;
 constexpr int kRowWarps = 4;    // warps per block
-constexpr int kSlots = 32;      // neighbour slots per accumulation pass (more take further passes)
+constexpr int kSlots = 28;      // neighbour slots per accumulation pass (more take further passes)
 constexpr int kAccStride = 12;  // accumulator values per slot (3 x 3 block, 16-byte aligned)
 
 // elements whose blocks a lane loads at once (in flight together); measured at 128^3: 2 is
