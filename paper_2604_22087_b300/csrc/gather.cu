@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_gather_rows(int64_t n_nodes,
                 const uint32_t wx = __shfl_sync(0xffffffffu, sw.x, gl0 + j), wy = __shfl_sync(0xffffffffu, sw.y, gl0 + j);
                 if (j < nc) {
                     const int sl = (int)(((lb < 4 ? wx : wy) >> (8 * (lb & 3))) & 0xffu);
-                    if (sc < n_sc && sl / kSlots == sc) {
-                        VT *d = acc + kAccStride * (sl % kSlots);
+                    const int rel = sl - kSlots * sc;  // the slot within this pass
+                    if (sc < n_sc && (unsigned)rel < (unsigned)kSlots) {
+                        VT *d = acc + kAccStride * rel;
                         VT z[kAccStride];
 #pragma unroll
                         for (int c = 0; c < kAccStride / kV16; c++)
