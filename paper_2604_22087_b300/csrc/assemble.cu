@@ -152,6 +152,12 @@ struct TangentLayout {
     // are held in registers until the matrices are assembled, and three items per thread
     // instead of five were 5% faster (four warps: slower).
     static constexpr int kThreads = kPre ? 192 : (std::is_same<T, float>::value ? 96 : 8 * kElems);
+    // Blocks per SM the kernels are compiled for: FP64 4 (56 KB of shared memory; 80 registers
+    // with a 12-byte spill, where the compiler's own choice of 96 registers allowed three: 28.19
+    // -> 27.99 ms at 128^3), FP32 12 (56 registers; at 10 the compiler took 64 and the element
+    // pass issued 777 instead of 788 warp instructions per element but ran 4% slower), two-float
+    // 5 (96 registers, its own choice).
+    static constexpr int kMinBlocks = kPre ? 4 : (std::is_same<T, float>::value ? 12 : 5);
     static constexpr int kNumVec = kPre ? 4 : 1;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
     static constexpr int kElem = 200;
@@ -613,7 +619,8 @@ __device__ __forceinline__ void tangent_element_pass(ElemArgs A, const double *_
 }
 
 template <typename T, typename VT, bool kRows>
-__global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs A, const double *__restrict__ u,
+__global__ void __launch_bounds__(TangentLayout<T>::kThreads, TangentLayout<T>::kMinBlocks)
+    k_tangent(ElemArgs A, const double *__restrict__ u,
                                                  const int64_t *__restrict__ rowptr,
                                                  const uint8_t *__restrict__ slotmap,
                                                  const uint8_t *__restrict__ first,
@@ -621,15 +628,6 @@ __global__ void __launch_bounds__(TangentLayout<T>::kThreads) k_tangent(ElemArgs
     tangent_element_pass<T, VT, kRows>(A, u, rowptr, slotmap, first, vals, R);
 }
 
-// The FP64 scatter asks for four blocks per SM (80 registers; its 56 KB of shared memory allow
-// four), the occupancy its FP64-pipe-bound pair loop was tuned at.
-template <>
-__global__ void __launch_bounds__(TangentLayout<double>::kThreads, 4)
-    k_tangent<double, double, false>(ElemArgs A, const double *__restrict__ u, const int64_t *__restrict__ rowptr,
-                                     const uint8_t *__restrict__ slotmap, const uint8_t *__restrict__ first,
-                                     double *__restrict__ vals, double *__restrict__ R) {
-    tangent_element_pass<double, double, false>(A, u, rowptr, slotmap, first, vals, R);
-}
 
 // ---------------------------------------------------------------------------- K v, matrix-free
 // y_a += sum_q w detJ Y G_a with Y the linearised first Piola-Kirchhoff stress in the direction
