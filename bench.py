@@ -57,7 +57,7 @@ TANGENT_DRAM_BYTES_PER_ELEM_FP64 = 14_617.0
 # tangent: the write-once FP32 CSR values 980 + slot map 64 + u, R and connectivity 82 + L_ab 288;
 # matrix-free K.v: u, v, coordinates and the y write 98 + connectivity and phase 33).
 FP32_FORMS = {
-    "tangent_csr_fp32": {"warp_instr": 720.0 + 349.0, "dram_bytes": 2639.0 + 3528.0, "alg_bytes": 1414.0,
+    "tangent_csr_fp32": {"warp_instr": 778.0 + 348.0, "dram_bytes": 2638.0 + 3529.0, "alg_bytes": 1414.0,
                          "kernels": "k_tangent<float,float,1> (element pass) + k_gather_rows<float> (row pass)"},
     "apply_matrix_free_fp32": {"warp_instr": 308.0, "dram_bytes": 858.0, "alg_bytes": 131.0,
                                "kernels": "k_apply_mf<float,0> (eight colour launches)"},
@@ -65,7 +65,7 @@ FP32_FORMS = {
                       "kernels": "k_residual<float,0> (eight colour launches)"},
     # TF32: the tensor-core element pass (profiles/k_tf32_tangent_fibre64.md, tensor pipe active
     # 20.7% of its cycles) + the same row pass; the same algorithmic bytes as the FP32 tangent
-    "tangent_csr_tf32": {"warp_instr": 474.0 + 349.0, "dram_bytes": 2642.0 + 3528.0, "alg_bytes": 1414.0,
+    "tangent_csr_tf32": {"warp_instr": 474.0 + 348.0, "dram_bytes": 2642.0 + 3529.0, "alg_bytes": 1414.0,
                          "kernels": "k_tf32 (tensor-core element pass) + k_gather_rows<float> (row pass)",
                          "tensor_pipe_active_element_pass": 0.207},
 }
