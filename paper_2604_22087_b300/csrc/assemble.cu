@@ -155,8 +155,8 @@ struct TangentLayout {
     // Blocks per SM the kernels are compiled for: FP64 4 (56 KB of shared memory; 80 registers
     // with a 12-byte spill, where the compiler's own choice of 96 registers allowed three: 28.19
     // -> 27.99 ms at 128^3), FP32 12 (56 registers; at 10 the compiler took 64 and the element
-    // pass issued 777 instead of 788 warp instructions per element but ran 4% slower), two-float
-    // 5 (96 registers, its own choice).
+    // pass ran 4% slower), two-float 5 (96 registers, its own choice; at 6, 80 registers with a
+    // 16-byte spill, the tangent ran 18.15 -> 18.40 ms).
     static constexpr int kMinBlocks = kPre ? 4 : (std::is_same<T, float>::value ? 12 : 5);
     static constexpr int kNumVec = kPre ? 4 : 1;
     static constexpr int kPoint = sizeof(T) == 4 ? 24 : 25;
