@@ -22,13 +22,14 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
 
 # Regression guards at about ten times the errors measured on B300 (largest over the 16^3 sphere
-# RVE linear and stretched, the ragged box and the high-valence mesh): FP32 CSR values 2.0e-7,
-# R 5.5e-6, matrix-free K.v 8.9e-8, CSR K.v 2.0e-7; TF32 CSR values 1.15e-4, K.v 8.4e-5.  The
-# derived bounds are worst cases two orders above these; the guards catch a regression that
-# would stay inside them.  At 128^3 the measured errors are lower still (FP32 R 1.5e-6, values
-# 1.2e-7, K.v 5.2e-8; TF32 values 4.1e-5, K.v 6.9e-5).
+# RVE linear and stretched, the ragged box and the high-valence mesh): FP32 CSR values 1.8e-7,
+# R 4.4e-6, matrix-free K.v 1.4e-7, CSR K.v 1.9e-7; TF32 CSR values 6.0e-5, CSR K.v 1.0e-4
+# (its R and matrix-free K.v are the FP32 ones: TF32 changes only the element stiffness, which
+# the matrix-free product does not form).  The derived bounds are worst cases two orders above
+# these; the guards catch a regression that would stay inside them.  At 128^3 the measured
+# errors are lower still (FP32 R 1.7e-6, values 1.1e-7, K.v 9.9e-8; TF32 values 3.4e-5).
 GUARD = {"FP32": dict(vals=2e-6, R=6e-5, ymf=1e-6, ycsr=2e-6),
-         "TF32": dict(vals=1.2e-3, R=6e-5, ymf=1e-3, ycsr=1e-3)}
+         "TF32": dict(vals=1.2e-3, R=6e-5, ymf=1e-6, ycsr=1e-3)}
 
 
 def jetsci():
@@ -566,9 +567,10 @@ def full_size():
 
 # (precision name, tolerance of R, of CSR values, of K.v), normwise over the sampled rows; FP32
 # and TF32 at the regression guards of the small cases (tighter than their derived bounds).
-FULL_SIZE_FORMS = [("FP64", FP64_TOL, FP64_TOL, FP64_TOL), ("DF64", FP64_TOL, FP64_TOL, FP64_TOL),
-                   ("FP32", GUARD["FP32"]["R"], GUARD["FP32"]["vals"], GUARD["FP32"]["ycsr"]),
-                   ("TF32", GUARD["TF32"]["R"], GUARD["TF32"]["vals"], GUARD["TF32"]["ycsr"])]
+FULL_SIZE_FORMS = [("FP64", FP64_TOL, FP64_TOL, FP64_TOL, FP64_TOL),
+                   ("DF64", FP64_TOL, FP64_TOL, FP64_TOL, FP64_TOL),
+                   ("FP32", GUARD["FP32"]["R"], GUARD["FP32"]["vals"], GUARD["FP32"]["ymf"], GUARD["FP32"]["ycsr"]),
+                   ("TF32", GUARD["TF32"]["R"], GUARD["TF32"]["vals"], GUARD["TF32"]["ymf"], GUARD["TF32"]["ycsr"])]
 
 
 def test_full_size_adjoint_sampled_elements():
@@ -615,7 +617,7 @@ def test_full_size_fibre_rve_sampled_rows(full_size, form):
     values and K.v (matrix-free and CSR) against the oracle."""
     prob, mesh, nodes, rows = full_size
     J = jetsci()
-    name, tol_R, tol_K, tol_y = form
+    name, tol_R, tol_K, tol_ymf, tol_ycsr = form
     p = getattr(J, name)
     u, v = cuda(prob.u), cuda(prob.v)
     R = mesh.new_vector()
@@ -631,8 +633,8 @@ def test_full_size_fibre_rve_sampled_rows(full_size, form):
     for n in nodes:
         Rn, Kvn, krow = rows[n]
         assert np.max(np.abs(R_h[3 * n:3 * n + 3] - Rn)) <= tol_R * scale_R
-        assert np.max(np.abs(y_h[3 * n:3 * n + 3] - Kvn)) <= tol_y * scale_y
-        assert np.max(np.abs(yc_h[3 * n:3 * n + 3] - Kvn)) <= tol_y * scale_y
+        assert np.max(np.abs(y_h[3 * n:3 * n + 3] - Kvn)) <= tol_ymf * scale_y
+        assert np.max(np.abs(yc_h[3 * n:3 * n + 3] - Kvn)) <= tol_ycsr * scale_y
         for i in range(3):
             r = 3 * n + i
             cs = col[rp[r]:rp[r + 1]]
