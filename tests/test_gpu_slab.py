@@ -104,3 +104,70 @@ def test_fp32_owned_rows():
             g = gd[r]
             assert np.max(np.abs(lv[lrp[r]:lrp[r + 1]][o] - vals_ref[rp[g]:rp[g + 1]])) <= 5e-5 * np.max(np.abs(vals_ref))
         pm.close()
+
+
+def _gpu_rank(rank, world, port, out_dir):
+    """One rank of the two-process test: its part's sub-mesh on cuda:0, ghosts filled by the
+    gloo halo exchange of host copies, the FP64 calls through the library, its owned rows
+    against the oracle's rows of the whole mesh, the norm all-gathered over gloo."""
+    import os
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        torch.cuda.set_device(0)
+        _, prob, _ = CASES[0]
+        om = oracle.Mesh.of(prob)
+        rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+        vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
+        y_ref = oracle.apply_tangent(om, prob.u, prob.v)
+        s = S.decompose(prob.coords, prob.conn, world)[rank]
+        pm = S.SlabMesh(s, prob.coords, prob.phase, prob.materials)
+        u_h = torch.as_tensor(s.scatter_owned(prob.u))
+        v_h = torch.as_tensor(s.scatter_owned(prob.v))
+        S.exchange(s, u_h)
+        S.exchange(s, v_h)
+        u, v = u_h.cuda(), v_h.cuda()
+        m = pm.mesh
+        R = m.new_vector()
+        vals = m.tangent_csr(u, R=R)
+        y_mf = m.apply_tangent(None, v)
+        y_csr = m.apply_tangent(None, v, mode=J().CSR, vals=vals)
+        assert m.check() == 0
+        gd, n = s.dofs(), s.n_owned_dof
+        sR, sK, sy = np.max(np.abs(R_ref)), np.max(np.abs(vals_ref)), np.max(np.abs(y_ref))
+        assert np.max(np.abs(pm.owned(R).cpu().numpy() - R_ref[gd[:n]])) <= FP64_TOL * sR
+        assert np.max(np.abs(pm.owned(y_mf).cpu().numpy() - y_ref[gd[:n]])) <= FP64_TOL * sy
+        assert np.max(np.abs(pm.owned(y_csr).cpu().numpy() - y_ref[gd[:n]])) <= FP64_TOL * sy
+        lrp, lcol = m.pattern()
+        lrp, lcol, lv = lrp.cpu().numpy(), lcol.cpu().numpy(), vals.cpu().numpy()
+        for r in range(n):
+            lc = gd[lcol[lrp[r]:lrp[r + 1]]]
+            o = np.argsort(lc)
+            g = gd[r]
+            assert np.array_equal(lc[o], col[rp[g]:rp[g + 1]])
+            assert np.max(np.abs(lv[lrp[r]:lrp[r + 1]][o] - vals_ref[rp[g]:rp[g + 1]])) <= FP64_TOL * sK
+        nrm = S.norm2(s, pm.owned_norm(R).item())
+        ref = oracle.norm2(R_ref)
+        assert abs(nrm - ref) <= 1e-14 * ref
+        pm.close()
+        with open(os.path.join(out_dir, f"rank{rank}.ok"), "w") as f:
+            f.write(repr(nrm))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_processes_on_the_gpu(tmp_path):
+    """Two processes (spawned, gloo over 127.0.0.1), each with its part on the one GPU: the
+    kernels of the two ranks never wait on each other (they meet only in host-side gloo
+    collectives between calls), so this runs the multi-rank path of the slab decomposition
+    through the library as separate processes do."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    mp.spawn(_gpu_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    vals = [open(tmp_path / f"rank{r}.ok").read() for r in range(2)]
+    assert vals[0] == vals[1]
