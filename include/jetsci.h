@@ -152,6 +152,16 @@ jetsci_status jetsci_mesh_check(jetsci_mesh mesh, uint32_t *flags_host);
  * bytes of device memory and synchronises `stream`. */
 jetsci_status jetsci_mesh_validate(jetsci_mesh mesh, uint64_t *counts_host, void *stream);
 
+/* Test hook for the bounded waits of the tensor-core kernels.  Their tcgen05 MMAs signal
+ * completion on an mbarrier that every thread polls a bounded number of times; a wait that runs
+ * out raises JETSCI_FLAG_NONFINITE and the kernel finishes instead of hanging.  This runs that
+ * wait on the current device: one block initialises an mbarrier that expects one arrival,
+ * arrives on it if `arrive` is non-zero, then polls it at most max_iter times (1 .. 2^20).
+ * *timed_out_host = 1 if the wait ran out (arrive = 0: nothing completes the barrier), 0 if it
+ * completed.  The device stays usable either way.  Synchronises the current device's legacy
+ * default stream.  JETSCI_ERR_ARG for a NULL output or max_iter out of range. */
+jetsci_status jetsci_selftest_bounded_wait(uint32_t max_iter, int arrive, uint32_t *timed_out_host);
+
 /* ---------------------------------------------------------------------------
  * Global residual R(u) = sum_e P_e^T R_e (Section II-A, R(u) = 0), with
  * R_e(a,i) = sum_q w_q detJ_q (F S)_iJ G_aJ.

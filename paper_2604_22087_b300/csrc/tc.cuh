@@ -95,6 +95,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
 }
 
+// One arrival on an mbarrier from a thread (completes its phase when the expected count is 1).
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_addr(mbar)) : "memory");
+    (void)state;
+}
+
 // Makes a freshly initialised mbarrier visible to the async proxy (tensor-core commits).
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

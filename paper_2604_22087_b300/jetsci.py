@@ -27,7 +27,7 @@ _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_MESH", 5:
 # Names the C ABI exports (include/jetsci.h); checked by the CPU tests.
 EXPORTS = [
     "jetsci_mesh_create", "jetsci_mesh_destroy", "jetsci_mesh_info", "jetsci_mesh_check",
-    "jetsci_mesh_copy_pattern", "jetsci_mesh_validate",
+    "jetsci_mesh_copy_pattern", "jetsci_mesh_validate", "jetsci_selftest_bounded_wait",
     "jetsci_residual", "jetsci_tangent_csr", "jetsci_apply_tangent", "jetsci_material_grad",
     "jetsci_assemble_element_blocks", "jetsci_norm2", "jetsci_norm2_static", "jetsci_last_error",
     "jetsci_version",
@@ -67,6 +67,7 @@ def _load():
         "jetsci_assemble_element_blocks": [_vp, _vp, _vp, i32, _vp],
         "jetsci_norm2": [_vp, _vp, i64, _vp, _vp],
         "jetsci_norm2_static": [_vp, i64, _vp, _vp],
+        "jetsci_selftest_bounded_wait": [C.c_uint32, i32, C.POINTER(C.c_uint32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -248,6 +249,14 @@ class Mesh:
         out = torch.empty(1, dtype=torch.float64, device="cuda") if out is None else out
         _check(lib.jetsci_norm2(self._h, _ptr(x), x.numel(), _ptr(out), _stream(stream)))
         return out
+
+
+def selftest_bounded_wait(max_iter, arrive):
+    """Runs the tensor-core kernels' bounded mbarrier wait on a barrier that one arrival
+    completes (arrive=True) or that nothing completes; True if the wait ran out."""
+    out = C.c_uint32(0)
+    _check(lib.jetsci_selftest_bounded_wait(int(max_iter), 1 if arrive else 0, C.byref(out)))
+    return bool(out.value)
 
 
 def version():

@@ -835,3 +835,27 @@ def test_row_gather_batch_edges(n):
         assert relerr(R.cpu().numpy(), R_ref) <= tr, name
     assert mesh.check() == 0
     mesh.close()
+
+
+def test_bounded_wait_runs_out_and_reports():
+    """The bounded mbarrier wait of the tensor-core kernels: on a barrier that nothing completes
+    it gives up after its poll limit and reports it (no hang, no fault), on one that an arrival
+    completes it returns at once; the device stays usable (a tangent afterwards matches the
+    oracle)."""
+    J = jetsci()
+    assert J.selftest_bounded_wait(1000, arrive=False) is True
+    assert J.selftest_bounded_wait(1000, arrive=True) is False
+    assert J.selftest_bounded_wait(1, arrive=True) is False
+    with pytest.raises(J.JetsciError):
+        J.selftest_bounded_wait(0, arrive=True)
+    prob = PROBLEMS[2][1]
+    om = oracle.Mesh.of(prob)
+    rp, col = oracle.csr_pattern(prob.conn, prob.n_nodes)
+    vals_ref, R_ref = oracle.tangent_csr(om, prob.u, rp, col)
+    mesh = J.Mesh.of(prob)
+    R = mesh.new_vector()
+    vals = mesh.tangent_csr(cuda(prob.u), R=R)
+    assert relerr(vals.cpu().numpy(), vals_ref) <= FP64_TOL
+    assert relerr(R.cpu().numpy(), R_ref) <= FP64_TOL
+    assert mesh.check() == 0
+    mesh.close()
